@@ -1,0 +1,209 @@
+/*
+ * grest.h -- C ABI of libgrest: GPU tracking of the leading eigenpairs of an
+ * evolving graph with the G-REST update (Graph Rayleigh-Ritz Eigenspace
+ * Tracking) of "Subspace Projection Methods for Fast Spectral Embeddings of
+ * Evolving Graphs" (arXiv 2603.19439).
+ *
+ * The calls follow the paper's Problem 1 (Sec. 2.1): given the K leading
+ * eigenpairs {(lambda_j, x_j)} of an N x N matrix and an (N+S) x (N+S)
+ * perturbation Delta (Eq. adj_update, Sec. 2), estimate the K leading
+ * eigenpairs of the updated matrix.  Alg. 2 applies that update once per
+ * received Delta: grest_init is Alg. 2's input and initial pairs (line 3),
+ * grest_apply_update is one pass of the loop (receive Delta, pad X, build an
+ * orthonormal basis Z, solve the projected eigenproblem, lift X = Z F_K), and
+ * grest_get_embedding returns (X_K, Lambda_K).
+ *
+ * Conventions common to every call:
+ *  - Status codes only; no C++ exception crosses this boundary.
+ *  - Node ids are 0-based.  The S new nodes of an update take the ids
+ *    N .. N+S-1, N being the number of ids before the update (Sec. 2).
+ *  - Dense N x K blocks are row-major (row i holds node i's K coordinates).
+ *  - Every input array is owned by the caller and is only read during the
+ *    call (its contents are copied); the context owns all device memory it
+ *    allocates; output arrays are allocated by the caller.
+ *  - A context is bound to the CUDA device that was current in grest_init
+ *    and to one CUDA stream; it must not be used by two threads at once.
+ *  - All computation runs in CUDA kernels of this library on that device.
+ *    There is no CPU fallback: without a usable GPU every call returns
+ *    GREST_ERR_CUDA.
+ */
+#ifndef GREST_H
+#define GREST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grest_ctx grest_ctx; /* opaque; owns every device buffer */
+
+typedef enum {
+  GREST_OK = 0,
+  GREST_ERR_INVALID_ARG = 1,     /* bad pointer, size or configuration field */
+  GREST_ERR_INVALID_UPDATE = 2,  /* batch violates Sec. 2's definition of Delta */
+  GREST_ERR_OOM = 3,             /* device allocation failed */
+  GREST_ERR_CAPACITY = 4,        /* node or edge capacity of the context exceeded */
+  GREST_ERR_NUMERIC = 5,         /* fewer than K Ritz pairs, or a Cholesky broke down */
+  GREST_ERR_CUDA = 6,            /* CUDA runtime error (no device, launch failure) */
+  GREST_ERR_TIMEOUT = 7,         /* a bounded device-side wait expired */
+  GREST_ERR_UNSUPPORTED = 8      /* option not implemented in this build */
+} grest_status;
+
+/* Operator whose leading eigenpairs are tracked (Sec. 2 and Sec. 4.3). */
+enum {
+  GREST_OP_ADJ = 0,  /* adjacency A; pairs ordered by |lambda| descending (Sec. 2) */
+  GREST_OP_LAP = 1,  /* T = alpha I - (D - A), alpha = 2 d_max of the current graph */
+  GREST_OP_NLAP = 2  /* T_n = 2I - L_n = I + D^-1/2 A D^-1/2 (isolated node: identity row) */
+};
+
+/* Projection subspace (Table 1 and Sec. 5): */
+enum {
+  GREST_SUB_GREST2 = 0, /* Ran[X_bar, P_perp W]            (residual-mode subspace)  */
+  GREST_SUB_GREST3 = 1, /* Ran[X_bar, P_perp [W, Delta_2]]  exact new-node block      */
+  GREST_SUB_RSVD = 2,   /* as GREST3 with Delta_2 replaced by its RSVD basis (Sec. 3.5) */
+  GREST_SUB_AUTO = 3    /* GREST3 when S <= L+P, RSVD otherwise (default)              */
+};
+
+enum { GREST_FP64 = 0, GREST_MIXED = 1 };                 /* arithmetic of the step */
+enum { GREST_PROJ_EXACT = 0, GREST_PROJ_LOWRANK = 1 };   /* Eq. (main2) / Eq. (main3) */
+enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };          /* W = P_perp M_new X_bar / P_perp Delta X_bar */
+
+/* grest_config.flags */
+#define GREST_FLAG_CHECK 1u /* after each step compute residual diagnostics into grest_stats */
+
+typedef struct {
+  int32_t op;          /* GREST_OP_*                                                   */
+  int32_t k;           /* K, number of tracked pairs, 1 <= k <= 64                      */
+  int32_t subspace;    /* GREST_SUB_*                                                  */
+  int32_t L, P;        /* RSVD rank and oversampling (Sec. 3.5); L+P <= 256             */
+  int32_t precision;   /* GREST_FP64 | GREST_MIXED                                      */
+  int32_t projection;  /* GREST_PROJ_*                                                 */
+  int32_t w_block;     /* GREST_WB_*                                                   */
+  uint32_t flags;      /* GREST_FLAG_*                                                 */
+  uint64_t seed;       /* key of the counter-based generator that draws Omega          */
+  double drop_tol;     /* relative pivot below which a basis direction is dropped      */
+  int64_t node_capacity;   /* maximum number of node ids; 0 = 1.25 x initial + 1024     */
+  int64_t nnz_capacity;    /* directed-edge arena size;   0 = 2 x initial + 2^20        */
+  int64_t max_batch_edges; /* largest n_ins + n_del per update; 0 = 2^20 (grows on demand) */
+} grest_config;
+
+/*
+ * One update Delta (Eq. adj_update, Sec. 2).
+ *  ins_u/ins_v (n_ins): edges to add.  An edge between two old nodes is a +1
+ *      entry of K and must not exist yet; an edge touching a new node is an
+ *      entry of G or C.  Each undirected edge is listed once, u != v.
+ *  ins_w: weights of the inserted edges for a weighted context (positive,
+ *      finite); NULL means 1.  Must be NULL for an unweighted context.
+ *  del_u/del_v (n_del): existing edges among old nodes to remove (-1 entries of K).
+ *  del_nodes (n_del_nodes): old live nodes to remove.  The paper leaves node
+ *      removal to future work (Sec. 6); this library reads it as: every
+ *      incident edge is removed, the id is tombstoned (never reused), the
+ *      operator becomes the principal submatrix on live nodes, and the
+ *      tombstoned rows of X are zeroed before X is re-orthonormalized.
+ *      No edge of the same batch may touch a removed node.
+ *  on_device: 0 = the arrays are host memory, 1 = device memory of the
+ *      context's device.
+ * The whole batch is validated before any state changes; on any error the
+ * context is left exactly as it was (GREST_ERR_INVALID_UPDATE).
+ */
+typedef struct {
+  int64_t n_new_nodes;
+  int64_t n_ins;
+  const int32_t *ins_u, *ins_v;
+  const double *ins_w;
+  int64_t n_del;
+  const int32_t *del_u, *del_v;
+  int64_t n_del_nodes;
+  const int32_t *del_nodes;
+  int32_t on_device;
+} grest_update;
+
+/* Per-step diagnostics (filled by grest_apply_update / grest_get_stats). */
+typedef struct {
+  int64_t step;            /* updates applied so far                                   */
+  int64_t n_nodes;         /* node ids after the step (live + tombstoned)               */
+  int64_t nnz;             /* directed nonzeros of the adjacency after the step        */
+  int32_t m;               /* dimension of Z                                           */
+  int32_t k_u;             /* columns of X_bar kept (< k only after node removal)      */
+  int32_t rank_q;          /* columns added to X_bar (W and new-node block, after drop) */
+  int32_t rank_y;          /* rank of the RSVD sketch Y (0 when not used)              */
+  int32_t mode;            /* 2 = GREST2, 3 = GREST3, 4 = RSVD                          */
+  int32_t pad0;
+  double pivot_kept_min;   /* smallest kept pivot / largest pivot                      */
+  double pivot_dropped_max;/* largest dropped pivot / largest pivot (0 if none)        */
+  double boundary_gap;     /* |theta_K - theta_{K+1}| / |theta_1| in the ordering      */
+  double orth_err;         /* max |X^T X - I|           (GREST_FLAG_CHECK)             */
+  double max_residual;     /* max_j ||M x_j - theta_j x_j|| / |theta_1| (CHECK)         */
+  double galerkin;         /* max |Z^T (M x_j - theta_j x_j)| / |theta_1| (CHECK)       */
+  float ms_total, ms_graph, ms_spmm, ms_basis, ms_project, ms_eig, ms_lift, ms_refine;
+} grest_stats;
+
+/* Fill *cfg with defaults for k tracked pairs: ADJ, AUTO, L = P = 100
+ * (the paper's setting, Sec. 5), FP64, EXACT, RESID, drop_tol 1e-7. */
+grest_status grest_config_default(grest_config *cfg, int32_t k);
+
+/*
+ * Create a context (Alg. 2 input).  The graph is given as a symmetric CSR on
+ * the host: rowptr[n+1] (int64), col[rowptr[n]] (int32, no self loops, each
+ * undirected edge present in both rows), val (nullable; positive weights,
+ * symmetric).  U0 (n x k row-major, orthonormal columns) and theta0 (k) are
+ * the initial leading pairs computed by any direct eigensolver (Alg. 2,
+ * line 3); both are required in this build (NULL -> GREST_ERR_UNSUPPORTED).
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ */
+grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowptr,
+                        const int32_t *col, const double *val, const double *U0,
+                        const double *theta0, void *cuda_stream, grest_ctx **out);
+
+/*
+ * Apply one update (one iteration of Alg. 2's loop): validate and apply
+ * Delta to the device CSR, pad X, build Z = [X_bar, Q] with
+ * Q = orth(P_perp [W, B]) (Sec. 3.3-3.5), form H = Z^T M Z (Eq. main2) or the
+ * rank-K surrogate (Eq. main3), solve H F = F Theta, set X = Z F_K,
+ * Lambda = Theta_K.  Returns when the step has finished on the device.
+ * stats may be NULL.
+ */
+grest_status grest_apply_update(grest_ctx *ctx, const grest_update *upd, grest_stats *stats);
+
+/* Wait for all work of the context's stream. */
+grest_status grest_sync(grest_ctx *ctx);
+
+/*
+ * Copy out (X_K, Lambda_K).  n_out (required) receives the number of node
+ * ids.  U (nullable) receives n_out x k row-major values (tombstoned rows are
+ * zero), theta (nullable) k values in tracking order, live_mask (nullable)
+ * n_out bytes (1 = live).  Columns are sign-normalized: the entry of largest
+ * magnitude (lowest index on ties) is positive.  on_device selects host (0)
+ * or device (1) destination pointers.  Call with all outputs NULL to query n.
+ */
+grest_status grest_get_embedding(grest_ctx *ctx, double *U, double *theta, uint8_t *live_mask,
+                                 int64_t *n_out, int32_t on_device);
+
+/* All m Ritz values of the last step in tracking order (Alg. 1); *m_out receives m.
+ * ritz may be NULL to query m; it must hold at least m values otherwise. */
+grest_status grest_get_ritz_values(grest_ctx *ctx, double *ritz, int32_t *m_out);
+
+/* Diagnostics of the last completed step. */
+grest_status grest_get_stats(grest_ctx *ctx, grest_stats *stats);
+
+/*
+ * Y = M X for the context's current operator M (Sec. 4.3 kinds, principal
+ * submatrix on live nodes).  X and Y are device arrays of n_nodes rows,
+ * row-major with leading dimensions ldx, ldy (>= w), w <= 288 columns.  This
+ * is the library's CSR SpMM, exposed for residual checks and measurement.
+ */
+grest_status grest_apply_operator(grest_ctx *ctx, const double *X, int64_t ldx, double *Y,
+                                  int64_t ldy, int32_t w);
+
+/* Release every device buffer of the context. NULL is ignored. */
+void grest_destroy(grest_ctx *ctx);
+
+/* Static string naming a status code. */
+const char *grest_status_str(grest_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GREST_H */

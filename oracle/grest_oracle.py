@@ -32,7 +32,10 @@ Readings where the paper is silent (each is restated in the design doc):
   R4  sign: each output column is flipped so its largest-|.| entry (lowest
       index among equal magnitudes) is positive.
   R5  rank deficiency: column-pivoted QR, columns whose |R_ii| falls below
-      drop_tol * |R_00| are dropped (Sec. 3.4 notes the low rank of Delta_2).
+      drop_tol * max(|R_00|, |theta_1|) are dropped (Sec. 3.4 notes the low
+      rank of Delta_2); |theta_1| of the previous step is about ||M||_2, so a
+      block that is pure rounding noise (W when X is exact and Delta = 0) is
+      dropped instead of spanning random directions.
   R6  Omega: Philox4x64-10 + Box-Muller, see oracle/philox.py.
   R7  the SVD of the (L+P) x S matrix in S.2 is taken through the eigenpairs
       of B B^T; exact basis when S <= L+P, RSVD otherwise (AUTO).
@@ -244,17 +247,19 @@ def project_out(X, V):
     return V - X @ (X.T @ V)
 
 
-def orth_pivoted(V, drop_tol):
+def orth_pivoted(V, drop_tol, abs_ref=0.0):
     """Orthonormal basis of Ran(V) by Householder QR with column pivoting;
-    columns with |R_ii| <= drop_tol * |R_00| are dropped.
+    columns with |R_ii| <= drop_tol * max(|R_00|, abs_ref) are dropped
+    (reading R5: abs_ref is a magnitude of the operator, so a block made only
+    of rounding noise is dropped whole).
     Returns (Q, kept_min_ratio, dropped_max_ratio)."""
     if V.shape[1] == 0:
         return np.zeros((V.shape[0], 0)), np.inf, 0.0
     Q, R, _ = sla.qr(V, mode="economic", pivoting=True)
     dg = np.abs(np.diag(R))
-    if dg.size == 0 or dg[0] == 0.0:
+    if dg.size == 0 or max(dg[0], abs_ref) == 0.0:
         return np.zeros((V.shape[0], 0)), np.inf, 0.0
-    ratio = dg / dg[0]
+    ratio = dg / max(dg[0], abs_ref)
     keep = ratio > drop_tol
     r = int(np.argmin(keep)) if not np.all(keep) else keep.size
     kmin = float(ratio[r - 1]) if r else np.inf
@@ -262,10 +267,10 @@ def orth_pivoted(V, drop_tol):
     return Q[:, :r], kmin, dmax
 
 
-def orth_against(X, V, drop_tol):
+def orth_against(X, V, drop_tol, abs_ref=0.0):
     """Q = orth(P_perp V), re-projected once against X (two projection passes)."""
     V1 = project_out(X, V)
-    Q1, kmin, dmax = orth_pivoted(V1, drop_tol)
+    Q1, kmin, dmax = orth_pivoted(V1, drop_tol, abs_ref)
     if Q1.shape[1] == 0:
         return Q1, kmin, dmax
     V2 = project_out(X, Q1)
@@ -296,11 +301,11 @@ def normalize_signs(X):
 
 # --------------------------------------------------------- RSVD (Sec. 3.5)
 
-def rsvd_range_basis(E, Xb, Omega, L, drop_tol):
+def rsvd_range_basis(E, Xb, Omega, L, drop_tol, abs_ref=0.0):
     """Steps S.1-S.4: Y = P_perp Delta_2 Omega, M = orth(Y), SVD of M^T P_perp Delta_2
     (through its Gram, reading R7), R = M U_hat_L.  Returns (R, rank of M)."""
     Y = project_out(Xb, E @ Omega)                              # S.1
-    Mb, _, _ = orth_pivoted(Y, drop_tol)                        # M = orth(Ran(Y))
+    Mb, _, _ = orth_pivoted(Y, drop_tol, abs_ref)               # M = orth(Ran(Y))
     if Mb.shape[1] == 0:
         return np.zeros((E.shape[0], 0)), 0
     # S.2: M^T P_perp Delta_2 = M^T Delta_2 - (M^T X_bar)(X_bar^T Delta_2), E kept sparse
@@ -332,9 +337,10 @@ def grest_step(state: State, b, cfg: Config, weighted=False, keep=False):
     Xb[:n] = state.X
     if np.asarray(b.del_nodes).size:
         Xb[~live] = 0.0
-        Xb, _, _ = orth_pivoted(Xb, cfg.drop_tol)
+        Xb, _, _ = orth_pivoted(Xb, cfg.drop_tol, 1.0)
     Ku = Xb.shape[1]
     info.K_u = Ku
+    scale = abs(state.lam[0]) if state.lam.size else 0.0   # |theta_1| ~ ||M||_2 (reading R5)
 
     # Delta of the operator (used by the paper's W block and by Eq. main3)
     def delta_op():
@@ -359,14 +365,14 @@ def grest_step(state: State, b, cfg: Config, weighted=False, keep=False):
         use_rsvd = cfg.subspace == SUB_RSVD or (cfg.subspace == SUB_AUTO and S > q)
         if use_rsvd:
             Omega = gaussian_matrix(cfg.seed, state.step, S, q)
-            Bblk, _ = rsvd_range_basis(E, Xb, Omega, cfg.L, cfg.drop_tol)
+            Bblk, _ = rsvd_range_basis(E, Xb, Omega, cfg.L, cfg.drop_tol, scale)
         else:
             Bblk = project_out(Xb, E.toarray())
     info.mode = "GREST2" if (S == 0 or cfg.subspace == SUB_GREST2) else ("RSVD" if use_rsvd else "GREST3")
 
     # orthonormalize only P_perp [W, B] (partial-orthogonality remark, Sec. 4)
     V = np.hstack([W, Bblk])
-    Q, kmin, dmax = orth_against(Xb, V, cfg.drop_tol)
+    Q, kmin, dmax = orth_against(Xb, V, cfg.drop_tol, scale)
     info.pivots_kept_min, info.pivots_dropped_max = kmin, dmax
     Z = np.hstack([Xb, Q])
     m = Z.shape[1]

@@ -1,0 +1,148 @@
+// Internal declarations shared by the libgrest translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/grest.h"
+
+namespace grest {
+
+constexpr int kWarp = 32;
+
+// Error word written by device-side validation; kernels that change state
+// return early once it is non-zero, so a failed step leaves no trace.
+enum DevErr : int32_t {
+  DERR_NONE = 0,
+  DERR_RANGE = 1,        // node id out of range
+  DERR_SELF = 2,         // self loop
+  DERR_DEAD = 3,         // edge touches a tombstoned or removed node
+  DERR_DUP = 4,          // the same edge twice in a batch
+  DERR_EXISTS = 5,       // inserted edge already present
+  DERR_MISSING = 6,      // deleted edge absent
+  DERR_NODE = 7,         // bad removed-node id (range, duplicate, dead)
+  DERR_WEIGHT = 8,       // weight not positive and finite
+  DERR_CAPACITY = 9,     // edge arena exhausted
+  DERR_NUMERIC = 10,     // Cholesky breakdown / rank below K
+};
+
+__device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
+
+// ---------------------------------------------------------------- CSR state
+// Slack CSR: row r occupies col[row_off[r] .. row_off[r] + row_len[r]) sorted
+// by column, inside a slot of row_cap[r] entries.  Rows that outgrow their slot
+// move to fresh space at the top of the arena (arena_top).
+struct Csr {
+  int64_t n = 0;          // node ids in use
+  int64_t n_cap = 0;      // capacity of the per-node arrays
+  int64_t nnz_cap = 0;    // arena entries
+  int64_t* row_off = nullptr;
+  int32_t* row_len = nullptr;
+  int32_t* row_cap = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;  // nullptr for an unweighted graph
+  uint8_t* live = nullptr;
+  double* deg = nullptr;     // weighted degree
+  double* dis = nullptr;     // d^-1/2 (0 for isolated or dead nodes)
+  int64_t* arena_top = nullptr;  // device scalar
+  double* dmax = nullptr;        // device scalar, max degree over live nodes
+};
+
+// Operator description for the SpMM epilogue (Sec. 4.3).
+struct OpParams {
+  int op;                  // GREST_OP_*
+  const double* deg;       // degree (LAP)
+  const double* dis;       // d^-1/2 (NLAP)
+  const double* dmax;      // device scalar (LAP: alpha = 2 dmax)
+  const uint8_t* live;
+};
+
+// ------------------------------------------------------------ launchers
+// scan.cu
+size_t scan_temp_bytes(int64_t n);
+// exclusive prefix sum of n int64 values; out may alias in; writes the total
+// to out[n] (out must hold n+1 values).
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
+
+// graph.cu
+struct BatchDev {
+  int64_t S = 0, n_ins = 0, n_del = 0, n_dn = 0;
+  const int32_t *ins_u = nullptr, *ins_v = nullptr, *del_u = nullptr, *del_v = nullptr, *dn = nullptr;
+  const double* ins_w = nullptr;
+};
+struct GraphWork {
+  int64_t ent_cap = 0;       // capacity of the entry arrays
+  int64_t tmp_cap = 0;       // merged-row staging entries
+  int32_t* cnt = nullptr;    // per row [n_cap+1]
+  int64_t* seg = nullptr;    // segment offsets [n_cap+1]
+  int32_t* cursor = nullptr; // [n_cap]
+  uint8_t* delflag = nullptr;// [n_cap]
+  int64_t* rowflag = nullptr;// [n_cap+1] scan scratch
+  int32_t* touched = nullptr;// [n_cap]
+  int64_t* tmp_off = nullptr;// [n_cap+1]
+  int64_t* need = nullptr;   // [n_cap+1]
+  int32_t* new_len = nullptr;// [n_cap]
+  uint64_t* ekey = nullptr;  // [ent_cap] entry keys
+  int32_t* erow = nullptr;   // [ent_cap]
+  double* ew = nullptr;      // [ent_cap] weight (inserts)
+  int32_t* eins = nullptr;   // [ent_cap] inserts before entry (prefix)
+  int32_t* tmp_col = nullptr;// [tmp_cap]
+  double* tmp_val = nullptr; // [tmp_cap]
+  int64_t* dn_pref = nullptr;// [max removed nodes + 1]
+  int64_t dn_cap = 0;
+  int32_t* long_rows = nullptr; // rows with len > kLongRow [n_cap]
+  int64_t* scalars = nullptr;   // device scalars: [0] n_touched [1] n_long [2] total entries [3] tmp total [4] need total
+  void* scan_tmp = nullptr;
+};
+constexpr int kLongRow = 512;
+// Validate and apply a batch.  Returns after enqueueing; errors land in *err.
+void graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, int64_t* host_scalars,
+                       cudaStream_t s);
+void graph_refresh_derived(Csr& g, GraphWork& w, int64_t n_rows, cudaStream_t s);
+
+// spmm.cu
+// Y[r0:r1) = (M X)[r0:r1) for rows r0..r1, w columns; when col_lo > 0 only
+// neighbours with id >= col_lo contribute, X is indexed by (id - col_lo), and
+// the diagonal term applies only to rows >= col_lo (the new-node block E).
+void spmm_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+              const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+              cudaStream_t s);
+void spmm_f32(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+              const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+              cudaStream_t s);
+
+// dense.cu
+// C (a x b, row-major, ldc) = X^T Y over rows [0,n) with X (n x a, ldx), Y (n x b, ldy).
+// part must hold parts(n,a,b) * a * b doubles.
+int64_t gram_parts(int64_t n, int a, int b);
+void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
+              double* C, int64_t ldc, double* part, bool symmetric, cudaStream_t s);
+// Out (n x c, ldo) = beta * Cin (n x c, ldc) + alpha * X (n x a, ldx) * B (a x c, row-major ldb).
+void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B,
+                 int64_t ldb, double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo,
+                 cudaStream_t s);
+// Pivoted Cholesky with drop tolerance on G (c x c, row-major, ldg; overwritten).
+// Produces T (c x c row-major, ldt; columns >= rank zero) with V T orthonormal,
+// rank and pivot statistics in info[0..3] (rank, kept_min, dropped_max, status).
+void pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                   double* T, int64_t ldt, double* info, cudaStream_t s);
+void symmetrize(double* H, int64_t ld, int m, cudaStream_t s);
+void fill_f64(double* p, double v, int64_t n, cudaStream_t s);
+void copy_cols_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
+void zero_dead_rows(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s);
+void sign_normalize(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s);
+void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,
+                    double* part, double* out, cudaStream_t s);
+
+// eig.cu
+// Symmetric eigensolver for H (m x m row-major, ld; overwritten).  Writes the
+// k leading pairs in tracking order: theta[k], F (m x k row-major, ldf), all m
+// eigenvalues in tracking order to ritz[m], boundary gap to info[0].
+void sym_eig_select(double* H, int64_t ld, int m, int k, int op_order, double* theta, double* F, int64_t ldf,
+                    double* ritz, double* info, double* work, cudaStream_t s);
+size_t eig_work_doubles(int mmax);
+
+// rsvd.cu
+// Omega (S x q, row-major ld) from Philox4x64-10 + Box-Muller at step t.
+void gaussian_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s);
+
+}  // namespace grest

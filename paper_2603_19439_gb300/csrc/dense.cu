@@ -1,0 +1,461 @@
+// Dense FP64 kernels of the G-REST step on tall-skinny row-major blocks:
+//   gram_f64      C = X^T Y (projections C = X_bar^T Y1, Gram matrices of the
+//                 CholQR2 passes, H = Z^T (M Z) of Alg. 1)
+//   gemm_nn_f64   Out = beta Cin + alpha X B (P_perp updates, V T, lift Z F_K)
+//   pchol_inverse pivoted Cholesky with a drop tolerance and the triangular
+//                 inverse, giving T with (V T)^T (V T) = I on the kept columns
+// plus small helpers (sign normalization, residual norms).
+//
+// The Gram is split over row chunks; each CTA writes a partial tile and a
+// second kernel sums the partials in a fixed order (deterministic results).
+// FP64 on GB300 runs on the CUDA-core DFMA pipe (about 1.2 TFLOP/s measured
+// for the whole GPU); 4x4 register tiles keep it the bound.
+#include "common.cuh"
+
+namespace grest {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 32;  // CTA tile (outputs) and row slab
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// partial Gram of one (ta, tb) tile over rows [rbeg, rend)
+__global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ X, int64_t ldx, int a,
+                                                   const double* __restrict__ Y, int64_t ldy, int b, int64_t n,
+                                                   int64_t rows_per_chunk, bool upper, double* __restrict__ part) {
+  __shared__ double Xs[TK][TM + 1];
+  __shared__ double Ys[TK][TN + 1];
+  // tile (ta, tb) from the block index; upper-triangular enumeration when symmetric
+  const int ntb = (b + TN - 1) / TN;
+  int bid = blockIdx.x, ta = 0, tb;
+  if (!upper) {
+    ta = bid / ntb;
+    tb = bid % ntb;
+  } else {
+    while (bid >= ntb - ta) { bid -= ntb - ta; ++ta; }
+    tb = ta + bid;
+  }
+  const int i0 = ta * TM, j0 = tb * TN;
+  const int64_t chunk = blockIdx.y;
+  const int64_t rbeg = chunk * rows_per_chunk;
+  int64_t rend = rbeg + rows_per_chunk;
+  if (rend > n) rend = n;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+  double acc[4][4] = {};
+  for (int64_t r0 = rbeg; r0 < rend; r0 += TK) {
+    for (int e = threadIdx.x; e < TK * TM; e += 256) {
+      int rr = e / TM, cc = e % TM;
+      int64_t r = r0 + rr;
+      Xs[rr][cc] = (r < rend && i0 + cc < a) ? X[r * ldx + i0 + cc] : 0.0;
+      Ys[rr][cc] = (r < rend && j0 + cc < b) ? Y[r * ldy + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < TK; ++k) {
+      double xa[4], yb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = Xs[k][ty * 4 + u];
+        yb[u] = Ys[k][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double* P = part + chunk * (int64_t)a * b;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < a && j < b) P[(int64_t)i * b + j] = acc[u][v];
+    }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int64_t chunks, int a, int b, double* C, int64_t ldc,
+                              bool symmetric) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a * b) return;
+  int i = (int)(e / b), j = (int)(e % b);
+  int si = i, sj = j;
+  if (symmetric && (i / TM) > (j / TN)) { si = j; sj = i; }  // only upper tiles were computed
+  double s = 0.0;
+  for (int64_t c = 0; c < chunks; ++c) s += part[c * (int64_t)a * b + (int64_t)si * b + sj];
+  C[(int64_t)i * ldc + j] = s;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_nn(int64_t n, int a, int c, double alpha, const double* __restrict__ X,
+                                                 int64_t ldx, const double* __restrict__ B, int64_t ldb, double beta,
+                                                 const double* Cin, int64_t ldc, double* Out, int64_t ldo) {
+  __shared__ double Xs[TM][TK + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int64_t r0 = blockIdx.x * (int64_t)TM;
+  const int j0 = blockIdx.y * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < a; k0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int rr = e / TK, kk = e % TK;
+      int64_t r = r0 + rr;
+      Xs[rr][kk] = (r < n && k0 + kk < a) ? X[r * ldx + k0 + kk] : 0.0;
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int kk = e / TN, cc = e % TN;
+      Bs[kk][cc] = (k0 + kk < a && j0 + cc < c) ? B[(int64_t)(k0 + kk) * ldb + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < TK; ++k) {
+      double xa[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = Xs[ty * 4 + u][k];
+        bb[u] = Bs[k][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], bb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t r = r0 + ty * 4 + u;
+    if (r >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int j = j0 + tx * 4 + v;
+      if (j >= c) continue;
+      double y = alpha * acc[u][v];
+      if (beta != 0.0) y += beta * Cin[r * ldc + j];
+      Out[r * ldo + j] = y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pivoted Cholesky
+// One CTA.  G (c x c) is overwritten: after step k, row k holds row k of R
+// (in pivot order) and the trailing block holds the Schur complement.  A
+// column is dropped when its pivot R_kk <= drop_tol * max(R_00, abs_ref)
+// (R_00 is the largest column norm, abs_ref a magnitude of the operator); the
+// loop stops there, so the kept rank is k.
+__global__ void __launch_bounds__(1024) k_pchol(double* G, int64_t ld, int c, double drop_tol, double abs_ref,
+                                                const double* abs_ref_ptr, double* T, int64_t ldt, double* info) {
+  extern __shared__ int perm[];  // c entries
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ double ref, rkk;
+  __shared__ int piv, rank_s, stop;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < c; i += nth) perm[i] = i;
+  if (tid == 0) { rank_s = c; stop = 0; ref = 0.0; }
+  __syncthreads();
+  double kept_min = 1.0, dropped_max = 0.0;
+  for (int k = 0; k < c; ++k) {
+    // pivot: largest remaining diagonal (lowest index on ties)
+    double bv = -1.0;
+    int bi = c;
+    for (int i = k + tid; i < c; i += nth) {
+      double d = G[(int64_t)i * ld + i];
+      if (d > bv || (d == bv && i < bi)) { bv = d; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { sval[wid] = bv; sidx[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = sval[0];
+      int idx = sidx[0];
+      for (int w = 1; w < (nth + 31) / 32; ++w)
+        if (sval[w] > v || (sval[w] == v && sidx[w] < idx)) { v = sval[w]; idx = sidx[w]; }
+      if (k == 0) {
+        // drop reference: max(R_00, |theta_1|)^2 where |theta_1| ~ ||M||_2 (abs_ref_ptr)
+        double a = abs_ref_ptr ? fabs(*abs_ref_ptr) : abs_ref;
+        ref = fmax(v, a * a);
+      }
+      if (!(v > 0.0) || !(v > drop_tol * drop_tol * ref) || !isfinite(v)) {
+        stop = 1;
+        rank_s = k;
+      }
+      piv = idx;
+      rkk = sqrt(v > 0.0 ? v : 0.0);
+    }
+    __syncthreads();
+    if (stop) {
+      double v = piv < c ? G[(int64_t)piv * ld + piv] : 0.0;
+      dropped_max = (ref > 0.0 && v > 0.0) ? sqrt(v / ref) : 0.0;
+      break;
+    }
+    const int p = piv;
+    // symmetric swap of rows/columns k and p
+    if (p != k) {
+      for (int j = tid; j < c; j += nth) {
+        double t = G[(int64_t)k * ld + j];
+        G[(int64_t)k * ld + j] = G[(int64_t)p * ld + j];
+        G[(int64_t)p * ld + j] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < c; i += nth) {
+        double t = G[(int64_t)i * ld + k];
+        G[(int64_t)i * ld + k] = G[(int64_t)i * ld + p];
+        G[(int64_t)i * ld + p] = t;
+      }
+      if (tid == 0) { int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+      __syncthreads();
+    }
+    const double r = rkk;
+    kept_min = ref > 0.0 ? r / sqrt(ref) : 0.0;
+    // row k of R
+    for (int j = k + 1 + tid; j < c; j += nth) G[(int64_t)k * ld + j] /= r;
+    __syncthreads();
+    if (tid == 0) G[(int64_t)k * ld + k] = r;
+    // trailing update of the upper triangle (and mirror for the diagonal scan)
+    const int m = c - k - 1;
+    for (int64_t e = tid; e < (int64_t)m * m; e += nth) {
+      int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      if (j < i) continue;
+      double v = G[(int64_t)i * ld + j] - G[(int64_t)k * ld + i] * G[(int64_t)k * ld + j];
+      G[(int64_t)i * ld + j] = v;
+      G[(int64_t)j * ld + i] = v;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rk = rank_s;
+  // T = P R^-1 (c x c, zero columns >= rk): thread j solves R x = e_j
+  for (int64_t e = tid; e < (int64_t)c * c; e += nth) T[(e / c) * ldt + (e % c)] = 0.0;
+  __syncthreads();
+  for (int j = tid; j < rk; j += nth) {
+    // x_j = 1/R_jj, x_i = -(sum_{l=i+1..j} R_il x_l) / R_ii
+    T[(int64_t)perm[j] * ldt + j] = 1.0 / G[(int64_t)j * ld + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1; l <= j; ++l) s = fma(G[(int64_t)i * ld + l], T[(int64_t)perm[l] * ldt + j], s);
+      T[(int64_t)perm[i] * ldt + j] = -s / G[(int64_t)i * ld + i];
+    }
+  }
+  if (tid == 0) {
+    info[0] = rk;
+    info[1] = rk > 0 ? kept_min : 0.0;
+    info[2] = dropped_max;
+    info[3] = 0.0;
+  }
+}
+
+__global__ void k_symmetrize(double* H, int64_t ld, int m) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  int i = (int)(e / m), j = (int)(e % m);
+  if (j <= i) return;
+  double v = 0.5 * (H[(int64_t)i * ld + j] + H[(int64_t)j * ld + i]);
+  H[(int64_t)i * ld + j] = v;
+  H[(int64_t)j * ld + i] = v;
+}
+
+__global__ void k_fill(double* p, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_copy_cols(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / w;
+    int c = (int)(e % w);
+    dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+__global__ void k_zero_dead(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / w;
+    if (!live[r]) X[r * ldx + (e % w)] = 0.0;
+  }
+}
+
+// per column: the entry of largest magnitude, lowest index on ties
+__global__ void k_argmax_part(const double* X, int64_t ldx, int w, int64_t n, int64_t rows_per_block, double* part,
+                              int64_t* ipart) {
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  const int64_t rb = blockIdx.x * rows_per_block;
+  int64_t re = rb + rows_per_block;
+  if (re > n) re = n;
+  for (int c = 0; c < w; ++c) {
+    double bv = -1.0;
+    int64_t bi = INT64_MAX;
+    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+      double v = fabs(X[r * ldx + c]);
+      if (v > bv) { bv = v; bi = r; }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        double ov = sv[threadIdx.x + o];
+        int64_t oi = si[threadIdx.x + o];
+        if (ov > sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+          sv[threadIdx.x] = ov;
+          si[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[(int64_t)blockIdx.x * w + c] = sv[0];
+      ipart[(int64_t)blockIdx.x * w + c] = si[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_argmax_final(const double* X, int64_t ldx, int w, int64_t nb, const double* part,
+                               const int64_t* ipart, double* sign) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= w) return;
+  double bv = -1.0;
+  int64_t bi = INT64_MAX;
+  for (int64_t b = 0; b < nb; ++b) {
+    double v = part[b * w + c];
+    int64_t i = ipart[b * w + c];
+    if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+  }
+  sign[c] = (bi != INT64_MAX && X[bi * ldx + c] < 0.0) ? -1.0 : 1.0;
+}
+
+__global__ void k_scale_cols(double* X, int64_t ldx, int w, int64_t n, const double* sign) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / w;
+    int c = (int)(e % w);
+    X[r * ldx + c] *= sign[c];
+  }
+}
+
+__global__ void k_resid_part(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,
+                             int64_t rows_per_block, double* part) {
+  __shared__ double red[256];
+  const int64_t rb = blockIdx.x * rows_per_block;
+  int64_t re = rb + rows_per_block;
+  if (re > n) re = n;
+  for (int c = 0; c < w; ++c) {
+    double s = 0.0;
+    const double th = theta[c];
+    for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
+      double d = MX[r * ld + c] - th * X[r * ld + c];
+      s = fma(d, d, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * w + c] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_resid_final(const double* part, int64_t nb, int w, double* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= w) return;
+  double s = 0.0;
+  for (int64_t b = 0; b < nb; ++b) s += part[b * w + c];
+  out[c] = sqrt(s);
+}
+
+int64_t gram_chunks(int64_t n, int ntiles) {
+  int64_t target = (152 * 4 + ntiles - 1) / ntiles;
+  int64_t maxc = cdiv(n, 256);
+  if (target > maxc) target = maxc;
+  if (target < 1) target = 1;
+  return target;
+}
+
+}  // namespace
+
+int64_t gram_parts(int64_t n, int a, int b) {
+  int nt = (int)(cdiv(a, TM) * cdiv(b, TN));
+  return gram_chunks(n, nt);
+}
+
+void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
+              int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
+  if (a <= 0 || b <= 0) return;
+  if (n <= 0) {
+    for (int i = 0; i < a; ++i) cudaMemsetAsync(C + (int64_t)i * ldc, 0, sizeof(double) * b, s);
+    return;
+  }
+  symmetric = symmetric && (X == Y) && (a == b) && (ldx == ldy);
+  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
+  const int nt = symmetric ? nta * (nta + 1) / 2 : nta * ntb;
+  int64_t chunks = gram_chunks(n, nta * ntb);
+  int64_t rpc = cdiv(n, chunks);
+  chunks = cdiv(n, rpc);
+  dim3 grid((unsigned)nt, (unsigned)chunks);
+  k_gram_part<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, symmetric, part);
+  int64_t tot = (int64_t)a * b;
+  k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric);
+}
+
+void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B, int64_t ldb,
+                 double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo, cudaStream_t s) {
+  if (n <= 0 || c <= 0) return;
+  dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
+  k_gemm_nn<<<grid, 256, 0, s>>>(n, a, c, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo);
+}
+
+void pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                   double* T, int64_t ldt, double* info, cudaStream_t s) {
+  k_pchol<<<1, 1024, sizeof(int) * (c + 1), s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
+}
+
+void symmetrize(double* H, int64_t ld, int m, cudaStream_t s) {
+  int64_t t = (int64_t)m * m;
+  k_symmetrize<<<(unsigned)cdiv(t, 256), 256, 0, s>>>(H, ld, m);
+}
+
+void fill_f64(double* p, double v, int64_t n, cudaStream_t s) {
+  if (n > 0) k_fill<<<(unsigned)(cdiv(n, 256) < 4096 ? cdiv(n, 256) : 4096), 256, 0, s>>>(p, v, n);
+}
+
+void copy_cols_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s) {
+  int64_t t = n * w;
+  if (t > 0) k_copy_cols<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(src, lds, dst, ldd, n, w);
+}
+
+void zero_dead_rows(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s) {
+  int64_t t = n * w;
+  if (t > 0) k_zero_dead<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, live, n);
+}
+
+void sign_normalize(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s) {
+  if (n <= 0 || w <= 0) return;
+  int64_t nb = 304;
+  int64_t rpb = cdiv(n, nb);
+  nb = cdiv(n, rpb);
+  k_argmax_part<<<(unsigned)nb, 256, 0, s>>>(X, ldx, w, n, rpb, part, ipart);
+  double* sign = part + nb * w;
+  k_argmax_final<<<(unsigned)cdiv(w, 64), 64, 0, s>>>(X, ldx, w, nb, part, ipart, sign);
+  int64_t t = n * w;
+  k_scale_cols<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, n, sign);
+}
+
+void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,
+                    double* part, double* out, cudaStream_t s) {
+  if (n <= 0 || w <= 0) return;
+  int64_t nb = 304;
+  int64_t rpb = cdiv(n, nb);
+  nb = cdiv(n, rpb);
+  k_resid_part<<<(unsigned)nb, 256, 0, s>>>(MX, X, ld, w, theta, n, rpb, part);
+  k_resid_final<<<(unsigned)cdiv(w, 64), 64, 0, s>>>(part, nb, w, out);
+}
+
+}  // namespace grest

@@ -1,0 +1,767 @@
+// libgrest: context, the G-REST step orchestration (Alg. 2), and the C ABI
+// declared in include/grest.h.
+//
+// One update, FP64 path (all on the context's stream):
+//   A1  validate + apply Delta to the slack CSR           graph.cu
+//   A2  X_bar = [X; 0] (Alg. 2 pad)                       copy / zero
+//   A3  Y1 = M X_bar                                      spmm.cu
+//   A4  C = X_bar^T Y1, W = P_perp Y1 (two passes)        dense.cu
+//   A5  new-node block: B = P_perp Delta_2 (S <= L+P) or
+//       the RSVD basis R of steps S.1-S.4 (Sec. 3.5)      rsvd.cu, spmm.cu, dense.cu, eig.cu
+//   A6  Q = orth(P_perp [W, B]) by CholQR2 with pivoting  dense.cu
+//   A7  MQ = M Q                                          spmm.cu
+//   A8  H = Z^T (M Z), Z = [X_bar, Q] (Eq. main2)         dense.cu
+//   A9  leading K eigenpairs of H (Alg. 1)                eig.cu
+//   A10 X = Z F_K, sign normalization                     dense.cu
+// Rank decisions (kept columns) are read back to the host at three points
+// so that later launches use the exact widths.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace grest;
+
+namespace {
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct grest_ctx {
+  grest_config cfg{};
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  Csr g;
+  GraphWork gw;
+  int K = 0, q = 0, Lr = 0, cmax = 0, mmax = 0;
+  int64_t ldu = 0, ldz = 0, ldq = 0, ldv = 0;
+  int64_t step = 0;
+  int Ku = 0;            // columns of X currently valid (K unless nodes were removed)
+  double* U = nullptr;   // n_cap x ldu
+  double* Un = nullptr;  // next U
+  double* theta = nullptr;
+  double* Z = nullptr;   // n_cap x ldz : [X_bar | W | B/R] -> [X_bar | Q]
+  double* MZ = nullptr;  // n_cap x ldz : [Y1 | MQ]
+  double* V2 = nullptr;  // n_cap x ldv : CholQR staging
+  double* Yr = nullptr;  // n_cap x ldq : RSVD sketch / basis
+  double* Yr2 = nullptr; // n_cap x ldq
+  double* Om = nullptr;  // S_cap x ldq
+  double* EtM = nullptr; // S_cap x ldq : rows N.. of M M_rs, then B_s^T
+  int64_t S_cap = 0;
+  double* Id = nullptr;  // q x q identity (exact new-node block)
+  double *Cm = nullptr, *Cv = nullptr, *G = nullptr, *T = nullptr, *H = nullptr, *F = nullptr, *XtM = nullptr,
+         *Gs = nullptr, *Uh = nullptr, *ritz = nullptr, *th_new = nullptr, *tmpk = nullptr;
+  double* info = nullptr;  // device diagnostics [64]
+  double* resn = nullptr;  // residual norms [64]
+  double* part = nullptr;
+  int64_t part_cap = 0;
+  int64_t* ipart = nullptr;
+  double* eigwork = nullptr;
+  int32_t* err = nullptr;
+  // batch staging
+  int32_t *b_iu = nullptr, *b_iv = nullptr, *b_du = nullptr, *b_dv = nullptr, *b_dn = nullptr;
+  double* b_w = nullptr;
+  int64_t b_cap = 0, b_dn_cap = 0;
+  // host mirrors
+  double* h_info = nullptr;  // pinned [64]
+  int32_t* h_err = nullptr;  // pinned
+  int64_t* h_scal = nullptr; // pinned [8]
+  grest_stats stats{};
+  std::vector<double> last_ritz;
+  int last_m = 0;
+  cudaEvent_t ev[10];
+};
+
+namespace {
+
+grest_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return GREST_OK;
+  if (e == cudaErrorMemoryAllocation) return GREST_ERR_OOM;
+  return GREST_ERR_CUDA;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return from_cuda(e_); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+grest_status map_dev_err(int32_t e) {
+  switch (e) {
+    case DERR_NONE: return GREST_OK;
+    case DERR_CAPACITY: return GREST_ERR_CAPACITY;
+    case DERR_NUMERIC: return GREST_ERR_NUMERIC;
+    default: return GREST_ERR_INVALID_UPDATE;
+  }
+}
+
+void free_ctx(grest_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->g.row_off, c->g.row_len, c->g.row_cap, c->g.col, c->g.val, c->g.live, c->g.deg, c->g.dis,
+                  c->g.arena_top, c->g.dmax, c->gw.cnt, c->gw.seg, c->gw.cursor, c->gw.delflag, c->gw.rowflag,
+                  c->gw.touched, c->gw.tmp_off, c->gw.need, c->gw.new_len, c->gw.ekey, c->gw.erow, c->gw.ew,
+                  c->gw.eins, c->gw.tmp_col, c->gw.tmp_val, c->gw.long_rows, c->gw.scalars, c->gw.scan_tmp,
+                  c->U, c->Un, c->theta, c->Z, c->MZ, c->V2, c->Yr, c->Yr2, c->Om, c->EtM, c->Id, c->Cm, c->Cv,
+                  c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
+                  c->ipart, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_info) cudaFreeHost(c->h_info);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+grest_status ensure_batch(grest_ctx* c, int64_t n_edges, int64_t n_dn) {
+  if (n_edges > c->b_cap) {
+    int64_t cap = std::max<int64_t>(n_edges, 2 * c->b_cap);
+    cudaFree(c->b_iu); cudaFree(c->b_iv); cudaFree(c->b_du); cudaFree(c->b_dv); cudaFree(c->b_w);
+    c->b_iu = c->b_iv = c->b_du = c->b_dv = nullptr;
+    c->b_w = nullptr;
+    CK(dalloc(&c->b_iu, cap)); CK(dalloc(&c->b_iv, cap)); CK(dalloc(&c->b_du, cap)); CK(dalloc(&c->b_dv, cap));
+    CK(dalloc(&c->b_w, cap));
+    c->b_cap = cap;
+  }
+  if (n_dn > c->b_dn_cap) {
+    int64_t cap = std::max<int64_t>(n_dn, 2 * c->b_dn_cap);
+    cudaFree(c->b_dn);
+    c->b_dn = nullptr;
+    CK(dalloc(&c->b_dn, cap));
+    c->b_dn_cap = cap;
+  }
+  return GREST_OK;
+}
+
+grest_status ensure_graph_work(grest_ctx* c, int64_t entries) {
+  GraphWork& w = c->gw;
+  if (entries > w.ent_cap) {
+    int64_t cap = std::max<int64_t>(entries, 2 * w.ent_cap);
+    cudaFree(w.ekey); cudaFree(w.ew); cudaFree(w.eins);
+    w.ekey = nullptr; w.ew = nullptr; w.eins = nullptr;
+    CK(dalloc(&w.ekey, cap)); CK(dalloc(&w.ew, cap)); CK(dalloc(&w.eins, cap));
+    w.ent_cap = cap;
+  }
+  int64_t tneed = c->g.nnz_cap + w.ent_cap;
+  if (tneed > w.tmp_cap) {
+    cudaFree(w.tmp_col); cudaFree(w.tmp_val);
+    w.tmp_col = nullptr; w.tmp_val = nullptr;
+    CK(dalloc(&w.tmp_col, tneed));
+    if (c->g.val) CK(dalloc(&w.tmp_val, tneed));
+    w.tmp_cap = tneed;
+  }
+  return GREST_OK;
+}
+
+grest_status ensure_S(grest_ctx* c, int64_t S) {
+  if (S <= c->S_cap) return GREST_OK;
+  int64_t cap = std::max<int64_t>(S, 2 * c->S_cap);
+  cudaFree(c->Om); cudaFree(c->EtM);
+  c->Om = c->EtM = nullptr;
+  CK(dalloc(&c->Om, cap * c->ldq));
+  CK(dalloc(&c->EtM, cap * c->ldq));
+  c->S_cap = cap;
+  return GREST_OK;
+}
+
+grest_status read_back(grest_ctx* c, int n_info) {
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  if (n_info > 0) CK(cudaMemcpyAsync(c->h_info, c->info, sizeof(double) * n_info, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GREST_OK;
+}
+
+OpParams op_params(const grest_ctx* c) {
+  OpParams p;
+  p.op = c->cfg.op;
+  p.deg = c->g.deg;
+  p.dis = c->g.dis;
+  p.dmax = c->g.dmax;
+  p.live = c->g.live;
+  return p;
+}
+
+void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
+          int64_t col_lo) {
+  spmm_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+}
+
+void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
+          double* C, int64_t ldc, bool sym) {
+  gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+}
+
+// X (n x w) <- P_perp X = X - U (U^T X), U = first ku columns of Z
+void project_out(grest_ctx* c, double* X, int64_t ldx, int w, int64_t n) {
+  if (c->Ku == 0 || w == 0) return;
+  gram(c, c->Z, c->ldz, c->Ku, X, ldx, w, n, c->Cv, w, false);
+  gemm_nn_f64(n, c->Ku, w, -1.0, c->Z, c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx, c->stream);
+}
+
+// CholQR with pivoting: Out (n x rank) = X (n x w) T; returns rank via info slot
+grest_status cholqr_pass(grest_ctx* c, const double* X, int64_t ldx, int w, int64_t n, double tol, double abs_ref,
+                         const double* abs_ref_ptr, double* Out, int64_t ldo, int info_slot, bool read_rank,
+                         int* rank_out) {
+  gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
+  pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->info + info_slot, c->stream);
+  int rank = w;
+  if (read_rank) {
+    grest_status st = read_back(c, info_slot + 4);
+    if (st != GREST_OK) return st;
+    rank = (int)c->h_info[info_slot];
+  }
+  if (rank > 0) gemm_nn_f64(n, w, rank, 1.0, X, ldx, c->T, w, 0.0, nullptr, 0, Out, ldo, c->stream);
+  if (rank_out) *rank_out = rank;
+  return GREST_OK;
+}
+
+__global__ void k_fill_identity(double* I, int64_t ld, int q) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < (int64_t)q * q) I[(e / q) * ld + (e % q)] = (e / q == e % q) ? 1.0 : 0.0;
+}
+
+__global__ void k_pad_copy(const double* U, int64_t ldu, double* Z, int64_t ldz, int64_t N, int64_t N2, int K) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N2 * K; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / K;
+    int c = (int)(e % K);
+    Z[r * ldz + c] = r < N ? U[r * ldu + c] : 0.0;
+  }
+}
+
+__global__ void k_sum_removed_degree(const int32_t* dn, int64_t n_dn, const int64_t N, const int32_t* row_len,
+                                     int64_t* out) {
+  int64_t s = 0;
+  for (int64_t i = threadIdx.x; i < n_dn; i += blockDim.x) {
+    int32_t d = dn[i];
+    if (d >= 0 && d < N) s += row_len[d];
+  }
+  __shared__ int64_t red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_orth_err(const double* G, int64_t ld, int k, double* out) {
+  double m = 0.0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    m = fmax(m, fabs(G[(int64_t)i * ld + j] - (i == j ? 1.0 : 0.0)));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_resid_vecs(const double* MU, const double* U, int64_t ld, int k, const double* theta, int64_t n,
+                             double* R, int64_t ldr) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / k;
+    int c = (int)(e % k);
+    R[r * ldr + c] = MU[r * ld + c] - theta[c] * U[r * ld + c];
+  }
+}
+
+__global__ void k_maxabs(const double* A, int64_t ld, int rows, int cols, double* out) {
+  double m = 0.0;
+  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) m = fmax(m, fabs(A[(int64_t)(e / cols) * ld + e % cols]));
+  __shared__ double red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, bool removed) {
+  const int64_t N2 = N + S;
+  cudaStream_t s = c->stream;
+  const int K = c->K;
+  Csr& g = c->g;
+  CK(cudaEventRecord(c->ev[1], s));
+  // A2: X_bar = [X; 0]; removed nodes: zero their rows and re-orthonormalize (reading of node removal)
+  k_pad_copy<<<1024, 256, 0, s>>>(c->U, c->ldu, c->Z, c->ldz, N, N2, c->Ku);
+  if (removed) {
+    zero_dead_rows(c->Z, c->ldz, c->Ku, g.live, N2, s);
+    int r1 = 0;
+    grest_status st = cholqr_pass(c, c->Z, c->ldz, c->Ku, N2, c->cfg.drop_tol, 1.0, nullptr, c->V2, c->ldv, 0, true, &r1);
+    if (st != GREST_OK) return st;
+    int r2 = 0;
+    st = cholqr_pass(c, c->V2, c->ldv, r1, N2, 1e-14, 0.0, nullptr, c->Z, c->ldz, 4, false, &r2);
+    if (st != GREST_OK) return st;
+    c->Ku = r1;
+  }
+  const int Ku = c->Ku;
+  // A3: Y1 = M X_bar
+  spmm(c, c->Z, c->ldz, c->MZ, c->ldz, Ku, 0, N2, 0);
+  CK(cudaEventRecord(c->ev[2], s));
+  // A4: C = X_bar^T Y1; W = Y1 - X_bar C, re-projected once
+  double* W = c->Z + Ku;
+  gram(c, c->Z, c->ldz, Ku, c->MZ, c->ldz, Ku, N2, c->Cm, Ku, false);
+  gemm_nn_f64(N2, Ku, Ku, -1.0, c->Z, c->ldz, c->Cm, Ku, 1.0, c->MZ, c->ldz, W, c->ldz, s);
+  project_out(c, W, c->ldz, Ku, N2);
+  // A5: new-node block
+  int cb = 0;
+  int mode = 2;
+  double* B = c->Z + 2 * Ku;
+  const int q = c->q;
+  if (S > 0 && c->cfg.subspace != GREST_SUB_GREST2) {
+    bool rsvd = c->cfg.subspace == GREST_SUB_RSVD || (c->cfg.subspace == GREST_SUB_AUTO && S > q);
+    if (!rsvd) {
+      if (S > q) return GREST_ERR_UNSUPPORTED;  // exact block wider than the basis buffers
+      mode = 3;
+      // E = M_new[:, N:N2] = M_new * [0; I_S] (restricted SpMM against the identity)
+      spmm(c, c->Id, c->ldq, B, c->ldz, (int)S, 0, N2, N);
+      project_out(c, B, c->ldz, (int)S, N2);
+      cb = (int)S;
+    } else {
+      mode = 4;
+      grest_status st = ensure_S(c, S);
+      if (st != GREST_OK) return st;
+      // S.1: Y = P_perp Delta_2 Omega
+      gaussian_omega(c->Om, c->ldq, S, q, c->cfg.seed, (uint64_t)c->step, s);
+      spmm(c, c->Om, c->ldq, c->Yr, c->ldq, q, 0, N2, N);
+      project_out(c, c->Yr, c->ldq, q, N2);
+      project_out(c, c->Yr, c->ldq, q, N2);
+      // M = orth(Y): CholQR2 with pivoting
+      int rY = 0;
+      st = cholqr_pass(c, c->Yr, c->ldq, q, N2, c->cfg.drop_tol, 0.0, c->theta, c->Yr2, c->ldq, 8, true, &rY);
+      if (st != GREST_OK) return st;
+      int rY2 = 0;
+      st = cholqr_pass(c, c->Yr2, c->ldq, rY, N2, 1e-14, 0.0, nullptr, c->Yr, c->ldq, 12, false, &rY2);
+      if (st != GREST_OK) return st;
+      c->stats.rank_y = rY;
+      if (rY > 0) {
+        // S.2: B_s^T = Delta_2^T M - (Delta_2^T X_bar)(X_bar^T M), Delta_2^T X_bar = Y1[N:N2]
+        spmm(c, c->Yr, c->ldq, c->EtM, c->ldq, rY, N, N2, 0);
+        gram(c, c->Z, c->ldz, Ku, c->Yr, c->ldq, rY, N2, c->XtM, rY, false);
+        gemm_nn_f64(S, Ku, rY, -1.0, c->MZ + N * c->ldz, c->ldz, c->XtM, rY, 1.0, c->EtM, c->ldq, c->EtM, c->ldq, s);
+        // left singular vectors of B_s via eig(B_s B_s^T), L leading
+        gram(c, c->EtM, c->ldq, rY, c->EtM, c->ldq, rY, S, c->Gs, rY, true);
+        const int Lp = std::min(c->Lr, rY);
+        sym_eig_select(c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16, c->eigwork, s);
+        // S.4: R = M U_hat
+        gemm_nn_f64(N2, rY, Lp, 1.0, c->Yr, c->ldq, c->Uh, Lp, 0.0, nullptr, 0, B, c->ldz, s);
+        cb = Lp;
+      }
+    }
+  }
+  CK(cudaEventRecord(c->ev[3], s));
+  // A6: Q = orth(P_perp [W, B]) by CholQR2 with pivoting (partial orthogonality: X_bar is fixed)
+  int cw = Ku + cb;
+  double* V = c->Z + Ku;
+  project_out(c, V, c->ldz, cw, N2);
+  int r = 0;
+  grest_status st = cholqr_pass(c, V, c->ldz, cw, N2, c->cfg.drop_tol, 0.0, c->theta, c->V2, c->ldv, 20, true, &r);
+  if (st != GREST_OK) return st;
+  c->stats.pivot_kept_min = c->h_info[21];
+  c->stats.pivot_dropped_max = c->h_info[22];
+  if (r > 0) {
+    project_out(c, c->V2, c->ldv, r, N2);
+    int r2 = 0;
+    st = cholqr_pass(c, c->V2, c->ldv, r, N2, 1e-14, 0.0, nullptr, V, c->ldz, 24, false, &r2);
+    if (st != GREST_OK) return st;
+  }
+  const int m = Ku + r;
+  if (m < K) return GREST_ERR_NUMERIC;
+  // A7: MQ = M Q
+  if (r > 0) spmm(c, V, c->ldz, c->MZ + Ku, c->ldz, r, 0, N2, 0);
+  CK(cudaEventRecord(c->ev[4], s));
+  // A8: H = Z^T (M Z) (Eq. main2), symmetrized
+  gram(c, c->Z, c->ldz, m, c->MZ, c->ldz, m, N2, c->H, m, false);
+  symmetrize(c->H, m, m, s);
+  CK(cudaEventRecord(c->ev[5], s));
+  // A9: leading K eigenpairs of H (Alg. 1)
+  sym_eig_select(c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, c->eigwork, s);
+  CK(cudaEventRecord(c->ev[6], s));
+  // A10: X = Z F_K, sign normalization
+  gemm_nn_f64(N2, m, K, 1.0, c->Z, c->ldz, c->F, K, 0.0, nullptr, 0, c->Un, c->ldu, s);
+  sign_normalize(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
+  CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+  std::swap(c->U, c->Un);
+  c->Ku = K;
+  CK(cudaEventRecord(c->ev[7], s));
+  c->stats.m = m;
+  c->stats.k_u = Ku;
+  c->stats.rank_q = r;
+  c->stats.mode = mode;
+  c->last_m = m;
+  return GREST_OK;
+}
+
+grest_status run_checks(grest_ctx* c, int64_t n) {
+  // M U, residual norms, orthonormality and Galerkin residual, in FP64
+  cudaStream_t s = c->stream;
+  const int K = c->K;
+  double* MU = c->Un;  // free after the swap; same leading dimension as U
+  spmm(c, c->U, c->ldu, MU, c->ldu, K, 0, n, 0);
+  residual_norms(MU, c->U, c->ldu, K, c->theta, n, c->part, c->resn, s);
+  gram(c, c->U, c->ldu, K, c->U, c->ldu, K, n, c->Cm, K, true);
+  k_orth_err<<<1, 256, 0, s>>>(c->Cm, K, K, c->info + 36);
+  // R = MU - U theta (ldv >= K), Galerkin residual Z^T R
+  double* R = c->V2;
+  k_resid_vecs<<<1024, 256, 0, s>>>(MU, c->U, c->ldu, K, c->theta, n, R, c->ldv);
+  gram(c, c->Z, c->ldz, c->last_m, R, c->ldv, K, n, c->H, K, false);
+  k_maxabs<<<1, 256, 0, s>>>(c->H, K, c->last_m, K, c->info + 37);
+  return GREST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grest_status grest_config_default(grest_config* cfg, int32_t k) {
+  if (!cfg) return GREST_ERR_INVALID_ARG;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->op = GREST_OP_ADJ;
+  cfg->k = k;
+  cfg->subspace = GREST_SUB_AUTO;
+  cfg->L = 100;
+  cfg->P = 100;
+  cfg->precision = GREST_FP64;
+  cfg->projection = GREST_PROJ_EXACT;
+  cfg->w_block = GREST_WB_RESID;
+  cfg->seed = 0;
+  cfg->drop_tol = 1e-7;
+  return GREST_OK;
+}
+
+const char* grest_status_str(grest_status s) {
+  switch (s) {
+    case GREST_OK: return "ok";
+    case GREST_ERR_INVALID_ARG: return "invalid argument";
+    case GREST_ERR_INVALID_UPDATE: return "invalid update batch";
+    case GREST_ERR_OOM: return "device out of memory";
+    case GREST_ERR_CAPACITY: return "capacity exceeded";
+    case GREST_ERR_NUMERIC: return "numerical breakdown";
+    case GREST_ERR_CUDA: return "CUDA error";
+    case GREST_ERR_TIMEOUT: return "device wait timed out";
+    case GREST_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowptr, const int32_t* col,
+                        const double* val, const double* U0, const double* theta0, void* cuda_stream,
+                        grest_ctx** out) {
+  if (!cfg || !out || n < 1 || !rowptr || (!col && rowptr[n] > 0)) return GREST_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->k < 1 || cfg->k > 64 || cfg->op < 0 || cfg->op > 2 || cfg->L < 1 || cfg->P < 0 || cfg->L + cfg->P > 256 ||
+      cfg->subspace < 0 || cfg->subspace > 3 || !(cfg->drop_tol > 0.0) || cfg->k > n)
+    return GREST_ERR_INVALID_ARG;
+  if (cfg->precision != GREST_FP64 || cfg->projection != GREST_PROJ_EXACT || cfg->w_block != GREST_WB_RESID)
+    return GREST_ERR_UNSUPPORTED;
+  if (!U0 || !theta0) return GREST_ERR_UNSUPPORTED;
+  const int64_t nnz = rowptr[n];
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return GREST_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GREST_ERR_CUDA;
+  grest_ctx* c = new grest_ctx();
+  for (auto& e : c->ev) e = nullptr;
+  c->cfg = *cfg;
+  c->dev = dev;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->K = cfg->k;
+  c->Ku = cfg->k;
+  c->q = cfg->L + cfg->P;
+  c->Lr = cfg->L;
+  c->cmax = cfg->k + std::max(c->q, cfg->L);
+  c->mmax = cfg->k + c->cmax;
+  c->ldu = round_up(c->K, 8);
+  c->ldz = round_up(c->mmax, 8);
+  c->ldq = round_up(c->q, 8);
+  c->ldv = round_up(std::max(c->cmax, c->K), 8);
+  Csr& g = c->g;
+  g.n = n;
+  g.n_cap = cfg->node_capacity > 0 ? cfg->node_capacity : (n + n / 4 + 1024);
+  if (g.n_cap < n) { free_ctx(c); return GREST_ERR_INVALID_ARG; }
+  // host layout with slack: cap = len + len/4 + 4, rows sorted
+  std::vector<int64_t> off(n);
+  std::vector<int32_t> len(n), cap(n);
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    len[i] = (int32_t)(rowptr[i + 1] - rowptr[i]);
+    cap[i] = len[i] + len[i] / 4 + 4;
+    off[i] = total;
+    total += cap[i];
+  }
+  g.nnz_cap = cfg->nnz_capacity > 0 ? cfg->nnz_capacity : (2 * total + (1 << 20));
+  if (g.nnz_cap < total) { free_ctx(c); return GREST_ERR_INVALID_ARG; }
+  std::vector<int32_t> hcol(total, 0);
+  std::vector<double> hval(val ? total : 0, 0.0), hdeg(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<std::pair<int32_t, double>> row;
+    row.reserve(len[i]);
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      int32_t cj = col[j];
+      if (cj < 0 || cj >= n || cj == i) { free_ctx(c); return GREST_ERR_INVALID_ARG; }
+      double w = val ? val[j] : 1.0;
+      if (!(w > 0.0) || w != w) { free_ctx(c); return GREST_ERR_INVALID_ARG; }
+      row.push_back({cj, w});
+    }
+    std::sort(row.begin(), row.end());
+    for (size_t j = 0; j < row.size(); ++j) {
+      if (j > 0 && row[j].first == row[j - 1].first) { free_ctx(c); return GREST_ERR_INVALID_ARG; }
+      hcol[off[i] + j] = row[j].first;
+      if (val) hval[off[i] + j] = row[j].second;
+      hdeg[i] += row[j].second;
+    }
+  }
+  (void)nnz;
+#define IK(x)                            \
+  do {                                   \
+    cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) {             \
+      free_ctx(c);                       \
+      return from_cuda(e_);              \
+    }                                    \
+  } while (0)
+  const int64_t nc = g.n_cap;
+  IK(dalloc(&g.row_off, nc)); IK(dalloc(&g.row_len, nc)); IK(dalloc(&g.row_cap, nc));
+  IK(dalloc(&g.col, g.nnz_cap));
+  if (val) IK(dalloc(&g.val, g.nnz_cap));
+  IK(dalloc(&g.live, nc)); IK(dalloc(&g.deg, nc)); IK(dalloc(&g.dis, nc));
+  IK(dalloc(&g.arena_top, 1)); IK(dalloc(&g.dmax, 1));
+  GraphWork& w = c->gw;
+  IK(dalloc(&w.cnt, nc + 1)); IK(dalloc(&w.seg, nc + 1)); IK(dalloc(&w.cursor, nc)); IK(dalloc(&w.delflag, nc));
+  IK(dalloc(&w.rowflag, nc + 1)); IK(dalloc(&w.touched, nc)); IK(dalloc(&w.tmp_off, nc + 1));
+  IK(dalloc(&w.need, nc + 1)); IK(dalloc(&w.new_len, nc)); IK(dalloc(&w.long_rows, nc));
+  IK(dalloc(&w.scalars, 8));
+  IK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(nc + 1)));
+  {
+    int64_t mb = cfg->max_batch_edges > 0 ? cfg->max_batch_edges : (1 << 20);
+    if (ensure_graph_work(c, 2 * mb) != GREST_OK) { free_ctx(c); return GREST_ERR_OOM; }
+    if (ensure_batch(c, mb, 1024) != GREST_OK) { free_ctx(c); return GREST_ERR_OOM; }
+  }
+  IK(dalloc(&c->U, nc * c->ldu)); IK(dalloc(&c->Un, nc * c->ldu)); IK(dalloc(&c->theta, 64));
+  IK(dalloc(&c->Z, nc * c->ldz)); IK(dalloc(&c->MZ, nc * c->ldz)); IK(dalloc(&c->V2, nc * c->ldv));
+  IK(dalloc(&c->Yr, nc * c->ldq)); IK(dalloc(&c->Yr2, nc * c->ldq));
+  IK(dalloc(&c->Id, (int64_t)c->q * c->ldq));
+  const int cm = c->cmax, mm = c->mmax;
+  IK(dalloc(&c->Cm, 64 * 64)); IK(dalloc(&c->Cv, (int64_t)64 * (cm + 64))); IK(dalloc(&c->G, (int64_t)cm * cm));
+  IK(dalloc(&c->T, (int64_t)cm * cm)); IK(dalloc(&c->H, (int64_t)mm * mm)); IK(dalloc(&c->F, (int64_t)mm * 64));
+  IK(dalloc(&c->XtM, (int64_t)64 * c->ldq)); IK(dalloc(&c->Gs, (int64_t)c->q * c->q));
+  IK(dalloc(&c->Uh, (int64_t)c->q * c->q)); IK(dalloc(&c->ritz, mm)); IK(dalloc(&c->th_new, 64));
+  IK(dalloc(&c->tmpk, 256)); IK(dalloc(&c->info, 64)); IK(dalloc(&c->resn, 64));
+  c->part_cap = 3'200'000;
+  IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));
+  IK(dalloc(&c->eigwork, eig_work_doubles(std::max(mm, c->q))));
+  IK(dalloc(&c->err, 1));
+  IK(cudaMallocHost((void**)&c->h_info, sizeof(double) * 64));
+  IK(cudaMallocHost((void**)&c->h_err, sizeof(int32_t)));
+  IK(cudaMallocHost((void**)&c->h_scal, sizeof(int64_t) * 8));
+  for (auto& e : c->ev) IK(cudaEventCreate(&e));
+  cudaStream_t s = c->stream;
+  // graph upload
+  IK(cudaMemcpyAsync(g.row_off, off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+  IK(cudaMemcpyAsync(g.row_len, len.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  IK(cudaMemcpyAsync(g.row_cap, cap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+  IK(cudaMemcpyAsync(g.col, hcol.data(), sizeof(int32_t) * total, cudaMemcpyHostToDevice, s));
+  if (val) IK(cudaMemcpyAsync(g.val, hval.data(), sizeof(double) * total, cudaMemcpyHostToDevice, s));
+  IK(cudaMemcpyAsync(g.deg, hdeg.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  IK(cudaMemsetAsync(g.live, 0, nc, s));
+  IK(cudaMemsetAsync(g.live, 1, n, s));
+  IK(cudaMemcpyAsync(g.arena_top, &total, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  IK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
+  // initial pairs
+  {
+    std::vector<double> hu((size_t)n * c->ldu, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int j = 0; j < c->K; ++j) hu[(size_t)i * c->ldu + j] = U0[(size_t)i * c->K + j];
+    IK(cudaMemcpyAsync(c->U, hu.data(), sizeof(double) * hu.size(), cudaMemcpyHostToDevice, s));
+    IK(cudaMemcpyAsync(c->theta, theta0, sizeof(double) * c->K, cudaMemcpyHostToDevice, s));
+    IK(cudaStreamSynchronize(s));
+  }
+  k_fill_identity<<<(unsigned)((c->q * c->q + 255) / 256), 256, 0, s>>>(c->Id, c->ldq, c->q);
+  graph_refresh_derived(g, w, n, s);
+  IK(cudaGetLastError());
+  IK(cudaStreamSynchronize(s));
+#undef IK
+  c->stats.n_nodes = n;
+  c->stats.nnz = nnz;
+  *out = c;
+  return GREST_OK;
+}
+
+grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats* stats) {
+  if (!c || !u) return GREST_ERR_INVALID_ARG;
+  if (u->n_new_nodes < 0 || u->n_ins < 0 || u->n_del < 0 || u->n_del_nodes < 0) return GREST_ERR_INVALID_ARG;
+  if ((u->n_ins > 0 && (!u->ins_u || !u->ins_v)) || (u->n_del > 0 && (!u->del_u || !u->del_v)) ||
+      (u->n_del_nodes > 0 && !u->del_nodes))
+    return GREST_ERR_INVALID_ARG;
+  if (u->ins_w && !c->g.val) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.n, S = u->n_new_nodes;
+  if (N + S > c->g.n_cap) return GREST_ERR_CAPACITY;
+  if (N + S > INT32_MAX) return GREST_ERR_CAPACITY;
+  grest_status st = ensure_batch(c, std::max(u->n_ins, u->n_del), u->n_del_nodes);
+  if (st != GREST_OK) return st;
+  CK(cudaEventRecord(c->ev[0], s));
+  const cudaMemcpyKind kind = u->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (u->n_ins > 0) {
+    CK(cudaMemcpyAsync(c->b_iu, u->ins_u, sizeof(int32_t) * u->n_ins, kind, s));
+    CK(cudaMemcpyAsync(c->b_iv, u->ins_v, sizeof(int32_t) * u->n_ins, kind, s));
+    if (u->ins_w) CK(cudaMemcpyAsync(c->b_w, u->ins_w, sizeof(double) * u->n_ins, kind, s));
+  }
+  if (u->n_del > 0) {
+    CK(cudaMemcpyAsync(c->b_du, u->del_u, sizeof(int32_t) * u->n_del, kind, s));
+    CK(cudaMemcpyAsync(c->b_dv, u->del_v, sizeof(int32_t) * u->n_del, kind, s));
+  }
+  if (u->n_del_nodes > 0) CK(cudaMemcpyAsync(c->b_dn, u->del_nodes, sizeof(int32_t) * u->n_del_nodes, kind, s));
+  // entry buffers: both directions of every edit plus the edges of removed nodes
+  int64_t entries = 2 * (u->n_ins + u->n_del);
+  if (u->n_del_nodes > 0) {
+    k_sum_removed_degree<<<1, 256, 0, s>>>(c->b_dn, u->n_del_nodes, N, c->g.row_len, c->gw.scalars + 4);
+    CK(cudaMemcpyAsync(c->h_scal + 4, c->gw.scalars + 4, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    entries += c->h_scal[4];
+  }
+  st = ensure_graph_work(c, entries + 1);
+  if (st != GREST_OK) return st;
+  BatchDev bd;
+  bd.S = S;
+  bd.n_ins = u->n_ins;
+  bd.n_del = u->n_del;
+  bd.n_dn = u->n_del_nodes;
+  bd.ins_u = c->b_iu;
+  bd.ins_v = c->b_iv;
+  bd.ins_w = u->ins_w ? c->b_w : nullptr;
+  bd.del_u = c->b_du;
+  bd.del_v = c->b_dv;
+  bd.dn = c->b_dn;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
+  graph_apply_batch(c->g, c->gw, bd, c->err, nullptr, s);
+  CK(cudaGetLastError());
+  st = read_back(c, 0);
+  if (st != GREST_OK) return st;
+  if (*c->h_err) return map_dev_err(*c->h_err);
+  // committed: the graph now has N + S ids
+  c->g.n = N + S;
+  graph_refresh_derived(c->g, c->gw, N + S, s);
+  c->stats.rank_y = 0;
+  st = fp64_step(c, bd, N, S, u->n_del_nodes > 0);
+  CK(cudaGetLastError());
+  if (st != GREST_OK) return st;
+  ++c->step;
+  if (c->cfg.flags & GREST_FLAG_CHECK) run_checks(c, N + S);
+  CK(cudaMemcpyAsync(c->h_info, c->info, sizeof(double) * 48, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_scal, c->g.arena_top, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  c->last_ritz.resize(c->last_m);
+  CK(cudaMemcpyAsync(c->last_ritz.data(), c->ritz, sizeof(double) * c->last_m, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  grest_stats& S_ = c->stats;
+  S_.step = c->step;
+  S_.n_nodes = c->g.n;
+  S_.boundary_gap = c->h_info[28];
+  if (c->h_info[24] < c->stats.rank_q) return GREST_ERR_NUMERIC;
+  if (c->cfg.flags & GREST_FLAG_CHECK) {
+    double th[64], rn[64];
+    CK(cudaMemcpy(th, c->theta, sizeof(double) * c->K, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rn, c->resn, sizeof(double) * c->K, cudaMemcpyDeviceToHost));
+    double th1 = 0.0, mr = 0.0;
+    for (int j = 0; j < c->K; ++j) {
+      th1 = std::max(th1, std::fabs(th[j]));
+      mr = std::max(mr, rn[j]);
+    }
+    S_.orth_err = c->h_info[36];
+    S_.max_residual = th1 > 0 ? mr / th1 : mr;
+    S_.galerkin = th1 > 0 ? c->h_info[37] / th1 : c->h_info[37];
+  }
+  S_.ms_total = ev_ms(c->ev[0], c->ev[7]);
+  S_.ms_graph = ev_ms(c->ev[0], c->ev[1]);
+  S_.ms_spmm = ev_ms(c->ev[1], c->ev[2]);
+  S_.ms_basis = ev_ms(c->ev[2], c->ev[4]);
+  S_.ms_project = ev_ms(c->ev[4], c->ev[5]);
+  S_.ms_eig = ev_ms(c->ev[5], c->ev[6]);
+  S_.ms_lift = ev_ms(c->ev[6], c->ev[7]);
+  if (stats) *stats = S_;
+  return GREST_OK;
+}
+
+grest_status grest_sync(grest_ctx* c) {
+  if (!c) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+grest_status grest_get_embedding(grest_ctx* c, double* U, double* theta, uint8_t* live, int64_t* n_out,
+                                 int32_t on_device) {
+  if (!c || !n_out) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  const int64_t n = c->g.n;
+  *n_out = n;
+  cudaStream_t s = c->stream;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K, n, kind, s));
+  if (theta) CK(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->K, kind, s));
+  if (live) CK(cudaMemcpyAsync(live, c->g.live, n, kind, s));
+  return from_cuda(cudaStreamSynchronize(s));
+}
+
+grest_status grest_get_ritz_values(grest_ctx* c, double* ritz, int32_t* m_out) {
+  if (!c || !m_out) return GREST_ERR_INVALID_ARG;
+  *m_out = c->last_m;
+  if (ritz) memcpy(ritz, c->last_ritz.data(), sizeof(double) * c->last_m);
+  return GREST_OK;
+}
+
+grest_status grest_get_stats(grest_ctx* c, grest_stats* st) {
+  if (!c || !st) return GREST_ERR_INVALID_ARG;
+  *st = c->stats;
+  return GREST_OK;
+}
+
+grest_status grest_apply_operator(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t w) {
+  if (!c || !X || !Y || w < 1 || w > 288 || ldx < w || ldy < w) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  spmm(c, X, ldx, Y, ldy, w, 0, c->g.n, 0);
+  CK(cudaGetLastError());
+  return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+void grest_destroy(grest_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

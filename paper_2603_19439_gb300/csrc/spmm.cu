@@ -1,0 +1,231 @@
+// CSR SpMM Y = M X over tall-skinny row-major blocks, with the operator of
+// Sec. 4.3 applied in the epilogue:
+//   ADJ   y_r = sum_j a_rj x_j
+//   LAP   y_r = (alpha - d_r) x_r + sum_j a_rj x_j,   alpha = 2 d_max
+//   NLAP  y_r = x_r + s_r sum_j a_rj s_j x_j,          s = d^-1/2
+// Tombstoned rows give zero (principal submatrix on live nodes).
+//
+// Scheduling: one warp per row; the warp loads 32 column indices at a time
+// (coalesced) and broadcasts them by shuffle, then every lane gathers its
+// columns of the neighbour's row (a whole row of X is one contiguous run, so
+// a gather is fully coalesced).  Rows longer than kLongRow (hubs of power-law
+// graphs) go to a second kernel where a block of 8 warps splits the
+// neighbour list and reduces in shared memory in a fixed order, so results
+// are deterministic.
+#include "common.cuh"
+
+namespace grest {
+
+namespace {
+
+template <typename T, int NCH>
+struct Acc {
+  T v[NCH];
+};
+
+template <typename T, int NCH, bool HASVAL>
+__device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                             int64_t beg, int64_t end, const OpParams& op, const T* __restrict__ X,
+                                             int64_t ldx, int w, int64_t col_lo, int lane, Acc<T, NCH>& acc) {
+  const bool nl = op.op == GREST_OP_NLAP;
+  for (int64_t j0 = beg; j0 < end; j0 += 32) {
+    int64_t j = j0 + lane;
+    int32_t mc = 0;
+    T ma = 0;
+    if (j < end) {
+      mc = col[j];
+      double a = HASVAL ? val[j] : 1.0;
+      if (nl) a *= op.dis[mc];
+      ma = (T)a;
+    }
+    const int cnt = (int)((end - j0) < 32 ? (end - j0) : 32);
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {
+      int32_t c0 = __shfl_sync(0xffffffffu, mc, k), c1 = __shfl_sync(0xffffffffu, mc, k + 1);
+      int32_t c2 = __shfl_sync(0xffffffffu, mc, k + 2), c3 = __shfl_sync(0xffffffffu, mc, k + 3);
+      T a0 = __shfl_sync(0xffffffffu, ma, k), a1 = __shfl_sync(0xffffffffu, ma, k + 1);
+      T a2 = __shfl_sync(0xffffffffu, ma, k + 2), a3 = __shfl_sync(0xffffffffu, ma, k + 3);
+      const T* x0 = X + (int64_t)(c0 - col_lo) * ldx;
+      const T* x1 = X + (int64_t)(c1 - col_lo) * ldx;
+      const T* x2 = X + (int64_t)(c2 - col_lo) * ldx;
+      const T* x3 = X + (int64_t)(c3 - col_lo) * ldx;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        int c = ch * 32 + lane;
+        if (c < w) {
+          T y0 = __ldg(x0 + c), y1 = __ldg(x1 + c), y2 = __ldg(x2 + c), y3 = __ldg(x3 + c);
+          acc.v[ch] += a0 * y0 + a1 * y1 + a2 * y2 + a3 * y3;
+        }
+      }
+    }
+    for (; k < cnt; ++k) {
+      int32_t c0 = __shfl_sync(0xffffffffu, mc, k);
+      T a0 = __shfl_sync(0xffffffffu, ma, k);
+      const T* x0 = X + (int64_t)(c0 - col_lo) * ldx;
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        int c = ch * 32 + lane;
+        if (c < w) acc.v[ch] += a0 * __ldg(x0 + c);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo, int64_t hi, int64_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// diagonal coefficient of row r (Sec. 4.3); the sum term is scaled by `scale`
+__device__ __forceinline__ void diag_terms(const OpParams& op, int64_t r, double& dcoef, double& scale) {
+  dcoef = 0.0;
+  scale = 1.0;
+  if (op.op == GREST_OP_LAP) dcoef = 2.0 * (*op.dmax) - op.deg[r];
+  else if (op.op == GREST_OP_NLAP) { dcoef = 1.0; scale = op.dis[r]; }
+}
+
+template <typename T, int NCH, bool HASVAL>
+__global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
+                                                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                   OpParams op, const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                   int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = r0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < r1; r += warps) {
+    const int len = row_len[r];
+    if (col_lo == 0 && len > kLongRow) continue;  // hub rows: k_spmm_long
+    T* yr = Y + (r - r0) * ldy;
+    if (!op.live[r]) {
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        int c = ch * 32 + lane;
+        if (c < w) yr[c] = 0;
+      }
+      continue;
+    }
+    const int64_t beg = row_off[r], end = beg + len;
+    int64_t s = beg;
+    if (col_lo > 0) s = lower_bound_i32(col, beg, end, col_lo);
+    Acc<T, NCH> acc;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) acc.v[ch] = 0;
+    gather_range<T, NCH, HASVAL>(col, val, s, end, op, X, ldx, w, col_lo, lane, acc);
+    double dcoef, scale;
+    diag_terms(op, r, dcoef, scale);
+    const bool has_diag = dcoef != 0.0 && r >= col_lo;
+    const T* xr = X + (r - col_lo) * ldx;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      int c = ch * 32 + lane;
+      if (c < w) {
+        T y = (T)scale * acc.v[ch];
+        if (has_diag) y += (T)dcoef * xr[c];
+        yr[c] = y;
+      }
+    }
+  }
+}
+
+// one block (8 warps) per long row; fixed-order reduction in shared memory
+template <typename T, int NCH, bool HASVAL>
+__global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
+                                                   const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                   OpParams op, const int32_t* __restrict__ rows,
+                                                   const int64_t* __restrict__ n_rows, const T* __restrict__ X,
+                                                   int64_t ldx, T* __restrict__ Y, int64_t ldy, int w, int64_t r0,
+                                                   int64_t r1) {
+  __shared__ T part[8][NCH * 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nr = *n_rows;
+  for (int64_t t = blockIdx.x; t < nr; t += gridDim.x) {
+    const int64_t r = rows[t];
+    if (r < r0 || r >= r1) continue;
+    T* yr = Y + (r - r0) * ldy;
+    if (!op.live[r]) {
+      for (int c = threadIdx.x; c < w; c += blockDim.x) yr[c] = 0;
+      continue;
+    }
+    const int64_t beg = row_off[r], len = row_len[r];
+    const int64_t per = ((len + 7) / 8 + 31) & ~(int64_t)31;
+    int64_t s = beg + wid * per, e = s + per;
+    if (e > beg + len) e = beg + len;
+    Acc<T, NCH> acc;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) acc.v[ch] = 0;
+    if (s < e) gather_range<T, NCH, HASVAL>(col, val, s, e, op, X, ldx, w, 0, lane, acc);
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) part[wid][ch * 32 + lane] = acc.v[ch];
+    __syncthreads();
+    double dcoef, scale;
+    diag_terms(op, r, dcoef, scale);
+    const T* xr = X + r * ldx;
+    for (int c = threadIdx.x; c < w; c += blockDim.x) {
+      T sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sum += part[q][c];
+      T y = (T)scale * sum;
+      if (dcoef != 0.0) y += (T)dcoef * xr[c];
+      yr[c] = y;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int NCH>
+void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const T* X,
+                int64_t ldx, T* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo, cudaStream_t s) {
+  const int64_t rows = r1 - r0;
+  int64_t blocks = (rows + 7) / 8;
+  const int64_t cap = 152 * 64;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (g.val) {
+    k_spmm_rows<T, NCH, true><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, X, ldx, Y, ldy,
+                                                               w, r0, r1, col_lo);
+    if (col_lo == 0)
+      k_spmm_long<T, NCH, true><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows, n_long_dev,
+                                                         X, ldx, Y, ldy, w, r0, r1);
+  } else {
+    k_spmm_rows<T, NCH, false><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, X, ldx, Y,
+                                                                ldy, w, r0, r1, col_lo);
+    if (col_lo == 0)
+      k_spmm_long<T, NCH, false><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
+                                                          n_long_dev, X, ldx, Y, ldy, w, r0, r1);
+  }
+}
+
+template <typename T>
+void spmm_dispatch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const T* X,
+                   int64_t ldx, T* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo, cudaStream_t s) {
+  if (r1 <= r0 || w <= 0) return;
+  switch ((w + 31) / 32) {
+    case 1: launch_nch<T, 1>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 2: launch_nch<T, 2>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 3: launch_nch<T, 3>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 4: launch_nch<T, 4>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 5: launch_nch<T, 5>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 6: launch_nch<T, 6>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 7: launch_nch<T, 7>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 8: launch_nch<T, 8>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    default: launch_nch<T, 9>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+  }
+}
+
+}  // namespace
+
+void spmm_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+              const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+              cudaStream_t s) {
+  spmm_dispatch<double>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
+}
+
+void spmm_f32(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+              const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+              cudaStream_t s) {
+  spmm_dispatch<float>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
+}
+
+}  // namespace grest

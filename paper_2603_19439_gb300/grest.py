@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libgrest (include/grest.h): argument marshalling only.
+
+Every step of the G-REST update runs in the library's CUDA kernels; this
+module only converts NumPy arrays / torch tensors to pointers and back.  It
+never computes anything itself and has no CPU fallback: if the shared library
+is missing or cannot be loaded, constructing a tracker raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrest.so")
+
+OP_ADJ, OP_LAP, OP_NLAP = 0, 1, 2
+SUB_GREST2, SUB_GREST3, SUB_RSVD, SUB_AUTO = 0, 1, 2, 3
+FP64, MIXED = 0, 1
+PROJ_EXACT, PROJ_LOWRANK = 0, 1
+WB_RESID, WB_DELTA = 0, 1
+FLAG_CHECK = 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid update batch", 3: "device out of memory",
+          4: "capacity exceeded", 5: "numerical breakdown", 6: "CUDA error", 7: "device wait timed out",
+          8: "unsupported option"}
+
+
+class GrestError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(int(code), 'unknown')} ({int(code)})")
+
+
+class Config(C.Structure):
+    _fields_ = [("op", C.c_int32), ("k", C.c_int32), ("subspace", C.c_int32), ("L", C.c_int32), ("P", C.c_int32),
+                ("precision", C.c_int32), ("projection", C.c_int32), ("w_block", C.c_int32), ("flags", C.c_uint32),
+                ("seed", C.c_uint64), ("drop_tol", C.c_double), ("node_capacity", C.c_int64),
+                ("nnz_capacity", C.c_int64), ("max_batch_edges", C.c_int64)]
+
+
+class Update(C.Structure):
+    _fields_ = [("n_new_nodes", C.c_int64), ("n_ins", C.c_int64), ("ins_u", C.c_void_p), ("ins_v", C.c_void_p),
+                ("ins_w", C.c_void_p), ("n_del", C.c_int64), ("del_u", C.c_void_p), ("del_v", C.c_void_p),
+                ("n_del_nodes", C.c_int64), ("del_nodes", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_nodes", C.c_int64), ("nnz", C.c_int64), ("m", C.c_int32), ("k_u", C.c_int32),
+                ("rank_q", C.c_int32), ("rank_y", C.c_int32), ("mode", C.c_int32), ("pad0", C.c_int32),
+                ("pivot_kept_min", C.c_double), ("pivot_dropped_max", C.c_double), ("boundary_gap", C.c_double),
+                ("orth_err", C.c_double), ("max_residual", C.c_double), ("galerkin", C.c_double),
+                ("ms_total", C.c_float), ("ms_graph", C.c_float), ("ms_spmm", C.c_float), ("ms_basis", C.c_float),
+                ("ms_project", C.c_float), ("ms_eig", C.c_float), ("ms_lift", C.c_float), ("ms_refine", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+
+
+EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
+           "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_destroy", "grest_status_str"]
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libgrest.so (raises OSError when it is absent or unloadable)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libgrest.so not built: {p} (run __graft_entry__.build())")
+    lib = C.CDLL(p)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    lib.grest_config_default.argtypes = [C.POINTER(Config), i32]
+    lib.grest_init.argtypes = [C.POINTER(Config), i64, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
+    lib.grest_apply_update.argtypes = [vp, C.POINTER(Update), C.POINTER(Stats)]
+    lib.grest_sync.argtypes = [vp]
+    lib.grest_get_embedding.argtypes = [vp, vp, vp, vp, C.POINTER(i64), i32]
+    lib.grest_get_ritz_values.argtypes = [vp, vp, C.POINTER(i32)]
+    lib.grest_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    lib.grest_apply_operator.argtypes = [vp, vp, i64, vp, i64, i32]
+    lib.grest_destroy.argtypes = [vp]
+    lib.grest_destroy.restype = None
+    lib.grest_status_str.argtypes = [i32]
+    lib.grest_status_str.restype = C.c_char_p
+    for f in EXPORTS[:-2]:
+        if f != "grest_destroy":
+            getattr(lib, f).restype = i32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def default_config(k, **kw):
+    lib = load_library()
+    cfg = Config()
+    lib.grest_config_default(C.byref(cfg), int(k))
+    for key, val in kw.items():
+        if not hasattr(cfg, key):
+            raise KeyError(key)
+        setattr(cfg, key, val)
+    return cfg
+
+
+class Tracker:
+    """One evolving graph and its K tracked eigenpairs on the GPU."""
+
+    def __init__(self, n, rowptr, col, val, U0, theta0, k, stream=None, **cfg_fields):
+        self.lib = load_library()
+        self.k = int(k)
+        self.cfg = default_config(k, **cfg_fields)
+        self._keep = [_host(rowptr, np.int64), _host(col, np.int32), _host(val, np.float64),
+                      _host(U0, np.float64), _host(theta0, np.float64)]
+        rp, cl, vl, u0, t0 = self._keep
+        h = C.c_void_p()
+        st = self.lib.grest_init(C.byref(self.cfg), int(n), _ptr(rp), _ptr(cl), _ptr(vl), _ptr(u0), _ptr(t0),
+                                 stream, C.byref(h))
+        if st != 0:
+            raise GrestError(st, "grest_init")
+        self.h = h
+        self._keep = None
+
+    def update(self, batch, on_device=False):
+        """Apply one batch (workloads.Batch with host arrays, or torch CUDA tensors
+        when on_device=True).  Returns the step diagnostics as a dict."""
+        if on_device:
+            arrs = [batch.ins_u, batch.ins_v, batch.ins_w, batch.del_u, batch.del_v, batch.del_nodes]
+        else:
+            arrs = [_host(batch.ins_u, np.int32), _host(batch.ins_v, np.int32), _host(batch.ins_w, np.float64),
+                    _host(batch.del_u, np.int32), _host(batch.del_v, np.int32), _host(batch.del_nodes, np.int32)]
+        iu, iv, iw, du, dv, dn = arrs
+        u = Update(n_new_nodes=int(batch.n_new), n_ins=int(len(iu)), ins_u=_ptr(iu), ins_v=_ptr(iv), ins_w=_ptr(iw),
+                   n_del=int(len(du)), del_u=_ptr(du), del_v=_ptr(dv),
+                   n_del_nodes=int(len(dn)) if dn is not None else 0, del_nodes=_ptr(dn),
+                   on_device=1 if on_device else 0)
+        s = Stats()
+        st = self.lib.grest_apply_update(self.h, C.byref(u), C.byref(s))
+        if st != 0:
+            raise GrestError(st, "grest_apply_update")
+        return s.as_dict()
+
+    def embedding(self):
+        n = C.c_int64()
+        st = self.lib.grest_get_embedding(self.h, None, None, None, C.byref(n), 0)
+        if st != 0:
+            raise GrestError(st, "grest_get_embedding")
+        U = np.empty((n.value, self.k))
+        th = np.empty(self.k)
+        live = np.empty(n.value, np.uint8)
+        st = self.lib.grest_get_embedding(self.h, _ptr(U), _ptr(th), _ptr(live), C.byref(n), 0)
+        if st != 0:
+            raise GrestError(st, "grest_get_embedding")
+        return U, th, live.astype(bool)
+
+    def embedding_device(self, U_dev, theta_dev):
+        """Copy (X_K, Lambda_K) into device tensors (n x k and k, float64)."""
+        n = C.c_int64()
+        st = self.lib.grest_get_embedding(self.h, _ptr(U_dev), _ptr(theta_dev), None, C.byref(n), 1)
+        if st != 0:
+            raise GrestError(st, "grest_get_embedding")
+        return n.value
+
+    def ritz_values(self):
+        m = C.c_int32()
+        self.lib.grest_get_ritz_values(self.h, None, C.byref(m))
+        out = np.empty(m.value)
+        self.lib.grest_get_ritz_values(self.h, _ptr(out), C.byref(m))
+        return out
+
+    def stats(self):
+        s = Stats()
+        self.lib.grest_get_stats(self.h, C.byref(s))
+        return s.as_dict()
+
+    def apply_operator(self, X, Y):
+        """Y = M X with X, Y torch CUDA float64 tensors (n x w, row-major)."""
+        st = self.lib.grest_apply_operator(self.h, X.data_ptr(), X.stride(0), Y.data_ptr(), Y.stride(0), X.shape[1])
+        if st != 0:
+            raise GrestError(st, "grest_apply_operator")
+
+    def sync(self):
+        st = self.lib.grest_sync(self.h)
+        if st != 0:
+            raise GrestError(st, "grest_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grest_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,61 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds for
+sm_103a, loads, and exports every entry point that include/grest.h declares;
+the ctypes structures match the header's layout."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_19439_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "grest.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(grest_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    assert L.grest_status_str(0) == b"ok"
+    assert L.grest_status_str(2) == b"invalid update batch"
+    cfg = grest.default_config(16)
+    assert (cfg.k, cfg.L, cfg.P, cfg.op, cfg.subspace) == (16, 100, 100, grest.OP_ADJ, grest.SUB_AUTO)
+    assert cfg.drop_tol == 1e-7
+
+
+def test_struct_sizes_match_header():
+    from paper_2603_19439_gb300 import grest
+    # int32 x 9, pad, uint64, double, int64 x 3
+    assert ctypes.sizeof(grest.Config) == 40 + 8 + 8 + 24
+    assert ctypes.sizeof(grest.Update) == 8 * 10 + 8
+    assert ctypes.sizeof(grest.Stats) == 24 + 24 + 48 + 32
+
+
+def test_init_rejects_bad_arguments_without_gpu(lib):
+    """Argument checks happen on the host before any device call."""
+    import numpy as np
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    cfg = grest.default_config(0)
+    h = ctypes.c_void_p()
+    rp = np.array([0, 0], np.int64)
+    assert L.grest_init(ctypes.byref(cfg), 1, rp.ctypes.data, None, None, None, None, None, ctypes.byref(h)) == 1
+    cfg = grest.default_config(2, L=200, P=100)
+    assert L.grest_init(ctypes.byref(cfg), 1, rp.ctypes.data, None, None, None, None, None, ctypes.byref(h)) == 1
