@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""G-REST update throughput on the 1M-node power-law stream (one JSON line).
+
+Workload (synthetic, seeded): Chung-Lu power-law graph, n = 1,000,000 nodes,
+degree exponent 2.3, mean degree 32, adjacency operator, K = 32 tracked pairs;
+each update adds 0.5% new nodes with 16 preferential-attachment edges each
+and deletes 0.1% of the edges uniformly (so S = 5,000 > L+P = 200 and the
+RSVD new-node basis of Sec. 3.5 is used, L = P = 100).  One step = one full
+G-REST update (graph update, basis, projection, eigensolve, lift) through the
+library's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grest|reference]
+
+`value` times K steps with the update batches already resident in device
+memory; `e2e` times K further steps through the same public call with the
+batches in pinned host memory (host->device copies inside the timed region)
+and a device->host read of the updated eigenvalues after every step.  Under
+torchrun every rank runs an independent replica (the update does not shard;
+there is no collective on the data path) and rank 0 prints the line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G-REST updates/s at n=1M,k=32: mixed vs FP64 GPU path; p50/p99 update latency"
+WL = dict(n=1_000_000, gamma=2.3, mean_degree=32, k=32, grow_frac=0.005, edges_per_new_node=16,
+          delete_frac=0.001, seed=20260306, L=100, P=100)
+SAMPLE_N = 100_000  # CPU-oracle sample of the same family
+# FP64 peak derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_desc(n):
+    return (f"Chung-Lu power-law stream n={n:,} gamma={WL['gamma']} mean_degree={WL['mean_degree']} adjacency "
+            f"K={WL['k']}, +{WL['grow_frac'] * 100:.1f}% nodes x {WL['edges_per_new_node']} PA edges and "
+            f"-{WL['delete_frac'] * 100:.1f}% edges per step, RSVD L=P={WL['L']}")
+
+
+def make_workload(n, steps, seed):
+    from paper_2603_19439_gb300 import workloads as wl
+    g, batches = wl.power_law_workload(n, WL["gamma"], WL["mean_degree"], steps, WL["grow_frac"],
+                                       WL["edges_per_new_node"], WL["delete_frac"], seed)
+    return g, batches
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling (every 200 ms) of SM clocks and throttle reasons."""
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 10:
+                    continue
+                if self.bus_id and self.bus_id not in p[1].lower() and p[1].lower() not in self.bus_id:
+                    continue
+                rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(steps, warmup=0):
+    """Time the FP64 CPU oracle on the n=SAMPLE_N member of the same workload
+    family; returns (seconds per step list, description)."""
+    import oracle as O
+    from paper_2603_19439_gb300 import workloads as wl
+    g, batches = make_workload(SAMPLE_N, steps + warmup, WL["seed"] + 7)
+    rp, col, _ = wl.csr_fast(g)
+    A = O.csr_from_arrays(g.n, rp, col)
+    import scipy.sparse.linalg as ssl
+    K = WL["k"]
+    ev, V = ssl.eigsh(A, k=K + 8, which="LM", tol=1e-10, v0=np.ones(g.n))
+    o = O.select_order(ev, O.OP_ADJ)[:K]
+    st = O.State(A=A, live=np.ones(g.n, bool), X=V[:, o], lam=ev[o])
+    cfg = O.Config(k=K, L=WL["L"], P=WL["P"], seed=WL["seed"])
+    times = []
+    for i, b in enumerate(batches):
+        t0 = time.perf_counter()
+        st, _ = O.grest_step(st, b, cfg)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    times = oracle_sample(args.steps, args.warmup)
+    t = sum(times)
+    ups_sample = len(times) / t
+    value = ups_sample * SAMPLE_N / WL["n"]  # linear-in-n scaling to the 1M workload
+    cores = os.cpu_count()
+    sample = (f"{len(times)} FP64 oracle steps on the n={SAMPLE_N:,} member of the same workload family "
+              f"({ups_sample:.4f} updates/s there), scaled by n to n={WL['n']:,}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(WL["n"]), "precision": "fp64", "sample_n": SAMPLE_N},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def roofline(prof_ms, prof_work, prof_launch, traffic_file):
+    from paper_2603_19439_gb300 import grest as G
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    cls = int(np.argmax(prof_ms))
+    name = G.PROF_CLASSES[cls]
+    ms = prof_ms[cls]
+    if name == "spmm":
+        achieved = prof_work[cls] / (ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        out = {"bound": "hbm", "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+    else:
+        achieved = prof_work[cls] / (ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        out = {"bound": "alu", "unit": "TFLOP/s",
+               "peak_source": "FP64 DFMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; DESIGN.md)"}
+    traffic = None
+    try:
+        t = json.load(open(traffic_file))
+        entry = t.get(name)
+        if entry and entry.get("source_hash") == source_hash(entry.get("sources", [])):
+            traffic = entry["bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    out.update({"kernel_class": name, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": traffic, "launches_per_step": prof_launch[cls], "ms_per_step": ms})
+    return out
+
+
+def source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        p = os.path.join(ROOT, f)
+        if not os.path.exists(p):
+            return None
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def initial_pairs(tr, n, k, torch):
+    """Leading K pairs of A^(0) (Alg. 2, line 3: any direct eigensolver):
+    ARPACK Lanczos whose products A x run in the library's SpMM."""
+    import scipy.sparse.linalg as ssl
+    x_d = torch.empty((n, 1), dtype=torch.float64, device="cuda")
+    y_d = torch.empty_like(x_d)
+
+    def mv(x):
+        x_d.copy_(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64).reshape(n, 1)))
+        tr.apply_operator(x_d, y_d)
+        return y_d.cpu().numpy().reshape(-1)
+
+    op = ssl.LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    ev, V = ssl.eigsh(op, k=k + 8, which="LM", tol=1e-10, v0=np.ones(n))
+    order = sorted(range(ev.size), key=lambda i: (-abs(ev[i]), -ev[i], i))[:k]
+    return np.ascontiguousarray(V[:, order]), ev[order]
+
+
+def run_grest(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_19439_gb300 import grest as G
+    from paper_2603_19439_gb300 import workloads as wl
+
+    n, K, W, steps = WL["n"], WL["k"], args.warmup, args.steps
+    t0 = time.time()
+    g, batches = make_workload(n, W + 2 * steps, WL["seed"] + 1000 * rank)
+    rp, col, _ = wl.csr_fast(g)
+    t_gen = time.time() - t0
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    tr = G.Tracker(g.n, rp, col, None, np.zeros((g.n, K)), np.zeros(K), K, stream=stream.cuda_stream,
+                   L=WL["L"], P=WL["P"], seed=WL["seed"], flags=G.FLAG_PROFILE,
+                   node_capacity=int(g.n * 1.2) + 4096)
+    U0, th0 = initial_pairs(tr, g.n, K, torch)
+    tr.set_embedding(U0, th0)
+    t_init = time.time() - t0
+
+    def dev_batch(b):
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+        return wl.Batch(b.n_new, t(b.ins_u), t(b.ins_v), t(b.del_u), t(b.del_v), t(b.del_nodes))
+
+    def pinned_batch(b):
+        def p(a):
+            x = torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+            return x.numpy()
+        return wl.Batch(b.n_new, p(b.ins_u), p(b.ins_v), p(b.del_u), p(b.del_v), p(b.del_nodes))
+
+    dev = [dev_batch(b) for b in batches[:W + steps]]
+    host = [pinned_batch(b) for b in batches[W + steps:]]
+    torch.cuda.synchronize()
+    for b in dev[:W]:
+        tr.update(b, on_device=True)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    bus = None
+    if hasattr(props, "pci_bus_id"):
+        bus = "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id, props.pci_device_id)
+    clocks = ClockSampler(bus)
+    # ---- timed region A: inputs resident in HBM
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    prof_ms = np.zeros(5)
+    prof_work = np.zeros(5)
+    prof_n = np.zeros(5)
+    launches = 0
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i, b in enumerate(dev[W:]):
+        ev[i][0].record(stream)
+        s = tr.update(b, on_device=True)
+        ev[i][1].record(stream)
+        prof_ms += s["prof_ms"]
+        prof_work += s["prof_work"]
+        prof_n += s["prof_launches"]
+        launches += s["kernel_launches"]
+        last = s
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_dev = e0.elapsed_time(e1) * 1e-3
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    # ---- timed region B: end to end through the public call from pinned host memory
+    theta_h = torch.empty(K, dtype=torch.float64).pin_memory().numpy()
+    h2d = d2h = 0
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for b in host:
+        tr.update(b, on_device=False)
+        tr.lib.grest_get_embedding(tr.h, None, theta_h.ctypes.data, None, G.C.byref(G.C.c_int64()), 0)
+        h2d += 4 * (2 * b.n_ins + 2 * b.n_del + b.del_nodes.size)
+        d2h += theta_h.nbytes
+    e3.record(stream)
+    barrier()
+    t_e2e = e2.elapsed_time(e3) * 1e-3
+    t_dev_max, t_e2e_max = t_dev, t_e2e
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev, t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev_max, t_e2e_max = tt.tolist()
+    tr.close()
+    if rank != 0:
+        return 0
+    value = world * steps / t_dev_max
+    res = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": steps, "warmup": W,
+        "ms_per_step": 1e3 * t_dev_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(n), "precision": "fp64", "k": K, "n0": g.n, "nnz0": int(rp[-1]),
+                   "l2": "inputs larger than L2 (graph and N x m blocks are GBs); no flush",
+                   "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "min": lat[0], "max": lat[-1]},
+        "fp64": {"updates_per_s": value, "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99))},
+        "mixed": None,
+        "e2e": {"value": world * steps / t_e2e_max, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
+                "d2h_bytes_per_step": d2h // steps},
+        "gpu_launches": int(launches),
+        "roofline": roofline(prof_ms / steps, prof_work / steps, prof_n / steps,
+                             os.path.join(ROOT, "profiles", "traffic.json")),
+        "phase_ms_per_step": {G.PROF_CLASSES[i]: prof_ms[i] / steps for i in range(5)},
+        "last_step": {k: last[k] for k in ("m", "rank_q", "rank_y", "mode", "n_nodes", "nnz", "pivot_kept_min",
+                                           "boundary_gap")},
+        "clocks": clk, "init_s": {"generate": t_gen, "init_and_eigsh": t_init},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        times = oracle_sample(2)
+        ups = len(times) / sum(times)
+        res["cpu_baseline"] = {"value": ups * SAMPLE_N / n, "unit": "updates/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"{len(times)} FP64 oracle steps on the n={SAMPLE_N:,} member of the same "
+                                         f"family ({ups:.4f} updates/s there), scaled by n to n={n:,}; "
+                                         f"BLAS on all cores, scipy.sparse products single-threaded"}
+    print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["grest", "reference"], default="grest")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_grest(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

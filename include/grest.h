@@ -71,7 +71,8 @@ enum { GREST_PROJ_EXACT = 0, GREST_PROJ_LOWRANK = 1 };   /* Eq. (main2) / Eq. (m
 enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };          /* W = P_perp M_new X_bar / P_perp Delta X_bar */
 
 /* grest_config.flags */
-#define GREST_FLAG_CHECK 1u /* after each step compute residual diagnostics into grest_stats */
+#define GREST_FLAG_CHECK 1u   /* after each step compute residual diagnostics into grest_stats */
+#define GREST_FLAG_PROFILE 2u /* time every kernel class with CUDA events (grest_stats.prof_*) */
 
 typedef struct {
   int32_t op;          /* GREST_OP_*                                                   */
@@ -83,7 +84,8 @@ typedef struct {
   int32_t w_block;     /* GREST_WB_*                                                   */
   uint32_t flags;      /* GREST_FLAG_*                                                 */
   uint64_t seed;       /* key of the counter-based generator that draws Omega          */
-  double drop_tol;     /* relative pivot below which a basis direction is dropped      */
+  double drop_tol;     /* a basis direction is dropped when its pivot R_kk is at most   *
+                        * drop_tol * max(R_00, |theta_1|) (|theta_1| ~ ||M||_2)         */
   int64_t node_capacity;   /* maximum number of node ids; 0 = 1.25 x initial + 1024     */
   int64_t nnz_capacity;    /* directed-edge arena size;   0 = 2 x initial + 2^20        */
   int64_t max_batch_edges; /* largest n_ins + n_del per update; 0 = 2^20 (grows on demand) */
@@ -138,6 +140,14 @@ typedef struct {
   double max_residual;     /* max_j ||M x_j - theta_j x_j|| / |theta_1| (CHECK)         */
   double galerkin;         /* max |Z^T (M x_j - theta_j x_j)| / |theta_1| (CHECK)       */
   float ms_total, ms_graph, ms_spmm, ms_basis, ms_project, ms_eig, ms_lift, ms_refine;
+  /* GREST_FLAG_PROFILE: summed device time and algorithmic work per kernel class
+   * (index 0 SpMM, 1 Gram X^T Y, 2 tall-skinny GEMM X B, 3 small dense: Cholesky,
+   * eigensolver; 4 graph update).  Work is bytes for SpMM (row pointers, column
+   * indices, one read of X and one write of Y) and flops for the dense classes. */
+  double prof_ms[5];
+  double prof_work[5];
+  int64_t prof_launches[5];
+  int64_t kernel_launches; /* kernels this library enqueued during the step       */
 } grest_stats;
 
 /* Fill *cfg with defaults for k tracked pairs: ADJ, AUTO, L = P = 100
@@ -181,6 +191,15 @@ grest_status grest_sync(grest_ctx *ctx);
 grest_status grest_get_embedding(grest_ctx *ctx, double *U, double *theta, uint8_t *live_mask,
                                  int64_t *n_out, int32_t on_device);
 
+/*
+ * Replace (X_K, Lambda_K) for the current graph, e.g. to resume from a saved
+ * embedding or to start from pairs computed after grest_init.  U: n x k
+ * row-major with orthonormal columns (rows of tombstoned ids are ignored and
+ * stored as zero), theta: k values in tracking order; host (on_device = 0) or
+ * device (1) pointers of the context's device.
+ */
+grest_status grest_set_embedding(grest_ctx *ctx, const double *U, const double *theta, int32_t on_device);
+
 /* All m Ritz values of the last step in tracking order (Alg. 1); *m_out receives m.
  * ritz may be NULL to query m; it must hold at least m values otherwise. */
 grest_status grest_get_ritz_values(grest_ctx *ctx, double *ritz, int32_t *m_out);
@@ -196,6 +215,17 @@ grest_status grest_get_stats(grest_ctx *ctx, grest_stats *stats);
  */
 grest_status grest_apply_operator(grest_ctx *ctx, const double *X, int64_t ldx, double *Y,
                                   int64_t ldy, int32_t w);
+
+/*
+ * C = X^T Y for device blocks X (n x a, row-major, leading dimension ldx) and
+ * Y (n x b, ldy), a, b <= 256, written to the device array C (a x b,
+ * row-major, ldc).  This is the split-K Gram kernel of the projection steps
+ * (X_bar^T Y1, Gram matrices of CholQR2, H = Z^T (M Z) of Alg. 1); it runs on
+ * the context's stream and uses the context's scratch, so calls on one
+ * context must not overlap.  Useful for checks such as X^T X - I.
+ */
+grest_status grest_gram(grest_ctx *ctx, const double *X, int64_t ldx, int32_t a, const double *Y, int64_t ldy,
+                        int32_t b, int64_t n, double *C, int64_t ldc);
 
 /* Release every device buffer of the context. NULL is ignored. */
 void grest_destroy(grest_ctx *ctx);

@@ -61,7 +61,8 @@ struct OpParams {
 size_t scan_temp_bytes(int64_t n);
 // exclusive prefix sum of n int64 values; out may alias in; writes the total
 // to out[n] (out must hold n+1 values).
-void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
+// returns the number of kernels launched
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
 
 // graph.cu
 struct BatchDev {
@@ -95,9 +96,11 @@ struct GraphWork {
 };
 constexpr int kLongRow = 512;
 // Validate and apply a batch.  Returns after enqueueing; errors land in *err.
-void graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, int64_t* host_scalars,
-                       cudaStream_t s);
-void graph_refresh_derived(Csr& g, GraphWork& w, int64_t n_rows, cudaStream_t s);
+// These launchers return the number of kernels they enqueued.
+int graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, cudaStream_t s);
+int graph_refresh_derived(Csr& g, GraphWork& w, int64_t n_rows, cudaStream_t s);
+// total row length over rows [0, n) into *out (device int64)
+int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s);
 
 // spmm.cu
 // Y[r0:r1) = (M X)[r0:r1) for rows r0..r1, w columns; when col_lo > 0 only

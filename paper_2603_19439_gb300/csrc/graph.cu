@@ -423,73 +423,130 @@ __global__ void k_max_reduce(const double* part, int64_t n, double* out) {
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 inline unsigned capped(int64_t n, int64_t cap) { return (unsigned)(n < 1 ? 1 : (n < cap ? n : cap)); }
 
+__global__ void k_sum_len(const int32_t* row_len, int64_t n, unsigned long long* out) {
+  __shared__ unsigned long long red[256];
+  unsigned long long v = 0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    v += (unsigned long long)row_len[r];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
 }  // namespace
 
-void graph_refresh_derived(Csr& g, GraphWork& w, int64_t n, cudaStream_t s) {
-  if (n <= 0) return;
+int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  unsigned nb = blocks_for(n, 256);
+  if (nb > 1024) nb = 1024;
+  if (nb < 1) nb = 1;
+  k_sum_len<<<nb, 256, 0, s>>>(g.row_len, n, reinterpret_cast<unsigned long long*>(out));
+  return 1;
+}
+
+int graph_refresh_derived(Csr& g, GraphWork& w, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  int nk = 0;
   const int T = 256;
   unsigned nb = blocks_for(n, T);
   double* bmax = reinterpret_cast<double*>(w.need);  // n_cap+1 int64 scratch reused as doubles
   k_derived<<<nb, T, 0, s>>>(n, g.live, g.deg, g.row_len, g.dis, w.rowflag, bmax);
+  ++nk;
   k_max_reduce<<<1, 1024, 0, s>>>(bmax, nb, g.dmax);
-  exclusive_scan_i64(w.rowflag, w.rowflag, n, w.scan_tmp, s);
+  ++nk;
+  nk += exclusive_scan_i64(w.rowflag, w.rowflag, n, w.scan_tmp, s);
   k_compact<<<nb, T, 0, s>>>(w.rowflag, n, w.long_rows, w.scalars + 1);
+  ++nk;
+  return nk;
 }
 
-void graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, int64_t* host_scalars,
-                       cudaStream_t s) {
+int graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, cudaStream_t s) {
+  int nk = 0;
   const int64_t N = g.n, N2 = g.n + b.S;
   const int T = 256;
   const unsigned gsz = 152 * 8;
   cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (N2 + 1), s);
   cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * N2, s);
   cudaMemsetAsync(w.delflag, 0, N2, s);
-  if (b.S > 0) k_init_new_rows<<<blocks_for(b.S, T), T, 0, s>>>(N, N2, g.row_off, g.row_len, g.row_cap);
+  if (b.S > 0) {
+    k_init_new_rows<<<blocks_for(b.S, T), T, 0, s>>>(N, N2, g.row_off, g.row_len, g.row_cap);
+    ++nk;
+  }
   if (b.n_dn > 0) {
     k_mark_removed<<<capped(blocks_for(b.n_dn, T), gsz), T, 0, s>>>(b.dn, b.n_dn, N, g.live, w.cursor, w.delflag, err);
+    ++nk;
     cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * N2, s);
   }
-  if (b.n_ins > 0)
+  if (b.n_ins > 0) {
     k_count_edges<<<capped(blocks_for(b.n_ins, T), gsz), T, 0, s>>>(b.ins_u, b.ins_v, b.ins_w, b.n_ins, N2, N, g.live,
                                                                    w.delflag, w.cnt, err);
-  if (b.n_del > 0)
+    ++nk;
+  }
+  if (b.n_del > 0) {
     k_count_edges<<<capped(blocks_for(b.n_del, T), gsz), T, 0, s>>>(b.del_u, b.del_v, nullptr, b.n_del, N, N, g.live,
                                                                    w.delflag, w.cnt, err);
-  if (b.n_dn > 0)
+    ++nk;
+  }
+  if (b.n_dn > 0) {
     k_count_removed<<<capped(b.n_dn, gsz), T, 0, s>>>(b.dn, b.n_dn, g.row_off, g.row_len, g.col, w.cnt, err);
+    ++nk;
+  }
   // segment offsets and staging offsets
   k_cnt_to_i64<<<blocks_for(N2, T), T, 0, s>>>(w.cnt, w.seg, N2);
-  exclusive_scan_i64(w.seg, w.seg, N2, w.scan_tmp, s);
+  ++nk;
+  nk += exclusive_scan_i64(w.seg, w.seg, N2, w.scan_tmp, s);
   k_touch_flags<<<blocks_for(N2, T), T, 0, s>>>(w.cnt, w.delflag, g.row_len, N2, w.rowflag, w.tmp_off);
-  exclusive_scan_i64(w.tmp_off, w.tmp_off, N2, w.scan_tmp, s);
-  exclusive_scan_i64(w.rowflag, w.rowflag, N2, w.scan_tmp, s);
+  ++nk;
+  nk += exclusive_scan_i64(w.tmp_off, w.tmp_off, N2, w.scan_tmp, s);
+  nk += exclusive_scan_i64(w.rowflag, w.rowflag, N2, w.scan_tmp, s);
   k_compact<<<blocks_for(N2, T), T, 0, s>>>(w.rowflag, N2, w.touched, w.scalars + 0);
+  ++nk;
   k_check_sizes<<<1, 1, 0, s>>>(w.seg, w.tmp_off, N2, w.ent_cap, w.tmp_cap, err);
+  ++nk;
   // scatter, sort, merge
-  if (b.n_ins > 0)
+  if (b.n_ins > 0) {
     k_scatter_edges<<<capped(blocks_for(b.n_ins, T), gsz), T, 0, s>>>(b.ins_u, b.ins_v, b.ins_w, b.n_ins, kTagIns,
                                                                      w.seg, w.cursor, w.ekey, w.ew, err);
-  if (b.n_del > 0)
+    ++nk;
+  }
+  if (b.n_del > 0) {
     k_scatter_edges<<<capped(blocks_for(b.n_del, T), gsz), T, 0, s>>>(b.del_u, b.del_v, nullptr, b.n_del, kTagDel,
                                                                      w.seg, w.cursor, w.ekey, w.ew, err);
-  if (b.n_dn > 0)
+    ++nk;
+  }
+  if (b.n_dn > 0) {
     k_scatter_removed<<<capped(b.n_dn, gsz), T, 0, s>>>(b.dn, b.n_dn, g.row_off, g.row_len, g.col, w.seg, w.cursor,
                                                         w.ekey, w.ew, err);
+    ++nk;
+  }
   k_sort_segments<<<gsz, 256, 0, s>>>(w.touched, w.scalars + 0, w.seg, w.ekey, w.eins, err);
+  ++nk;
   k_merge_rows<<<gsz, 256, 0, s>>>(w.touched, w.scalars + 0, w.seg, w.ekey, w.ew, w.eins, w.delflag, g.row_off,
                                     g.row_len, g.col, g.val, w.tmp_off, w.tmp_col, g.val ? w.tmp_val : nullptr,
                                     w.new_len, err);
+  ++nk;
   // capacity: touched rows that outgrow their slot
   const int64_t max_t = N2;  // upper bound of the touched count
   k_need<<<blocks_for(max_t, T), T, 0, s>>>(w.touched, w.scalars + 0, max_t, w.new_len, g.row_cap, w.need, err);
-  exclusive_scan_i64(w.need, w.need, max_t, w.scan_tmp, s);
+  ++nk;
+  nk += exclusive_scan_i64(w.need, w.need, max_t, w.scan_tmp, s);
   k_check_arena<<<1, 1, 0, s>>>(w.need, max_t, g.arena_top, g.nnz_cap, err);
+  ++nk;
   k_commit_rows<<<gsz, 256, 0, s>>>(w.touched, w.scalars + 0, w.need, g.arena_top, w.new_len, w.tmp_off, w.tmp_col,
                                      w.tmp_val, g.row_off, g.row_len, g.row_cap, g.col, g.val, g.deg, err);
+  ++nk;
   k_bump_arena<<<1, 1, 0, s>>>(g.arena_top, w.need, max_t, err);
+  ++nk;
   int64_t nc = b.S > b.n_dn ? b.S : b.n_dn;
-  if (nc > 0) k_commit_nodes<<<blocks_for(nc, T), T, 0, s>>>(N, N2, g.live, g.deg, b.dn, b.n_dn, err);
-  (void)host_scalars;
+  if (nc > 0) {
+    k_commit_nodes<<<blocks_for(nc, T), T, 0, s>>>(N, N2, g.live, g.deg, b.dn, b.n_dn, err);
+    ++nk;
+  }
+  return nk;
 }
 
 }  // namespace grest

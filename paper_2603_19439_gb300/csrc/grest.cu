@@ -80,7 +80,17 @@ struct grest_ctx {
   grest_stats stats{};
   std::vector<double> last_ritz;
   int last_m = 0;
+  int64_t nnz = 0;        // directed nonzeros (exact, read back after each graph update)
+  int64_t batch_new_edges = 0;  // inserted edges of the current batch (upper bound for the new-node block)
+  int64_t launches = 0;         // kernels enqueued during the current step
   cudaEvent_t ev[10];
+  // GREST_FLAG_PROFILE: event pairs around every launch group of the step
+  static constexpr int kProfEvents = 512;
+  cudaEvent_t pev[kProfEvents];
+  int prof_n = 0;
+  int prof_cls[kProfEvents / 2];
+  double prof_work[kProfEvents / 2];
+  bool profiling() const { return (cfg.flags & GREST_FLAG_PROFILE) != 0; }
 };
 
 namespace {
@@ -128,6 +138,8 @@ void free_ctx(grest_ctx* c) {
   if (c->h_err) cudaFreeHost(c->h_err);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->pev)
     if (e) cudaEventDestroy(e);
   delete c;
 }
@@ -190,6 +202,38 @@ grest_status read_back(grest_ctx* c, int n_info) {
   return GREST_OK;
 }
 
+int prof_begin(grest_ctx* c) {
+  if (!c->profiling() || c->prof_n + 2 > grest_ctx::kProfEvents) return -1;
+  int i = c->prof_n;
+  cudaEventRecord(c->pev[i], c->stream);
+  c->prof_n += 2;
+  return i;
+}
+
+void prof_end(grest_ctx* c, int i, int cls, double work) {
+  if (i < 0) return;
+  cudaEventRecord(c->pev[i + 1], c->stream);
+  c->prof_cls[i / 2] = cls;
+  c->prof_work[i / 2] = work;
+}
+
+void prof_collect(grest_ctx* c, grest_stats& st) {
+  for (int k = 0; k < 5; ++k) {
+    st.prof_ms[k] = 0.0;
+    st.prof_work[k] = 0.0;
+    st.prof_launches[k] = 0;
+  }
+  for (int i = 0; i + 1 < c->prof_n; i += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->pev[i], c->pev[i + 1]);
+    int k = c->prof_cls[i / 2];
+    st.prof_ms[k] += ms;
+    st.prof_work[k] += c->prof_work[i / 2];
+    st.prof_launches[k] += 1;
+  }
+  c->prof_n = 0;
+}
+
 OpParams op_params(const grest_ctx* c) {
   OpParams p;
   p.op = c->cfg.op;
@@ -200,21 +244,48 @@ OpParams op_params(const grest_ctx* c) {
   return p;
 }
 
+// nnz_proc: entries of the processed rows that take part (all of them, or the
+// new-node block); x_rows: rows of X read at least once
 void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
-          int64_t col_lo) {
+          int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
+  int p = prof_begin(c);
   spmm_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+  if (r1 > r0 && w > 0) c->launches += col_lo == 0 ? 2 : 1;
+  if (nnz_proc < 0) nnz_proc = c->nnz;
+  if (x_rows < 0) x_rows = r1 - r0;
+  const double eb = c->g.val ? 12.0 : 4.0;
+  prof_end(c, p, 0, 12.0 * (r1 - r0) + eb * nnz_proc + 8.0 * w * ((r1 - r0) + x_rows));
 }
 
 void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
           double* C, int64_t ldc, bool sym) {
+  int p = prof_begin(c);
   gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+  if (a > 0 && b > 0 && n > 0) c->launches += 2;
+  prof_end(c, p, 1, 2.0 * n * a * b);
+}
+
+void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X, int64_t ldx, const double* B,
+          int64_t ldb, double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo) {
+  int p = prof_begin(c);
+  gemm_nn_f64(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
+  if (n > 0 && cc > 0) c->launches += 1;
+  prof_end(c, p, 2, 2.0 * n * a * cc);
+}
+
+void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf,
+         double* ritz, double* info) {
+  int p = prof_begin(c);
+  sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, c->stream);
+  c->launches += 4;
+  prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
 // X (n x w) <- P_perp X = X - U (U^T X), U = first ku columns of Z
 void project_out(grest_ctx* c, double* X, int64_t ldx, int w, int64_t n) {
   if (c->Ku == 0 || w == 0) return;
   gram(c, c->Z, c->ldz, c->Ku, X, ldx, w, n, c->Cv, w, false);
-  gemm_nn_f64(n, c->Ku, w, -1.0, c->Z, c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx, c->stream);
+  gemm(c, n, c->Ku, w, -1.0, c->Z, c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx);
 }
 
 // CholQR with pivoting: Out (n x rank) = X (n x w) T; returns rank via info slot
@@ -222,14 +293,17 @@ grest_status cholqr_pass(grest_ctx* c, const double* X, int64_t ldx, int w, int6
                          const double* abs_ref_ptr, double* Out, int64_t ldo, int info_slot, bool read_rank,
                          int* rank_out) {
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
+  int p = prof_begin(c);
   pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->info + info_slot, c->stream);
+  c->launches += 1;
+  prof_end(c, p, 3, (double)w * w * w / 3.0 + (double)w * w * w / 3.0);
   int rank = w;
   if (read_rank) {
     grest_status st = read_back(c, info_slot + 4);
     if (st != GREST_OK) return st;
     rank = (int)c->h_info[info_slot];
   }
-  if (rank > 0) gemm_nn_f64(n, w, rank, 1.0, X, ldx, c->T, w, 0.0, nullptr, 0, Out, ldo, c->stream);
+  if (rank > 0) gemm(c, n, w, rank, 1.0, X, ldx, c->T, w, 0.0, nullptr, 0, Out, ldo);
   if (rank_out) *rank_out = rank;
   return GREST_OK;
 }
@@ -316,8 +390,10 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
   CK(cudaEventRecord(c->ev[1], s));
   // A2: X_bar = [X; 0]; removed nodes: zero their rows and re-orthonormalize (reading of node removal)
   k_pad_copy<<<1024, 256, 0, s>>>(c->U, c->ldu, c->Z, c->ldz, N, N2, c->Ku);
+  c->launches += 1;
   if (removed) {
     zero_dead_rows(c->Z, c->ldz, c->Ku, g.live, N2, s);
+    c->launches += 1;
     int r1 = 0;
     grest_status st = cholqr_pass(c, c->Z, c->ldz, c->Ku, N2, c->cfg.drop_tol, 1.0, nullptr, c->V2, c->ldv, 0, true, &r1);
     if (st != GREST_OK) return st;
@@ -333,7 +409,7 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
   // A4: C = X_bar^T Y1; W = Y1 - X_bar C, re-projected once
   double* W = c->Z + Ku;
   gram(c, c->Z, c->ldz, Ku, c->MZ, c->ldz, Ku, N2, c->Cm, Ku, false);
-  gemm_nn_f64(N2, Ku, Ku, -1.0, c->Z, c->ldz, c->Cm, Ku, 1.0, c->MZ, c->ldz, W, c->ldz, s);
+  gemm(c, N2, Ku, Ku, -1.0, c->Z, c->ldz, c->Cm, Ku, 1.0, c->MZ, c->ldz, W, c->ldz);
   project_out(c, W, c->ldz, Ku, N2);
   // A5: new-node block
   int cb = 0;
@@ -346,7 +422,7 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
       if (S > q) return GREST_ERR_UNSUPPORTED;  // exact block wider than the basis buffers
       mode = 3;
       // E = M_new[:, N:N2] = M_new * [0; I_S] (restricted SpMM against the identity)
-      spmm(c, c->Id, c->ldq, B, c->ldz, (int)S, 0, N2, N);
+      spmm(c, c->Id, c->ldq, B, c->ldz, (int)S, 0, N2, N, c->batch_new_edges + S, S);
       project_out(c, B, c->ldz, (int)S, N2);
       cb = (int)S;
     } else {
@@ -355,7 +431,8 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
       if (st != GREST_OK) return st;
       // S.1: Y = P_perp Delta_2 Omega
       gaussian_omega(c->Om, c->ldq, S, q, c->cfg.seed, (uint64_t)c->step, s);
-      spmm(c, c->Om, c->ldq, c->Yr, c->ldq, q, 0, N2, N);
+      c->launches += 1;
+      spmm(c, c->Om, c->ldq, c->Yr, c->ldq, q, 0, N2, N, c->batch_new_edges + S, S);
       project_out(c, c->Yr, c->ldq, q, N2);
       project_out(c, c->Yr, c->ldq, q, N2);
       // M = orth(Y): CholQR2 with pivoting
@@ -368,15 +445,15 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
       c->stats.rank_y = rY;
       if (rY > 0) {
         // S.2: B_s^T = Delta_2^T M - (Delta_2^T X_bar)(X_bar^T M), Delta_2^T X_bar = Y1[N:N2]
-        spmm(c, c->Yr, c->ldq, c->EtM, c->ldq, rY, N, N2, 0);
+        spmm(c, c->Yr, c->ldq, c->EtM, c->ldq, rY, N, N2, 0, c->batch_new_edges + S, N2);
         gram(c, c->Z, c->ldz, Ku, c->Yr, c->ldq, rY, N2, c->XtM, rY, false);
-        gemm_nn_f64(S, Ku, rY, -1.0, c->MZ + N * c->ldz, c->ldz, c->XtM, rY, 1.0, c->EtM, c->ldq, c->EtM, c->ldq, s);
+        gemm(c, S, Ku, rY, -1.0, c->MZ + N * c->ldz, c->ldz, c->XtM, rY, 1.0, c->EtM, c->ldq, c->EtM, c->ldq);
         // left singular vectors of B_s via eig(B_s B_s^T), L leading
         gram(c, c->EtM, c->ldq, rY, c->EtM, c->ldq, rY, S, c->Gs, rY, true);
         const int Lp = std::min(c->Lr, rY);
-        sym_eig_select(c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16, c->eigwork, s);
+        eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16);
         // S.4: R = M U_hat
-        gemm_nn_f64(N2, rY, Lp, 1.0, c->Yr, c->ldq, c->Uh, Lp, 0.0, nullptr, 0, B, c->ldz, s);
+        gemm(c, N2, rY, Lp, 1.0, c->Yr, c->ldq, c->Uh, Lp, 0.0, nullptr, 0, B, c->ldz);
         cb = Lp;
       }
     }
@@ -405,13 +482,15 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
   // A8: H = Z^T (M Z) (Eq. main2), symmetrized
   gram(c, c->Z, c->ldz, m, c->MZ, c->ldz, m, N2, c->H, m, false);
   symmetrize(c->H, m, m, s);
+  c->launches += 1;
   CK(cudaEventRecord(c->ev[5], s));
   // A9: leading K eigenpairs of H (Alg. 1)
-  sym_eig_select(c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, c->eigwork, s);
+  eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28);
   CK(cudaEventRecord(c->ev[6], s));
   // A10: X = Z F_K, sign normalization
-  gemm_nn_f64(N2, m, K, 1.0, c->Z, c->ldz, c->F, K, 0.0, nullptr, 0, c->Un, c->ldu, s);
+  gemm(c, N2, m, K, 1.0, c->Z, c->ldz, c->F, K, 0.0, nullptr, 0, c->Un, c->ldu);
   sign_normalize(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
+  c->launches += 3;
   CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
   std::swap(c->U, c->Un);
   c->Ku = K;
@@ -433,11 +512,13 @@ grest_status run_checks(grest_ctx* c, int64_t n) {
   residual_norms(MU, c->U, c->ldu, K, c->theta, n, c->part, c->resn, s);
   gram(c, c->U, c->ldu, K, c->U, c->ldu, K, n, c->Cm, K, true);
   k_orth_err<<<1, 256, 0, s>>>(c->Cm, K, K, c->info + 36);
+  c->launches += 3;  // residual_norms (2) + k_orth_err
   // R = MU - U theta (ldv >= K), Galerkin residual Z^T R
   double* R = c->V2;
   k_resid_vecs<<<1024, 256, 0, s>>>(MU, c->U, c->ldu, K, c->theta, n, R, c->ldv);
   gram(c, c->Z, c->ldz, c->last_m, R, c->ldv, K, n, c->H, K, false);
   k_maxabs<<<1, 256, 0, s>>>(c->H, K, c->last_m, K, c->info + 37);
+  c->launches += 2;  // k_resid_vecs + k_maxabs
   return GREST_OK;
 }
 
@@ -494,6 +575,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   if (cudaGetDevice(&dev) != cudaSuccess) return GREST_ERR_CUDA;
   grest_ctx* c = new grest_ctx();
   for (auto& e : c->ev) e = nullptr;
+  for (auto& e : c->pev) e = nullptr;
   c->cfg = *cfg;
   c->dev = dev;
   c->stream = (cudaStream_t)cuda_stream;
@@ -587,6 +669,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(cudaMallocHost((void**)&c->h_err, sizeof(int32_t)));
   IK(cudaMallocHost((void**)&c->h_scal, sizeof(int64_t) * 8));
   for (auto& e : c->ev) IK(cudaEventCreate(&e));
+  for (auto& e : c->pev) IK(cudaEventCreate(&e));
   cudaStream_t s = c->stream;
   // graph upload
   IK(cudaMemcpyAsync(g.row_off, off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
@@ -609,12 +692,13 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
     IK(cudaStreamSynchronize(s));
   }
   k_fill_identity<<<(unsigned)((c->q * c->q + 255) / 256), 256, 0, s>>>(c->Id, c->ldq, c->q);
-  graph_refresh_derived(g, w, n, s);
+  (void)graph_refresh_derived(g, w, n, s);
   IK(cudaGetLastError());
   IK(cudaStreamSynchronize(s));
 #undef IK
   c->stats.n_nodes = n;
   c->stats.nnz = nnz;
+  c->nnz = nnz;
   *out = c;
   return GREST_OK;
 }
@@ -633,6 +717,8 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   if (N + S > INT32_MAX) return GREST_ERR_CAPACITY;
   grest_status st = ensure_batch(c, std::max(u->n_ins, u->n_del), u->n_del_nodes);
   if (st != GREST_OK) return st;
+  c->prof_n = 0;
+  c->launches = 0;
   CK(cudaEventRecord(c->ev[0], s));
   const cudaMemcpyKind kind = u->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (u->n_ins > 0) {
@@ -649,6 +735,7 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   int64_t entries = 2 * (u->n_ins + u->n_del);
   if (u->n_del_nodes > 0) {
     k_sum_removed_degree<<<1, 256, 0, s>>>(c->b_dn, u->n_del_nodes, N, c->g.row_len, c->gw.scalars + 4);
+    c->launches += 1;
     CK(cudaMemcpyAsync(c->h_scal + 4, c->gw.scalars + 4, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     entries += c->h_scal[4];
@@ -667,14 +754,25 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   bd.del_v = c->b_dv;
   bd.dn = c->b_dn;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
-  graph_apply_batch(c->g, c->gw, bd, c->err, nullptr, s);
+  c->batch_new_edges = u->n_ins;
+  {
+    int p = prof_begin(c);
+    c->launches += graph_apply_batch(c->g, c->gw, bd, c->err, s);
+    prof_end(c, p, 4, 0.0);
+  }
+  c->launches += graph_count_nnz(c->g, N + S, c->gw.scalars + 5, s);
+  CK(cudaMemcpyAsync(c->h_scal + 5, c->gw.scalars + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   st = read_back(c, 0);
   if (st != GREST_OK) return st;
-  if (*c->h_err) return map_dev_err(*c->h_err);
+  if (*c->h_err) {
+    c->prof_n = 0;
+    return map_dev_err(*c->h_err);
+  }
+  c->nnz = c->h_scal[5];
   // committed: the graph now has N + S ids
   c->g.n = N + S;
-  graph_refresh_derived(c->g, c->gw, N + S, s);
+  c->launches += graph_refresh_derived(c->g, c->gw, N + S, s);
   c->stats.rank_y = 0;
   st = fp64_step(c, bd, N, S, u->n_del_nodes > 0);
   CK(cudaGetLastError());
@@ -690,6 +788,9 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   grest_stats& S_ = c->stats;
   S_.step = c->step;
   S_.n_nodes = c->g.n;
+  S_.nnz = c->nnz;
+  prof_collect(c, S_);
+  S_.kernel_launches = c->launches;
   S_.boundary_gap = c->h_info[28];
   if (c->h_info[24] < c->stats.rank_q) return GREST_ERR_NUMERIC;
   if (c->cfg.flags & GREST_FLAG_CHECK) {
@@ -736,6 +837,20 @@ grest_status grest_get_embedding(grest_ctx* c, double* U, double* theta, uint8_t
   return from_cuda(cudaStreamSynchronize(s));
 }
 
+grest_status grest_set_embedding(grest_ctx* c, const double* U, const double* theta, int32_t on_device) {
+  if (!c || !U || !theta) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->g.n;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpy2DAsync(c->U, sizeof(double) * c->ldu, U, sizeof(double) * c->K, sizeof(double) * c->K, n, kind, s));
+  CK(cudaMemcpyAsync(c->theta, theta, sizeof(double) * c->K, kind, s));
+  zero_dead_rows(c->U, c->ldu, c->K, c->g.live, n, s);
+  c->Ku = c->K;
+  CK(cudaGetLastError());
+  return from_cuda(cudaStreamSynchronize(s));
+}
+
 grest_status grest_get_ritz_values(grest_ctx* c, double* ritz, int32_t* m_out) {
   if (!c || !m_out) return GREST_ERR_INVALID_ARG;
   *m_out = c->last_m;
@@ -753,6 +868,17 @@ grest_status grest_apply_operator(grest_ctx* c, const double* X, int64_t ldx, do
   if (!c || !X || !Y || w < 1 || w > 288 || ldx < w || ldy < w) return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
   spmm(c, X, ldx, Y, ldy, w, 0, c->g.n, 0);
+  CK(cudaGetLastError());
+  return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+grest_status grest_gram(grest_ctx* c, const double* X, int64_t ldx, int32_t a, const double* Y, int64_t ldy,
+                        int32_t b, int64_t n, double* C, int64_t ldc) {
+  if (!c || !X || !Y || !C || a < 1 || b < 1 || a > 256 || b > 256 || n < 0 || ldx < a || ldy < b || ldc < b)
+    return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  if (gram_parts(n, a, b) * (int64_t)a * b > c->part_cap) return GREST_ERR_CAPACITY;
+  gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);
   CK(cudaGetLastError());
   return from_cuda(cudaStreamSynchronize(c->stream));
 }

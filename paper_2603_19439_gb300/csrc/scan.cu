@@ -85,22 +85,23 @@ size_t scan_temp_bytes(int64_t n) {
   return bytes + 256;
 }
 
-void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s) {
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s) {
   if (n <= 0) {
     cudaMemsetAsync(out, 0, sizeof(int64_t), s);
-    return;
+    return 0;
   }
   int64_t nt = (n + kScanTile - 1) / kScanTile;
   int64_t* tiles = reinterpret_cast<int64_t*>(temp);
   k_scan_tiles<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n, tiles);
   if (nt == 1) {  // a single tile: its total is the grand total
     k_scan_total<<<1, 1, 0, s>>>(out, n, tiles, 0);
-    return;
+    return 2;
   }
   // tiles[0..nt) -> exclusive offsets in place, total in tiles[nt]
-  exclusive_scan_i64(tiles, tiles, nt, tiles + nt + 1, s);
+  int k = exclusive_scan_i64(tiles, tiles, nt, tiles + nt + 1, s);
   k_scan_add<<<(unsigned)nt, kScanThreads, 0, s>>>(out, n, tiles);
   k_scan_total<<<1, 1, 0, s>>>(out, n, tiles, nt);
+  return k + 3;
 }
 
 }  // namespace grest

@@ -21,6 +21,8 @@ FP64, MIXED = 0, 1
 PROJ_EXACT, PROJ_LOWRANK = 0, 1
 WB_RESID, WB_DELTA = 0, 1
 FLAG_CHECK = 1
+FLAG_PROFILE = 2
+PROF_CLASSES = ("spmm", "gram", "gemm", "small", "graph")
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid update batch", 3: "device out of memory",
           4: "capacity exceeded", 5: "numerical breakdown", 6: "CUDA error", 7: "device wait timed out",
@@ -52,14 +54,23 @@ class Stats(C.Structure):
                 ("pivot_kept_min", C.c_double), ("pivot_dropped_max", C.c_double), ("boundary_gap", C.c_double),
                 ("orth_err", C.c_double), ("max_residual", C.c_double), ("galerkin", C.c_double),
                 ("ms_total", C.c_float), ("ms_graph", C.c_float), ("ms_spmm", C.c_float), ("ms_basis", C.c_float),
-                ("ms_project", C.c_float), ("ms_eig", C.c_float), ("ms_lift", C.c_float), ("ms_refine", C.c_float)]
+                ("ms_project", C.c_float), ("ms_eig", C.c_float), ("ms_lift", C.c_float), ("ms_refine", C.c_float),
+                ("prof_ms", C.c_double * 5), ("prof_work", C.c_double * 5), ("prof_launches", C.c_int64 * 5),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad0"}
+        out = {}
+        for f, _ in self._fields_:
+            if f == "pad0":
+                continue
+            v = getattr(self, f)
+            out[f] = list(v) if f.startswith("prof_") else v
+        return out
 
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
-           "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_destroy", "grest_status_str"]
+           "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
+           "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -79,9 +90,11 @@ def load_library(path=None):
     lib.grest_apply_update.argtypes = [vp, C.POINTER(Update), C.POINTER(Stats)]
     lib.grest_sync.argtypes = [vp]
     lib.grest_get_embedding.argtypes = [vp, vp, vp, vp, C.POINTER(i64), i32]
+    lib.grest_set_embedding.argtypes = [vp, vp, vp, i32]
     lib.grest_get_ritz_values.argtypes = [vp, vp, C.POINTER(i32)]
     lib.grest_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.grest_apply_operator.argtypes = [vp, vp, i64, vp, i64, i32]
+    lib.grest_gram.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
     lib.grest_status_str.argtypes = [i32]
@@ -175,6 +188,16 @@ class Tracker:
             raise GrestError(st, "grest_get_embedding")
         return n.value
 
+    def set_embedding(self, U, theta):
+        """Replace (X_K, Lambda_K): numpy arrays, or torch CUDA float64 tensors."""
+        dev = hasattr(U, "data_ptr")
+        if not dev:
+            U = _host(U, np.float64)
+            theta = _host(theta, np.float64)
+        st = self.lib.grest_set_embedding(self.h, _ptr(U), _ptr(theta), 1 if dev else 0)
+        if st != 0:
+            raise GrestError(st, "grest_set_embedding")
+
     def ritz_values(self):
         m = C.c_int32()
         self.lib.grest_get_ritz_values(self.h, None, C.byref(m))
@@ -192,6 +215,13 @@ class Tracker:
         st = self.lib.grest_apply_operator(self.h, X.data_ptr(), X.stride(0), Y.data_ptr(), Y.stride(0), X.shape[1])
         if st != 0:
             raise GrestError(st, "grest_apply_operator")
+
+    def gram(self, X, Y, C):
+        """C = X^T Y for torch CUDA float64 tensors (row-major)."""
+        st = self.lib.grest_gram(self.h, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(), Y.stride(0), Y.shape[1],
+                                 X.shape[0], C.data_ptr(), C.stride(0))
+        if st != 0:
+            raise GrestError(st, "grest_gram")
 
     def sync(self):
         st = self.lib.grest_sync(self.h)

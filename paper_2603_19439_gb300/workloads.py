@@ -206,6 +206,16 @@ def sbm_graph(n, n_comm, p_in, p_out, seed, equal_sizes=True):
     return EdgeSetGraph(n, keys), labels
 
 
+def _sorted_unique(a):
+    a = np.sort(a)
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def chung_lu_graph(n, gamma, mean_deg, seed, i0=None):
     """Chung-Lu power-law graph by ball dropping; self-loops and repeats removed."""
     rng = np.random.default_rng(seed)
@@ -225,12 +235,14 @@ def chung_lu_graph(n, gamma, mean_deg, seed, i0=None):
     while keys.size < target and tries < 8:
         need = target - keys.size
         draw = int(need * 1.05) + 64
-        u = np.searchsorted(cdf, rng.random(draw), side="right")
-        v = np.searchsorted(cdf, rng.random(draw), side="right")
+        # endpoints ~ w: sorted uniforms make the search sequential; a random
+        # permutation of sorted i.i.d. draws is again i.i.d.
+        u = rng.permutation(np.searchsorted(cdf, np.sort(rng.random(draw)), side="right"))
+        v = rng.permutation(np.searchsorted(cdf, np.sort(rng.random(draw)), side="right"))
         u = np.minimum(u, n - 1)
         v = np.minimum(v, n - 1)
         ok = u != v
-        keys = np.unique(np.concatenate([keys, keys_of(u[ok], v[ok])]))
+        keys = _sorted_unique(np.concatenate([keys, keys_of(u[ok], v[ok])]))
         tries += 1
     if keys.size > target:
         keys = np.sort(rng.choice(keys, size=target, replace=False))
@@ -390,3 +402,92 @@ def chung_lu_stream(n, gamma, mean_deg, steps, grow_frac, edges_per_node, del_fr
         g.apply(b)
         batches.append(b)
     return g0, batches
+
+
+class PowerLawStream:
+    """Fast generator of the power-law growth stream: per step, S new nodes
+    attach `edges_per_node` distinct old targets drawn proportionally to degree
+    (preferential attachment) and `n_delete` uniformly chosen existing edges
+    are removed.  Edges live in an append-only key array with an alive mask,
+    so no step needs a search over the whole edge set."""
+
+    def __init__(self, g: EdgeSetGraph, seed):
+        self.rng = np.random.default_rng(seed)
+        self.n = g.n
+        self.keys = g.keys.copy()
+        self.alive = np.ones(self.keys.size, bool)
+        self.n_alive = int(self.keys.size)
+        self.deg = g.degrees().astype(np.float64)
+
+    def next_batch(self, S, edges_per_node, n_delete):
+        rng = self.rng
+        n = self.n
+        cdf = np.cumsum(self.deg[:n])
+        cdf /= cdf[-1]
+        c = 3 * edges_per_node
+        cand = np.searchsorted(cdf, rng.random((S, c)), side="right")
+        np.minimum(cand, n - 1, out=cand)
+        # first occurrences per row in draw order, keep the first edges_per_node
+        order = np.argsort(cand, axis=1, kind="stable")
+        srt = np.take_along_axis(cand, order, axis=1)
+        dup_s = np.zeros_like(srt, dtype=bool)
+        dup_s[:, 1:] = srt[:, 1:] == srt[:, :-1]
+        dup = np.zeros_like(dup_s)
+        np.put_along_axis(dup, order, dup_s, axis=1)
+        rank = np.cumsum(~dup, axis=1)
+        keep = (~dup) & (rank <= edges_per_node)
+        rows, cols = np.nonzero(keep)
+        tgt = cand[rows, cols].astype(np.int64)
+        newid = (n + rows).astype(np.int64)
+        ik = keys_of(tgt, newid)
+        # uniform deletions among alive edges
+        dk = np.zeros(0, np.int64)
+        if n_delete > 0:
+            alive_idx = np.flatnonzero(self.alive)
+            pick = rng.choice(alive_idx.size, size=min(n_delete, alive_idx.size), replace=False)
+            di = np.sort(alive_idx[pick])
+            dk = self.keys[di]
+            self.alive[di] = False
+            du, dv = split_keys(dk)
+            np.subtract.at(self.deg, du, 1.0)
+            np.subtract.at(self.deg, dv, 1.0)
+        # commit the insertions
+        self.deg = np.concatenate([self.deg, np.zeros(S)])
+        np.add.at(self.deg, tgt, 1.0)
+        np.add.at(self.deg, newid, 1.0)
+        self.keys = np.concatenate([self.keys, ik])
+        self.alive = np.concatenate([self.alive, np.ones(ik.size, bool)])
+        self.n = n + S
+        iu, iv = split_keys(ik)
+        du, dv = split_keys(dk)
+        return Batch(n_new=S, ins_u=iu, ins_v=iv, del_u=du, del_v=dv)
+
+
+def power_law_workload(n, gamma, mean_deg, steps, grow_frac, edges_per_node, del_frac, seed, lcc=False):
+    """Initial Chung-Lu graph and `steps` batches of the growth stream
+    (+grow_frac*N nodes, -del_frac*|E| edges per step), sizes taken from the
+    graph at the start of each step."""
+    g = chung_lu_graph(n, gamma, mean_deg, seed)
+    if lcc:
+        g = largest_component(g)
+    st = PowerLawStream(g, seed + 1)
+    batches = []
+    for _ in range(steps):
+        S = int(np.floor(grow_frac * st.n))
+        nd = int(np.floor(del_frac * st.n_alive))
+        b = st.next_batch(S, edges_per_node, nd)
+        st.n_alive += b.n_ins - b.n_del
+        batches.append(b)
+    return g, batches
+
+
+def csr_fast(g: EdgeSetGraph):
+    """Symmetric CSR of an EdgeSetGraph without per-row column sorting."""
+    u, v = split_keys(g.keys)
+    rows = np.concatenate([u, v])
+    cols = np.concatenate([v, u])
+    order = np.argsort(rows, kind="stable")
+    rowptr = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=g.n), out=rowptr[1:])
+    val = None if g.w is None else np.concatenate([g.w, g.w])[order]
+    return rowptr, cols[order].astype(np.int32), val

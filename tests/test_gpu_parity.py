@@ -208,3 +208,24 @@ def test_chung_lu_200k_nlap_one_step(cuda):
     assert s["mode"] == 4 and s["m"] == info.m
     U.compare(tr, st, info, O.OP_NLAP, 16, "cl200k")
     tr.close()
+
+
+def test_gram_entry_point(cuda):
+    """grest_gram: C = X^T Y against a plain float64 product, several tile
+    shapes, row counts that leave a ragged final chunk."""
+    torch = cuda
+    g, _ = wl.sbm_graph(200, 2, 0.1, 0.02, 61)
+    rp, col, _ = g.csr()
+    tr = G.Tracker(g.n, rp, col, None, np.linalg.qr(np.random.default_rng(0).standard_normal((200, 4)))[0],
+                   np.ones(4), 4)
+    rng = np.random.default_rng(62)
+    for n, a, b in ((1, 1, 1), (1000, 7, 9), (100_003, 64, 65), (50_001, 200, 132), (3000, 256, 256)):
+        X = rng.standard_normal((n, a))
+        Y = rng.standard_normal((n, b))
+        Xd = torch.tensor(X, device="cuda")
+        Yd = torch.tensor(Y, device="cuda")
+        Cd = torch.empty((a, b), dtype=torch.float64, device="cuda")
+        tr.gram(Xd, Yd, Cd)
+        ref = X.T @ Y
+        assert np.abs(Cd.cpu().numpy() - ref).max() <= 1e-12 * max(1.0, np.abs(X).max() * np.abs(Y).max() * n)
+    tr.close()
