@@ -227,6 +227,34 @@ grest_status grest_apply_operator(grest_ctx *ctx, const double *X, int64_t ldx, 
 grest_status grest_gram(grest_ctx *ctx, const double *X, int64_t ldx, int32_t a, const double *Y, int64_t ldy,
                         int32_t b, int64_t n, double *C, int64_t ldc);
 
+/*
+ * grest_gram_noalloc -- the same product as grest_gram, C = X^T Y, for
+ * callers that cannot allocate device memory: a host application that hands
+ * all of the GPU's memory to its own pool (a cudaMalloc would fail or break
+ * the pool's accounting), or a latency-critical loop that must not pay the
+ * device-wide synchronization a cudaMalloc/cudaFree can cause.  It needs no
+ * context and allocates nothing: it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  (The paper has no counterpart; this is a library
+ * service.)
+ *
+ * X (n x a, ldx), Y (n x b, ldy) and C (a x b, ldc) are row-major device
+ * arrays owned by the caller; 1 <= a, b <= 256 (larger widths return
+ * GREST_ERR_CAPACITY), n >= 1.  The split-K partial sums live in one
+ * fixed 4 MiB array of device memory inside the library (a file-scope
+ * __device__ array that every GPU loading the library holds until the
+ * process exits).  Every call on a device shares that array and the array
+ * keeps the last call's contents, so calls that overlap on the GPU (two
+ * streams, or two host threads) race and must be serialized by the caller;
+ * every partial a call reads is written earlier in the same call, so nothing
+ * needs clearing.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  The work is enqueued on cuda_stream
+ * (NULL = legacy default stream) and C is complete when that stream's work
+ * is; the call itself does not synchronize.
+ */
+grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const double *Y, int64_t ldy, int32_t b,
+                                int64_t n, double *C, int64_t ldc, void *cuda_stream);
+
 /* Release every device buffer of the context. NULL is ignored. */
 void grest_destroy(grest_ctx *ctx);
 

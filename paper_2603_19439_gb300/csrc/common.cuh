@@ -119,6 +119,10 @@ void spmm_f32(const Csr& g, const OpParams& op, const int32_t* long_rows, const 
 int64_t gram_parts(int64_t n, int a, int b);
 void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
               double* C, int64_t ldc, double* part, bool symmetric, cudaStream_t s);
+// As gram_f64 (non-symmetric), with the row-chunk count capped so that the
+// partials fit in part_cap doubles; returns -1 when even one chunk does not fit.
+int gram_f64_capped(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
+                    int64_t ldc, double* part, int64_t part_cap, cudaStream_t s);
 // Out (n x c, ldo) = beta * Cin (n x c, ldc) + alpha * X (n x a, ldx) * B (a x c, row-major ldb).
 void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B,
                  int64_t ldb, double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo,

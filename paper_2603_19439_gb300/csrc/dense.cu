@@ -405,6 +405,22 @@ void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy,
   k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric);
 }
 
+int gram_f64_capped(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
+                    int64_t ldc, double* part, int64_t part_cap, cudaStream_t s) {
+  if (a <= 0 || b <= 0 || n <= 0) return -1;
+  const int64_t per_chunk = (int64_t)a * b;
+  if (per_chunk > part_cap) return -1;
+  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
+  int64_t chunks = gram_chunks(n, nta * ntb);
+  if (chunks > part_cap / per_chunk) chunks = part_cap / per_chunk;
+  int64_t rpc = cdiv(n, chunks);
+  chunks = cdiv(n, rpc);
+  dim3 grid((unsigned)(nta * ntb), (unsigned)chunks);
+  k_gram_part<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, false, part);
+  k_gram_reduce<<<(unsigned)cdiv(per_chunk, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, false);
+  return 0;
+}
+
 void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B, int64_t ldb,
                  double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo, cudaStream_t s) {
   if (n <= 0 || c <= 0) return;
