@@ -36,8 +36,11 @@ METRIC = "G-REST updates/s at n=1M,k=32: mixed vs FP64 GPU path; p50/p99 update 
 WL = dict(n=1_000_000, gamma=2.3, mean_degree=32, k=32, grow_frac=0.005, edges_per_new_node=16,
           delete_frac=0.001, seed=20260306, L=100, P=100)
 SAMPLE_N = 100_000  # CPU-oracle sample of the same family
+# pivots of an FP32-accumulated Gram are resolved only to ~5e-4 R_00 (reading R5)
+MIXED_DROP_TOL = 1e-3
 # FP64 peak derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def env_rank():
@@ -160,7 +163,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def roofline(prof_ms, prof_work, prof_launch, traffic_file):
+def roofline(prof_ms, prof_work, prof_launch, traffic_file, precision="fp64"):
     from paper_2603_19439_gb300 import grest as G
     peaks = {}
     try:
@@ -174,11 +177,16 @@ def roofline(prof_ms, prof_work, prof_launch, traffic_file):
         achieved = prof_work[cls] / (ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         out = {"bound": "hbm", "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
-    else:
+    elif precision == "fp64" or name == "small":
         achieved = prof_work[cls] / (ms * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS
         out = {"bound": "alu", "unit": "TFLOP/s",
                "peak_source": "FP64 DFMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; DESIGN.md)"}
+    else:
+        achieved = prof_work[cls] / (ms * 1e-3) / 1e12
+        peak = FP32_PEAK_TFLOPS
+        out = {"bound": "alu", "unit": "TFLOP/s",
+               "peak_source": "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (derived; DESIGN.md)"}
     traffic = None
     try:
         t = json.load(open(traffic_file))
@@ -240,11 +248,14 @@ def run_grest(args):
     t_gen = time.time() - t0
     stream = torch.cuda.current_stream()
     t0 = time.time()
-    tr = G.Tracker(g.n, rp, col, None, np.zeros((g.n, K)), np.zeros(K), K, stream=stream.cuda_stream,
-                   L=WL["L"], P=WL["P"], seed=WL["seed"], flags=G.FLAG_PROFILE,
-                   node_capacity=int(g.n * 1.2) + 4096)
-    U0, th0 = initial_pairs(tr, g.n, K, torch)
-    tr.set_embedding(U0, th0)
+    common = dict(stream=stream.cuda_stream, L=WL["L"], P=WL["P"], seed=WL["seed"], flags=G.FLAG_PROFILE,
+                  node_capacity=int(g.n * 1.2) + 4096)
+    tr64 = G.Tracker(g.n, rp, col, None, np.zeros((g.n, K)), np.zeros(K), K, precision=G.FP64, **common)
+    U0, th0 = initial_pairs(tr64, g.n, K, torch)
+    tr64.set_embedding(U0, th0)
+    tr32 = None
+    if not args.fp64_only:
+        tr32 = G.Tracker(g.n, rp, col, None, U0, th0, K, precision=G.MIXED, drop_tol=MIXED_DROP_TOL, **common)
     t_init = time.time() - t0
 
     def dev_batch(b):
@@ -260,8 +271,6 @@ def run_grest(args):
     dev = [dev_batch(b) for b in batches[:W + steps]]
     host = [pinned_batch(b) for b in batches[W + steps:]]
     torch.cuda.synchronize()
-    for b in dev[:W]:
-        tr.update(b, on_device=True)
 
     def barrier():
         if world > 1:
@@ -272,33 +281,60 @@ def run_grest(args):
     bus = None
     if hasattr(props, "pci_bus_id"):
         bus = "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id, props.pci_device_id)
-    clocks = ClockSampler(bus)
-    # ---- timed region A: inputs resident in HBM
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    prof_ms = np.zeros(5)
-    prof_work = np.zeros(5)
-    prof_n = np.zeros(5)
-    launches = 0
-    clocks.start()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i, b in enumerate(dev[W:]):
-        ev[i][0].record(stream)
-        s = tr.update(b, on_device=True)
-        ev[i][1].record(stream)
-        prof_ms += s["prof_ms"]
-        prof_work += s["prof_work"]
-        prof_n += s["prof_launches"]
-        launches += s["kernel_launches"]
-        last = s
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    t_dev = e0.elapsed_time(e1) * 1e-3
-    lat = sorted(a.elapsed_time(b) for a, b in ev)
-    # ---- timed region B: end to end through the public call from pinned host memory
+
+    def timed(tr):
+        """Warm-up, then K timed steps with device-resident batches."""
+        for b in dev[:W]:
+            tr.update(b, on_device=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        prof = {"ms": np.zeros(5), "work": np.zeros(5), "n": np.zeros(5), "launches": 0}
+        clocks = ClockSampler(bus)
+        clocks.start()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = None
+        for i, b in enumerate(dev[W:]):
+            ev[i][0].record(stream)
+            s = tr.update(b, on_device=True)
+            ev[i][1].record(stream)
+            prof["ms"] += s["prof_ms"]
+            prof["work"] += s["prof_work"]
+            prof["n"] += s["prof_launches"]
+            prof["launches"] += s["kernel_launches"]
+            last = s
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop()
+        t = e0.elapsed_time(e1) * 1e-3
+        lat = sorted(a.elapsed_time(b) for a, b in ev)
+        return t, lat, prof, last, clk
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        tt = torch.tensor([x], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return tt.item()
+
+    t64, lat64, prof64, last64, clk64 = timed(tr64)
+    t64 = max_over_ranks(t64)
+    tr64.close()
+    main = dict(t=t64, lat=lat64, prof=prof64, last=last64, clk=clk64, tr=None, precision="fp64")
+    res32 = None
+    if tr32 is not None:
+        t32, lat32, prof32, last32, clk32 = timed(tr32)
+        t32 = max_over_ranks(t32)
+        res32 = dict(t=t32, lat=lat32, prof=prof32, last=last32, clk=clk32)
+        main = dict(res32, precision="mixed")
+    # ---- end to end through the public call from pinned host memory (headline path)
+    tr_e2e = tr32
+    if tr_e2e is None:
+        tr_e2e = G.Tracker(g.n, rp, col, None, U0, th0, K, precision=G.FP64, **common)
+        for b in dev[:W + steps]:
+            tr_e2e.update(b, on_device=True)
     theta_h = torch.empty(K, dtype=torch.float64).pin_memory().numpy()
     h2d = d2h = 0
     barrier()
@@ -306,44 +342,47 @@ def run_grest(args):
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for b in host:
-        tr.update(b, on_device=False)
-        tr.lib.grest_get_embedding(tr.h, None, theta_h.ctypes.data, None, G.C.byref(G.C.c_int64()), 0)
+        tr_e2e.update(b, on_device=False)
+        tr_e2e.lib.grest_get_embedding(tr_e2e.h, None, theta_h.ctypes.data, None, G.C.byref(G.C.c_int64()), 0)
         h2d += 4 * (2 * b.n_ins + 2 * b.n_del + b.del_nodes.size)
         d2h += theta_h.nbytes
     e3.record(stream)
     barrier()
-    t_e2e = e2.elapsed_time(e3) * 1e-3
-    t_dev_max, t_e2e_max = t_dev, t_e2e
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev, t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev_max, t_e2e_max = tt.tolist()
-    tr.close()
+    t_e2e = max_over_ranks(e2.elapsed_time(e3) * 1e-3)
+    if tr32 is not None:
+        tr32.close()
+    else:
+        tr_e2e.close()
     if rank != 0:
         return 0
-    value = world * steps / t_dev_max
+
+    def summary(r):
+        return {"updates_per_s": world * steps / r["t"], "ms_per_step": 1e3 * r["t"] / steps,
+                "p50_ms": float(np.percentile(r["lat"], 50)), "p99_ms": float(np.percentile(r["lat"], 99)),
+                "phase_ms_per_step": {G.PROF_CLASSES[i]: float(r["prof"]["ms"][i] / steps) for i in range(5)},
+                "last_step": {k: r["last"][k] for k in ("m", "rank_q", "rank_y", "mode", "n_nodes", "nnz",
+                                                        "pivot_kept_min", "boundary_gap", "ms_refine")}}
+
+    value = world * steps / main["t"]
     res = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": steps, "warmup": W,
-        "ms_per_step": 1e3 * t_dev_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(n), "precision": "fp64", "k": K, "n0": g.n, "nnz0": int(rp[-1]),
-                   "l2": "inputs larger than L2 (graph and N x m blocks are GBs); no flush",
-                   "parallelism": f"replicas{world}"},
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "min": lat[0], "max": lat[-1]},
-        "fp64": {"updates_per_s": value, "p50_ms": float(np.percentile(lat, 50)),
-                 "p99_ms": float(np.percentile(lat, 99))},
-        "mixed": None,
-        "e2e": {"value": world * steps / t_e2e_max, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
-                "d2h_bytes_per_step": d2h // steps},
-        "gpu_launches": int(launches),
-        "roofline": roofline(prof_ms / steps, prof_work / steps, prof_n / steps,
-                             os.path.join(ROOT, "profiles", "traffic.json")),
-        "phase_ms_per_step": {G.PROF_CLASSES[i]: prof_ms[i] / steps for i in range(5)},
-        "last_step": {k: last[k] for k in ("m", "rank_q", "rank_y", "mode", "n_nodes", "nnz", "pivot_kept_min",
-                                           "boundary_gap")},
-        "clocks": clk, "init_s": {"generate": t_gen, "init_and_eigsh": t_init},
+        "ms_per_step": 1e3 * main["t"] / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if main["precision"] == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(n), "precision": main["precision"], "k": K, "n0": g.n,
+                   "nnz0": int(rp[-1]), "l2": "inputs larger than L2 (graph and N x m blocks are GBs); no flush",
+                   "parallelism": f"replicas{world}",
+                   "mixed_drop_tol": MIXED_DROP_TOL},
+        "latency_ms": {"p50": float(np.percentile(main["lat"], 50)), "p99": float(np.percentile(main["lat"], 99)),
+                       "min": main["lat"][0], "max": main["lat"][-1]},
+        "mixed": summary(res32) if res32 else None,
+        "fp64": summary(dict(t=t64, lat=lat64, prof=prof64, last=last64)),
+        "e2e": {"value": world * steps / t_e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
+                "d2h_bytes_per_step": d2h // steps, "precision": main["precision"]},
+        "gpu_launches": int(main["prof"]["launches"]),
+        "roofline": roofline(main["prof"]["ms"] / steps, main["prof"]["work"] / steps, main["prof"]["n"] / steps,
+                             os.path.join(ROOT, "profiles", "traffic.json"), main["precision"]),
+        "clocks": main["clk"], "clocks_fp64": clk64,
+        "init_s": {"generate": t_gen, "init_and_eigsh": t_init},
     }
     if not args.no_cpu_baseline and world == 1:
         times = oracle_sample(2)
@@ -366,6 +405,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["grest", "reference"], default="grest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -112,6 +112,10 @@ void spmm_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const 
 void spmm_f32(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
               const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
               cudaStream_t s);
+// FP32 X, FP64 accumulation and output (the refinement pass of the mixed path)
+void spmm_f32_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+                  const float* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+                  cudaStream_t s);
 
 // dense.cu
 // C (a x b, row-major, ldc) = X^T Y over rows [0,n) with X (n x a, ldx), Y (n x b, ldy).
@@ -136,7 +140,16 @@ void symmetrize(double* H, int64_t ld, int m, cudaStream_t s);
 void fill_f64(double* p, double v, int64_t n, cudaStream_t s);
 void copy_cols_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
 void zero_dead_rows(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s);
+void zero_dead_rows(float* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s);
 void sign_normalize(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s);
+void sign_normalize(float* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s);
+// mixed precision: FP32 blocks, FP64 small matrices
+void gram_f32(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+              int64_t ldc, double* part, bool symmetric, cudaStream_t s);
+void gemm_nn_f32(int64_t n, int a, int c, double alpha, const float* X, int64_t ldx, const double* B, int64_t ldb,
+                 double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, cudaStream_t s);
+void convert_f32_to_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
+void convert_f64_to_f32(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
 void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,
                     double* part, double* out, cudaStream_t s);
 
@@ -151,5 +164,6 @@ size_t eig_work_doubles(int mmax);
 // rsvd.cu
 // Omega (S x q, row-major ld) from Philox4x64-10 + Box-Muller at step t.
 void gaussian_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s);
+void gaussian_omega(float* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s);
 
 }  // namespace grest

@@ -76,6 +76,67 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ X,
     }
 }
 
+// FP32 inputs: products and 32-row slab sums in FP32, slab sums added into
+// FP64 accumulators, partials written in FP64.
+__global__ void __launch_bounds__(256) k_gram_part_f32(const float* __restrict__ X, int64_t ldx, int a,
+                                                       const float* __restrict__ Y, int64_t ldy, int b, int64_t n,
+                                                       int64_t rows_per_chunk, bool upper, double* __restrict__ part) {
+  __shared__ float Xs[TK][TM + 4];
+  __shared__ float Ys[TK][TN + 4];
+  const int ntb = (b + TN - 1) / TN;
+  int bid = blockIdx.x, ta = 0, tb;
+  if (!upper) {
+    ta = bid / ntb;
+    tb = bid % ntb;
+  } else {
+    while (bid >= ntb - ta) { bid -= ntb - ta; ++ta; }
+    tb = ta + bid;
+  }
+  const int i0 = ta * TM, j0 = tb * TN;
+  const int64_t chunk = blockIdx.y;
+  const int64_t rbeg = chunk * rows_per_chunk;
+  int64_t rend = rbeg + rows_per_chunk;
+  if (rend > n) rend = n;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int64_t r0 = rbeg; r0 < rend; r0 += TK) {
+    for (int e = threadIdx.x; e < TK * TM; e += 256) {
+      int rr = e / TM, cc = e % TM;
+      int64_t r = r0 + rr;
+      Xs[rr][cc] = (r < rend && i0 + cc < a) ? X[r * ldx + i0 + cc] : 0.f;
+      Ys[rr][cc] = (r < rend && j0 + cc < b) ? Y[r * ldy + j0 + cc] : 0.f;
+    }
+    __syncthreads();
+    float sl[4][4] = {};
+#pragma unroll 8
+    for (int k = 0; k < TK; ++k) {
+      float xa[4], yb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = Xs[k][ty * 4 + u];
+        yb[u] = Ys[k][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sl[u][v] = fmaf(xa[u], yb[v], sl[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += (double)sl[u][v];
+    __syncthreads();
+  }
+  double* P = part + chunk * (int64_t)a * b;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < a && j < b) P[(int64_t)i * b + j] = acc[u][v];
+    }
+}
+
 __global__ void k_gram_reduce(const double* __restrict__ part, int64_t chunks, int a, int b, double* C, int64_t ldc,
                               bool symmetric) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -135,6 +196,66 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t n, int a, int c, double
       if (beta != 0.0) y += beta * Cin[r * ldc + j];
       Out[r * ldo + j] = y;
     }
+  }
+}
+
+// FP32 tall-skinny update: Out = beta Cin + alpha X B with B given in FP64
+__global__ void __launch_bounds__(256) k_gemm_nn_f32(int64_t n, int a, int c, float alpha, const float* __restrict__ X,
+                                                     int64_t ldx, const double* __restrict__ B, int64_t ldb, float beta,
+                                                     const float* Cin, int64_t ldc, float* Out, int64_t ldo) {
+  __shared__ float Xs[TM][TK + 1];
+  __shared__ float Bs[TK][TN + 4];
+  const int64_t r0 = blockIdx.x * (int64_t)TM;
+  const int j0 = blockIdx.y * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < a; k0 += TK) {
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int rr = e / TK, kk = e % TK;
+      int64_t r = r0 + rr;
+      Xs[rr][kk] = (r < n && k0 + kk < a) ? X[r * ldx + k0 + kk] : 0.f;
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int kk = e / TN, cc = e % TN;
+      Bs[kk][cc] = (k0 + kk < a && j0 + cc < c) ? (float)B[(int64_t)(k0 + kk) * ldb + j0 + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < TK; ++k) {
+      float xa[4], bb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = Xs[ty * 4 + u][k];
+        bb[u] = Bs[k][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xa[u], bb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int64_t r = r0 + ty * 4 + u;
+    if (r >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      int j = j0 + tx * 4 + v;
+      if (j >= c) continue;
+      float y = alpha * acc[u][v];
+      if (beta != 0.f) y += beta * Cin[r * ldc + j];
+      Out[r * ldo + j] = y;
+    }
+  }
+}
+
+template <typename Ts, typename Td>
+__global__ void k_convert(const Ts* src, int64_t lds, Td* dst, int64_t ldd, int64_t n, int w) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e / w;
+    int c = (int)(e % w);
+    dst[r * ldd + c] = (Td)src[r * lds + c];
   }
 }
 
@@ -273,15 +394,17 @@ __global__ void k_copy_cols(const double* src, int64_t lds, double* dst, int64_t
   }
 }
 
-__global__ void k_zero_dead(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n) {
+template <typename T>
+__global__ void k_zero_dead(T* X, int64_t ldx, int w, const uint8_t* live, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e / w;
-    if (!live[r]) X[r * ldx + (e % w)] = 0.0;
+    if (!live[r]) X[r * ldx + (e % w)] = (T)0;
   }
 }
 
 // per column: the entry of largest magnitude, lowest index on ties
-__global__ void k_argmax_part(const double* X, int64_t ldx, int w, int64_t n, int64_t rows_per_block, double* part,
+template <typename T>
+__global__ void k_argmax_part(const T* X, int64_t ldx, int w, int64_t n, int64_t rows_per_block, double* part,
                               int64_t* ipart) {
   __shared__ double sv[256];
   __shared__ int64_t si[256];
@@ -292,7 +415,7 @@ __global__ void k_argmax_part(const double* X, int64_t ldx, int w, int64_t n, in
     double bv = -1.0;
     int64_t bi = INT64_MAX;
     for (int64_t r = rb + threadIdx.x; r < re; r += blockDim.x) {
-      double v = fabs(X[r * ldx + c]);
+      double v = fabs((double)X[r * ldx + c]);
       if (v > bv) { bv = v; bi = r; }
     }
     sv[threadIdx.x] = bv;
@@ -317,7 +440,8 @@ __global__ void k_argmax_part(const double* X, int64_t ldx, int w, int64_t n, in
   }
 }
 
-__global__ void k_argmax_final(const double* X, int64_t ldx, int w, int64_t nb, const double* part,
+template <typename T>
+__global__ void k_argmax_final(const T* X, int64_t ldx, int w, int64_t nb, const double* part,
                                const int64_t* ipart, double* sign) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= w) return;
@@ -328,14 +452,15 @@ __global__ void k_argmax_final(const double* X, int64_t ldx, int w, int64_t nb, 
     int64_t i = ipart[b * w + c];
     if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
   }
-  sign[c] = (bi != INT64_MAX && X[bi * ldx + c] < 0.0) ? -1.0 : 1.0;
+  sign[c] = (bi != INT64_MAX && (double)X[bi * ldx + c] < 0.0) ? -1.0 : 1.0;
 }
 
-__global__ void k_scale_cols(double* X, int64_t ldx, int w, int64_t n, const double* sign) {
+template <typename T>
+__global__ void k_scale_cols(T* X, int64_t ldx, int w, int64_t n, const double* sign) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e / w;
     int c = (int)(e % w);
-    X[r * ldx + c] *= sign[c];
+    X[r * ldx + c] *= (T)sign[c];
   }
 }
 
@@ -447,21 +572,70 @@ void copy_cols_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int
   if (t > 0) k_copy_cols<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(src, lds, dst, ldd, n, w);
 }
 
-void zero_dead_rows(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s) {
+template <typename T>
+void zero_dead_rows_t(T* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s) {
   int64_t t = n * w;
-  if (t > 0) k_zero_dead<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, live, n);
+  if (t > 0) k_zero_dead<T><<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, live, n);
+}
+void zero_dead_rows(double* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s) {
+  zero_dead_rows_t(X, ldx, w, live, n, s);
+}
+void zero_dead_rows(float* X, int64_t ldx, int w, const uint8_t* live, int64_t n, cudaStream_t s) {
+  zero_dead_rows_t(X, ldx, w, live, n, s);
 }
 
-void sign_normalize(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s) {
+template <typename T>
+void sign_normalize_t(T* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s) {
   if (n <= 0 || w <= 0) return;
   int64_t nb = 304;
   int64_t rpb = cdiv(n, nb);
   nb = cdiv(n, rpb);
-  k_argmax_part<<<(unsigned)nb, 256, 0, s>>>(X, ldx, w, n, rpb, part, ipart);
+  k_argmax_part<T><<<(unsigned)nb, 256, 0, s>>>(X, ldx, w, n, rpb, part, ipart);
   double* sign = part + nb * w;
-  k_argmax_final<<<(unsigned)cdiv(w, 64), 64, 0, s>>>(X, ldx, w, nb, part, ipart, sign);
+  k_argmax_final<T><<<(unsigned)cdiv(w, 64), 64, 0, s>>>(X, ldx, w, nb, part, ipart, sign);
   int64_t t = n * w;
-  k_scale_cols<<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, n, sign);
+  k_scale_cols<T><<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(X, ldx, w, n, sign);
+}
+void sign_normalize(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s) {
+  sign_normalize_t(X, ldx, w, n, part, ipart, s);
+}
+void sign_normalize(float* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s) {
+  sign_normalize_t(X, ldx, w, n, part, ipart, s);
+}
+
+void gram_f32(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+              int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
+  if (a <= 0 || b <= 0) return;
+  if (n <= 0) {
+    for (int i = 0; i < a; ++i) cudaMemsetAsync(C + (int64_t)i * ldc, 0, sizeof(double) * b, s);
+    return;
+  }
+  symmetric = symmetric && (X == Y) && (a == b) && (ldx == ldy);
+  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
+  const int nt = symmetric ? nta * (nta + 1) / 2 : nta * ntb;
+  int64_t chunks = gram_chunks(n, nta * ntb);
+  int64_t rpc = cdiv(n, chunks);
+  chunks = cdiv(n, rpc);
+  dim3 grid((unsigned)nt, (unsigned)chunks);
+  k_gram_part_f32<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, symmetric, part);
+  int64_t tot = (int64_t)a * b;
+  k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric);
+}
+
+void gemm_nn_f32(int64_t n, int a, int c, double alpha, const float* X, int64_t ldx, const double* B, int64_t ldb,
+                 double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, cudaStream_t s) {
+  if (n <= 0 || c <= 0) return;
+  dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
+  k_gemm_nn_f32<<<grid, 256, 0, s>>>(n, a, c, (float)alpha, X, ldx, B, ldb, (float)beta, Cin, ldc, Out, ldo);
+}
+
+void convert_f32_to_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s) {
+  int64_t t = n * w;
+  if (t > 0) k_convert<float, double><<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(src, lds, dst, ldd, n, w);
+}
+void convert_f64_to_f32(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t n, int w, cudaStream_t s) {
+  int64_t t = n * w;
+  if (t > 0) k_convert<double, float><<<(unsigned)(cdiv(t, 256) < 8192 ? cdiv(t, 256) : 8192), 256, 0, s>>>(src, lds, dst, ldd, n, w);
 }
 
 void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,

@@ -51,15 +51,19 @@ struct grest_ctx {
   double* U = nullptr;   // n_cap x ldu
   double* Un = nullptr;  // next U
   double* theta = nullptr;
-  double* Z = nullptr;   // n_cap x ldz : [X_bar | W | B/R] -> [X_bar | Q]
-  double* MZ = nullptr;  // n_cap x ldz : [Y1 | MQ]
-  double* V2 = nullptr;  // n_cap x ldv : CholQR staging
-  double* Yr = nullptr;  // n_cap x ldq : RSVD sketch / basis
-  double* Yr2 = nullptr; // n_cap x ldq
-  double* Om = nullptr;  // S_cap x ldq
-  double* EtM = nullptr; // S_cap x ldq : rows N.. of M M_rs, then B_s^T
+  // N x w blocks in the step's storage type (double for FP64, float for MIXED)
+  size_t esz = 8;
+  void* Zv = nullptr;    // n_cap x ldz : [X_bar | W | B/R] -> [X_bar | Q]
+  void* MZv = nullptr;   // n_cap x ldz : [Y1 | MQ]
+  void* V2v = nullptr;   // n_cap x ldv : CholQR staging
+  void* Yrv = nullptr;   // n_cap x ldq : RSVD sketch / basis
+  void* Yr2v = nullptr;  // n_cap x ldq
+  void* Omv = nullptr;   // S_cap x ldq
+  void* EtMv = nullptr;  // S_cap x ldq : rows N.. of M M_rs, then B_s^T
   int64_t S_cap = 0;
-  double* Id = nullptr;  // q x q identity (exact new-node block)
+  void* Idv = nullptr;   // q x q identity (exact new-node block)
+  float* U32 = nullptr;  // mixed path: Ritz vectors before the FP64 refinement (n_cap x ldu)
+  double* Rres = nullptr;  // residual vectors for GREST_FLAG_CHECK (n_cap x ldu)
   double *Cm = nullptr, *Cv = nullptr, *G = nullptr, *T = nullptr, *H = nullptr, *F = nullptr, *XtM = nullptr,
          *Gs = nullptr, *Uh = nullptr, *ritz = nullptr, *th_new = nullptr, *tmpk = nullptr;
   double* info = nullptr;  // device diagnostics [64]
@@ -129,7 +133,8 @@ void free_ctx(grest_ctx* c) {
                   c->g.arena_top, c->g.dmax, c->gw.cnt, c->gw.seg, c->gw.cursor, c->gw.delflag, c->gw.rowflag,
                   c->gw.touched, c->gw.tmp_off, c->gw.need, c->gw.new_len, c->gw.ekey, c->gw.erow, c->gw.ew,
                   c->gw.eins, c->gw.tmp_col, c->gw.tmp_val, c->gw.long_rows, c->gw.scalars, c->gw.scan_tmp,
-                  c->U, c->Un, c->theta, c->Z, c->MZ, c->V2, c->Yr, c->Yr2, c->Om, c->EtM, c->Id, c->Cm, c->Cv,
+                  c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
+                  c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
                   c->ipart, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
@@ -187,10 +192,10 @@ grest_status ensure_graph_work(grest_ctx* c, int64_t entries) {
 grest_status ensure_S(grest_ctx* c, int64_t S) {
   if (S <= c->S_cap) return GREST_OK;
   int64_t cap = std::max<int64_t>(S, 2 * c->S_cap);
-  cudaFree(c->Om); cudaFree(c->EtM);
-  c->Om = c->EtM = nullptr;
-  CK(dalloc(&c->Om, cap * c->ldq));
-  CK(dalloc(&c->EtM, cap * c->ldq));
+  cudaFree(c->Omv); cudaFree(c->EtMv);
+  c->Omv = c->EtMv = nullptr;
+  CK(cudaMalloc(&c->Omv, c->esz * cap * c->ldq));
+  CK(cudaMalloc(&c->EtMv, c->esz * cap * c->ldq));
   c->S_cap = cap;
   return GREST_OK;
 }
@@ -244,23 +249,51 @@ OpParams op_params(const grest_ctx* c) {
   return p;
 }
 
+// ---------------------------------------------------------------- typed launch wrappers
 // nnz_proc: entries of the processed rows that take part (all of them, or the
 // new-node block); x_rows: rows of X read at least once
-void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
-          int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
-  int p = prof_begin(c);
-  spmm_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+void prof_spmm(grest_ctx* c, int p, int w, int64_t r0, int64_t r1, int64_t col_lo, int64_t nnz_proc, int64_t x_rows,
+               double xbytes, double ybytes) {
   if (r1 > r0 && w > 0) c->launches += col_lo == 0 ? 2 : 1;
   if (nnz_proc < 0) nnz_proc = c->nnz;
   if (x_rows < 0) x_rows = r1 - r0;
   const double eb = c->g.val ? 12.0 : 4.0;
-  prof_end(c, p, 0, 12.0 * (r1 - r0) + eb * nnz_proc + 8.0 * w * ((r1 - r0) + x_rows));
+  prof_end(c, p, 0, 12.0 * (r1 - r0) + eb * nnz_proc + w * (ybytes * (r1 - r0) + xbytes * x_rows));
+}
+
+void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
+          int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
+  int p = prof_begin(c);
+  spmm_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 8.0, 8.0);
+}
+
+void spmm(grest_ctx* c, const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
+          int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
+  int p = prof_begin(c);
+  spmm_f32(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 4.0);
+}
+
+void spmm(grest_ctx* c, const float* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
+          int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
+  int p = prof_begin(c);
+  spmm_f32_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 8.0);
 }
 
 void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
           double* C, int64_t ldc, bool sym) {
   int p = prof_begin(c);
   gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+  if (a > 0 && b > 0 && n > 0) c->launches += 2;
+  prof_end(c, p, 1, 2.0 * n * a * b);
+}
+
+void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+          int64_t ldc, bool sym) {
+  int p = prof_begin(c);
+  gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
   prof_end(c, p, 1, 2.0 * n * a * b);
 }
@@ -273,6 +306,14 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X,
   prof_end(c, p, 2, 2.0 * n * a * cc);
 }
 
+void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, int64_t ldx, const double* B,
+          int64_t ldb, double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo) {
+  int p = prof_begin(c);
+  gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
+  if (n > 0 && cc > 0) c->launches += 1;
+  prof_end(c, p, 2, 2.0 * n * a * cc);
+}
+
 void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf,
          double* ritz, double* info) {
   int p = prof_begin(c);
@@ -281,16 +322,35 @@ void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* thet
   prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
-// X (n x w) <- P_perp X = X - U (U^T X), U = first ku columns of Z
-void project_out(grest_ctx* c, double* X, int64_t ldx, int w, int64_t n) {
+template <typename T>
+T* Zp(grest_ctx* c) { return static_cast<T*>(c->Zv); }
+template <typename T>
+T* MZp(grest_ctx* c) { return static_cast<T*>(c->MZv); }
+template <typename T>
+T* V2p(grest_ctx* c) { return static_cast<T*>(c->V2v); }
+template <typename T>
+T* Yrp(grest_ctx* c) { return static_cast<T*>(c->Yrv); }
+template <typename T>
+T* Yr2p(grest_ctx* c) { return static_cast<T*>(c->Yr2v); }
+template <typename T>
+T* Omp(grest_ctx* c) { return static_cast<T*>(c->Omv); }
+template <typename T>
+T* EtMp(grest_ctx* c) { return static_cast<T*>(c->EtMv); }
+template <typename T>
+T* Idp(grest_ctx* c) { return static_cast<T*>(c->Idv); }
+
+// X (n x w) <- P_perp X = X - U (U^T X), U = first Ku columns of Z
+template <typename T>
+void project_out(grest_ctx* c, T* X, int64_t ldx, int w, int64_t n) {
   if (c->Ku == 0 || w == 0) return;
-  gram(c, c->Z, c->ldz, c->Ku, X, ldx, w, n, c->Cv, w, false);
-  gemm(c, n, c->Ku, w, -1.0, c->Z, c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx);
+  gram(c, Zp<T>(c), c->ldz, c->Ku, X, ldx, w, n, c->Cv, w, false);
+  gemm(c, n, c->Ku, w, -1.0, Zp<T>(c), c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx);
 }
 
 // CholQR with pivoting: Out (n x rank) = X (n x w) T; returns rank via info slot
-grest_status cholqr_pass(grest_ctx* c, const double* X, int64_t ldx, int w, int64_t n, double tol, double abs_ref,
-                         const double* abs_ref_ptr, double* Out, int64_t ldo, int info_slot, bool read_rank,
+template <typename T>
+grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n, double tol, double abs_ref,
+                         const double* abs_ref_ptr, T* Out, int64_t ldo, int info_slot, bool read_rank,
                          int* rank_out) {
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
   int p = prof_begin(c);
@@ -303,21 +363,23 @@ grest_status cholqr_pass(grest_ctx* c, const double* X, int64_t ldx, int w, int6
     if (st != GREST_OK) return st;
     rank = (int)c->h_info[info_slot];
   }
-  if (rank > 0) gemm(c, n, w, rank, 1.0, X, ldx, c->T, w, 0.0, nullptr, 0, Out, ldo);
+  if (rank > 0) gemm(c, n, w, rank, 1.0, X, ldx, c->T, w, 0.0, static_cast<const T*>(nullptr), 0, Out, ldo);
   if (rank_out) *rank_out = rank;
   return GREST_OK;
 }
 
-__global__ void k_fill_identity(double* I, int64_t ld, int q) {
+template <typename T>
+__global__ void k_fill_identity(T* I, int64_t ld, int q) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < (int64_t)q * q) I[(e / q) * ld + (e % q)] = (e / q == e % q) ? 1.0 : 0.0;
+  if (e < (int64_t)q * q) I[(e / q) * ld + (e % q)] = (e / q == e % q) ? (T)1 : (T)0;
 }
 
-__global__ void k_pad_copy(const double* U, int64_t ldu, double* Z, int64_t ldz, int64_t N, int64_t N2, int K) {
+template <typename T>
+__global__ void k_pad_copy(const double* U, int64_t ldu, T* Z, int64_t ldz, int64_t N, int64_t N2, int K) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N2 * K; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e / K;
     int c = (int)(e % K);
-    Z[r * ldz + c] = r < N ? U[r * ldu + c] : 0.0;
+    Z[r * ldz + c] = r < N ? (T)U[r * ldu + c] : (T)0;
   }
 }
 
@@ -376,45 +438,107 @@ __global__ void k_maxabs(const double* A, int64_t ld, int rows, int cols, double
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// Small k x k products for the refinement: Hs = T^T H T, and F' = T F.
+__global__ void k_small_tht(const double* T, const double* H, int k, double* HT, double* out) {
+  // HT = H T, then out = T^T HT (one block, k <= 64)
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s = fma(H[i * k + l], T[l * k + j], s);
+    HT[i * k + j] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s = fma(T[l * k + i], HT[l * k + j], s);
+    out[i * k + j] = s;
+  }
+}
+
+__global__ void k_small_mm(const double* A, const double* B, int k, double* out) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s = fma(A[i * k + l], B[l * k + j], s);
+    out[i * k + j] = s;
+  }
+}
+
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
   return ms;
 }
 
-grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, bool removed) {
+// Mixed path, A11: FP64 Rayleigh-Ritz in span(U32).  With G = U^T U, the
+// pivoted Cholesky gives T with (U T)^T (U T) = I; the K x K problem
+// T^T (U^T M U) T F'' = F'' Theta is solved in FP64 and X = U (T F'').  The
+// products with U read its exact FP32 values and accumulate in FP64.
+grest_status refine_mixed(grest_ctx* c, int64_t N2) {
+  cudaStream_t s = c->stream;
+  const int K = c->K;
+  double* U64 = c->Un;  // exact FP64 copy of the FP32 Ritz vectors
+  convert_f32_to_f64(c->U32, c->ldu, U64, c->ldu, N2, K, s);
+  c->launches += 1;
+  gram(c, U64, c->ldu, K, U64, c->ldu, K, N2, c->G, K, true);
+  double* MU = c->U;  // the previous embedding is no longer needed
+  spmm(c, c->U32, c->ldu, MU, c->ldu, K, 0, N2, 0);
+  gram(c, U64, c->ldu, K, MU, c->ldu, K, N2, c->H, K, false);
+  int p = prof_begin(c);
+  pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
+  k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
+  symmetrize(c->Uh, K, K, s);
+  c->launches += 3;
+  prof_end(c, p, 3, 4.0 * K * K * K);
+  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48);
+  k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
+  c->launches += 1;
+  gemm(c, N2, K, K, 1.0, U64, c->ldu, c->Gs, K, 0.0, static_cast<const double*>(nullptr), 0, c->U, c->ldu);
+  sign_normalize(c->U, c->ldu, K, N2, c->part, c->ipart, s);
+  c->launches += 3;
+  CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+  return GREST_OK;
+}
+
+template <typename T>
+grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   const int64_t N2 = N + S;
   cudaStream_t s = c->stream;
   const int K = c->K;
   Csr& g = c->g;
+  T* Z = Zp<T>(c);
+  T* MZ = MZp<T>(c);
+  T* V2 = V2p<T>(c);
+  const int64_t ldz = c->ldz, ldv = c->ldv, ldq = c->ldq;
   CK(cudaEventRecord(c->ev[1], s));
   // A2: X_bar = [X; 0]; removed nodes: zero their rows and re-orthonormalize (reading of node removal)
-  k_pad_copy<<<1024, 256, 0, s>>>(c->U, c->ldu, c->Z, c->ldz, N, N2, c->Ku);
+  k_pad_copy<T><<<1024, 256, 0, s>>>(c->U, c->ldu, Z, ldz, N, N2, c->Ku);
   c->launches += 1;
   if (removed) {
-    zero_dead_rows(c->Z, c->ldz, c->Ku, g.live, N2, s);
+    zero_dead_rows(Z, ldz, c->Ku, g.live, N2, s);
     c->launches += 1;
     int r1 = 0;
-    grest_status st = cholqr_pass(c, c->Z, c->ldz, c->Ku, N2, c->cfg.drop_tol, 1.0, nullptr, c->V2, c->ldv, 0, true, &r1);
+    grest_status st = cholqr_pass(c, Z, ldz, c->Ku, N2, c->cfg.drop_tol, 1.0, nullptr, V2, ldv, 0, true, &r1);
     if (st != GREST_OK) return st;
     int r2 = 0;
-    st = cholqr_pass(c, c->V2, c->ldv, r1, N2, 1e-14, 0.0, nullptr, c->Z, c->ldz, 4, false, &r2);
+    st = cholqr_pass(c, V2, ldv, r1, N2, 1e-14, 0.0, nullptr, Z, ldz, 4, false, &r2);
     if (st != GREST_OK) return st;
     c->Ku = r1;
   }
   const int Ku = c->Ku;
   // A3: Y1 = M X_bar
-  spmm(c, c->Z, c->ldz, c->MZ, c->ldz, Ku, 0, N2, 0);
+  spmm(c, Z, ldz, MZ, ldz, Ku, 0, N2, 0);
   CK(cudaEventRecord(c->ev[2], s));
   // A4: C = X_bar^T Y1; W = Y1 - X_bar C, re-projected once
-  double* W = c->Z + Ku;
-  gram(c, c->Z, c->ldz, Ku, c->MZ, c->ldz, Ku, N2, c->Cm, Ku, false);
-  gemm(c, N2, Ku, Ku, -1.0, c->Z, c->ldz, c->Cm, Ku, 1.0, c->MZ, c->ldz, W, c->ldz);
-  project_out(c, W, c->ldz, Ku, N2);
+  T* W = Z + Ku;
+  gram(c, Z, ldz, Ku, MZ, ldz, Ku, N2, c->Cm, Ku, false);
+  gemm(c, N2, Ku, Ku, -1.0, Z, ldz, c->Cm, Ku, 1.0, MZ, ldz, W, ldz);
+  project_out(c, W, ldz, Ku, N2);
   // A5: new-node block
   int cb = 0;
   int mode = 2;
-  double* B = c->Z + 2 * Ku;
+  T* B = Z + 2 * Ku;
   const int q = c->q;
   if (S > 0 && c->cfg.subspace != GREST_SUB_GREST2) {
     bool rsvd = c->cfg.subspace == GREST_SUB_RSVD || (c->cfg.subspace == GREST_SUB_AUTO && S > q);
@@ -422,38 +546,42 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
       if (S > q) return GREST_ERR_UNSUPPORTED;  // exact block wider than the basis buffers
       mode = 3;
       // E = M_new[:, N:N2] = M_new * [0; I_S] (restricted SpMM against the identity)
-      spmm(c, c->Id, c->ldq, B, c->ldz, (int)S, 0, N2, N, c->batch_new_edges + S, S);
-      project_out(c, B, c->ldz, (int)S, N2);
+      spmm(c, Idp<T>(c), ldq, B, ldz, (int)S, 0, N2, N, c->batch_new_edges + S, S);
+      project_out(c, B, ldz, (int)S, N2);
       cb = (int)S;
     } else {
       mode = 4;
       grest_status st = ensure_S(c, S);
       if (st != GREST_OK) return st;
+      T* Yr = Yrp<T>(c);
+      T* Yr2 = Yr2p<T>(c);
+      T* Om = Omp<T>(c);
+      T* EtM = EtMp<T>(c);
       // S.1: Y = P_perp Delta_2 Omega
-      gaussian_omega(c->Om, c->ldq, S, q, c->cfg.seed, (uint64_t)c->step, s);
+      gaussian_omega(Om, ldq, S, q, c->cfg.seed, (uint64_t)c->step, s);
       c->launches += 1;
-      spmm(c, c->Om, c->ldq, c->Yr, c->ldq, q, 0, N2, N, c->batch_new_edges + S, S);
-      project_out(c, c->Yr, c->ldq, q, N2);
-      project_out(c, c->Yr, c->ldq, q, N2);
+      spmm(c, Om, ldq, Yr, ldq, q, 0, N2, N, c->batch_new_edges + S, S);
+      project_out(c, Yr, ldq, q, N2);
+      project_out(c, Yr, ldq, q, N2);
       // M = orth(Y): CholQR2 with pivoting
       int rY = 0;
-      st = cholqr_pass(c, c->Yr, c->ldq, q, N2, c->cfg.drop_tol, 0.0, c->theta, c->Yr2, c->ldq, 8, true, &rY);
+      st = cholqr_pass(c, Yr, ldq, q, N2, c->cfg.drop_tol, 0.0, c->theta, Yr2, ldq, 8, true, &rY);
       if (st != GREST_OK) return st;
       int rY2 = 0;
-      st = cholqr_pass(c, c->Yr2, c->ldq, rY, N2, 1e-14, 0.0, nullptr, c->Yr, c->ldq, 12, false, &rY2);
+      st = cholqr_pass(c, Yr2, ldq, rY, N2, 1e-14, 0.0, nullptr, Yr, ldq, 12, false, &rY2);
       if (st != GREST_OK) return st;
       c->stats.rank_y = rY;
       if (rY > 0) {
         // S.2: B_s^T = Delta_2^T M - (Delta_2^T X_bar)(X_bar^T M), Delta_2^T X_bar = Y1[N:N2]
-        spmm(c, c->Yr, c->ldq, c->EtM, c->ldq, rY, N, N2, 0, c->batch_new_edges + S, N2);
-        gram(c, c->Z, c->ldz, Ku, c->Yr, c->ldq, rY, N2, c->XtM, rY, false);
-        gemm(c, S, Ku, rY, -1.0, c->MZ + N * c->ldz, c->ldz, c->XtM, rY, 1.0, c->EtM, c->ldq, c->EtM, c->ldq);
+        spmm(c, Yr, ldq, EtM, ldq, rY, N, N2, 0, c->batch_new_edges + S, N2);
+        gram(c, Z, ldz, Ku, Yr, ldq, rY, N2, c->XtM, rY, false);
+        gemm(c, S, Ku, rY, -1.0, MZ + N * ldz, ldz, c->XtM, rY, 1.0, EtM, ldq, EtM, ldq);
         // left singular vectors of B_s via eig(B_s B_s^T), L leading
-        gram(c, c->EtM, c->ldq, rY, c->EtM, c->ldq, rY, S, c->Gs, rY, true);
+        gram(c, EtM, ldq, rY, EtM, ldq, rY, S, c->Gs, rY, true);
         const int Lp = std::min(c->Lr, rY);
         eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16);
         // S.4: R = M U_hat
-        gemm(c, N2, rY, Lp, 1.0, c->Yr, c->ldq, c->Uh, Lp, 0.0, nullptr, 0, B, c->ldz);
+        gemm(c, N2, rY, Lp, 1.0, Yr, ldq, c->Uh, Lp, 0.0, static_cast<const T*>(nullptr), 0, B, ldz);
         cb = Lp;
       }
     }
@@ -461,26 +589,26 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
   CK(cudaEventRecord(c->ev[3], s));
   // A6: Q = orth(P_perp [W, B]) by CholQR2 with pivoting (partial orthogonality: X_bar is fixed)
   int cw = Ku + cb;
-  double* V = c->Z + Ku;
-  project_out(c, V, c->ldz, cw, N2);
+  T* V = Z + Ku;
+  project_out(c, V, ldz, cw, N2);
   int r = 0;
-  grest_status st = cholqr_pass(c, V, c->ldz, cw, N2, c->cfg.drop_tol, 0.0, c->theta, c->V2, c->ldv, 20, true, &r);
+  grest_status st = cholqr_pass(c, V, ldz, cw, N2, c->cfg.drop_tol, 0.0, c->theta, V2, ldv, 20, true, &r);
   if (st != GREST_OK) return st;
   c->stats.pivot_kept_min = c->h_info[21];
   c->stats.pivot_dropped_max = c->h_info[22];
   if (r > 0) {
-    project_out(c, c->V2, c->ldv, r, N2);
+    project_out(c, V2, ldv, r, N2);
     int r2 = 0;
-    st = cholqr_pass(c, c->V2, c->ldv, r, N2, 1e-14, 0.0, nullptr, V, c->ldz, 24, false, &r2);
+    st = cholqr_pass(c, V2, ldv, r, N2, 1e-14, 0.0, nullptr, V, ldz, 24, false, &r2);
     if (st != GREST_OK) return st;
   }
   const int m = Ku + r;
   if (m < K) return GREST_ERR_NUMERIC;
   // A7: MQ = M Q
-  if (r > 0) spmm(c, V, c->ldz, c->MZ + Ku, c->ldz, r, 0, N2, 0);
+  if (r > 0) spmm(c, V, ldz, MZ + Ku, ldz, r, 0, N2, 0);
   CK(cudaEventRecord(c->ev[4], s));
   // A8: H = Z^T (M Z) (Eq. main2), symmetrized
-  gram(c, c->Z, c->ldz, m, c->MZ, c->ldz, m, N2, c->H, m, false);
+  gram(c, Z, ldz, m, MZ, ldz, m, N2, c->H, m, false);
   symmetrize(c->H, m, m, s);
   c->launches += 1;
   CK(cudaEventRecord(c->ev[5], s));
@@ -488,13 +616,23 @@ grest_status fp64_step(grest_ctx* c, const BatchDev& bd, int64_t N, int64_t S, b
   eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28);
   CK(cudaEventRecord(c->ev[6], s));
   // A10: X = Z F_K, sign normalization
-  gemm(c, N2, m, K, 1.0, c->Z, c->ldz, c->F, K, 0.0, nullptr, 0, c->Un, c->ldu);
-  sign_normalize(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
-  c->launches += 3;
-  CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
-  std::swap(c->U, c->Un);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    gemm(c, N2, m, K, 1.0, Z, ldz, c->F, K, 0.0, static_cast<const T*>(nullptr), 0, c->Un, c->ldu);
+    sign_normalize(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
+    c->launches += 3;
+    CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+    std::swap(c->U, c->Un);
+    CK(cudaEventRecord(c->ev[7], s));
+    CK(cudaEventRecord(c->ev[8], s));
+  } else {
+    gemm(c, N2, m, K, 1.0, Z, ldz, c->F, K, 0.0, static_cast<const T*>(nullptr), 0, c->U32, c->ldu);
+    CK(cudaEventRecord(c->ev[7], s));
+    // A11: FP64 refinement
+    grest_status st2 = refine_mixed(c, N2);
+    if (st2 != GREST_OK) return st2;
+    CK(cudaEventRecord(c->ev[8], s));
+  }
   c->Ku = K;
-  CK(cudaEventRecord(c->ev[7], s));
   c->stats.m = m;
   c->stats.k_u = Ku;
   c->stats.rank_q = r;
@@ -507,17 +645,23 @@ grest_status run_checks(grest_ctx* c, int64_t n) {
   // M U, residual norms, orthonormality and Galerkin residual, in FP64
   cudaStream_t s = c->stream;
   const int K = c->K;
-  double* MU = c->Un;  // free after the swap; same leading dimension as U
+  double* MU = c->Un;  // free after the step; same leading dimension as U
   spmm(c, c->U, c->ldu, MU, c->ldu, K, 0, n, 0);
   residual_norms(MU, c->U, c->ldu, K, c->theta, n, c->part, c->resn, s);
   gram(c, c->U, c->ldu, K, c->U, c->ldu, K, n, c->Cm, K, true);
   k_orth_err<<<1, 256, 0, s>>>(c->Cm, K, K, c->info + 36);
   c->launches += 3;  // residual_norms (2) + k_orth_err
-  // R = MU - U theta (ldv >= K), Galerkin residual Z^T R
-  double* R = c->V2;
-  k_resid_vecs<<<1024, 256, 0, s>>>(MU, c->U, c->ldu, K, c->theta, n, R, c->ldv);
-  gram(c, c->Z, c->ldz, c->last_m, R, c->ldv, K, n, c->H, K, false);
-  k_maxabs<<<1, 256, 0, s>>>(c->H, K, c->last_m, K, c->info + 37);
+  // R = MU - U theta, Galerkin residual: Z^T R for the FP64 path (Z = [X_bar, Q]),
+  // U^T R for the mixed path (its last Rayleigh-Ritz runs in span(U))
+  double* R = c->Rres;
+  k_resid_vecs<<<1024, 256, 0, s>>>(MU, c->U, c->ldu, K, c->theta, n, R, c->ldu);
+  if (c->cfg.precision == GREST_FP64) {
+    gram(c, Zp<double>(c), c->ldz, c->last_m, R, c->ldu, K, n, c->H, K, false);
+    k_maxabs<<<1, 256, 0, s>>>(c->H, K, c->last_m, K, c->info + 37);
+  } else {
+    gram(c, c->U, c->ldu, K, R, c->ldu, K, n, c->H, K, false);
+    k_maxabs<<<1, 256, 0, s>>>(c->H, K, K, K, c->info + 37);
+  }
   c->launches += 2;  // k_resid_vecs + k_maxabs
   return GREST_OK;
 }
@@ -565,7 +709,8 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   if (cfg->k < 1 || cfg->k > 64 || cfg->op < 0 || cfg->op > 2 || cfg->L < 1 || cfg->P < 0 || cfg->L + cfg->P > 256 ||
       cfg->subspace < 0 || cfg->subspace > 3 || !(cfg->drop_tol > 0.0) || cfg->k > n)
     return GREST_ERR_INVALID_ARG;
-  if (cfg->precision != GREST_FP64 || cfg->projection != GREST_PROJ_EXACT || cfg->w_block != GREST_WB_RESID)
+  if ((cfg->precision != GREST_FP64 && cfg->precision != GREST_MIXED) || cfg->projection != GREST_PROJ_EXACT ||
+      cfg->w_block != GREST_WB_RESID)
     return GREST_ERR_UNSUPPORTED;
   if (!U0 || !theta0) return GREST_ERR_UNSUPPORTED;
   const int64_t nnz = rowptr[n];
@@ -652,9 +797,13 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
     if (ensure_batch(c, mb, 1024) != GREST_OK) { free_ctx(c); return GREST_ERR_OOM; }
   }
   IK(dalloc(&c->U, nc * c->ldu)); IK(dalloc(&c->Un, nc * c->ldu)); IK(dalloc(&c->theta, 64));
-  IK(dalloc(&c->Z, nc * c->ldz)); IK(dalloc(&c->MZ, nc * c->ldz)); IK(dalloc(&c->V2, nc * c->ldv));
-  IK(dalloc(&c->Yr, nc * c->ldq)); IK(dalloc(&c->Yr2, nc * c->ldq));
-  IK(dalloc(&c->Id, (int64_t)c->q * c->ldq));
+  c->esz = cfg->precision == GREST_MIXED ? sizeof(float) : sizeof(double);
+  IK(cudaMalloc(&c->Zv, c->esz * nc * c->ldz)); IK(cudaMalloc(&c->MZv, c->esz * nc * c->ldz));
+  IK(cudaMalloc(&c->V2v, c->esz * nc * c->ldv));
+  IK(cudaMalloc(&c->Yrv, c->esz * nc * c->ldq)); IK(cudaMalloc(&c->Yr2v, c->esz * nc * c->ldq));
+  IK(cudaMalloc(&c->Idv, c->esz * (int64_t)c->q * c->ldq));
+  if (cfg->precision == GREST_MIXED) IK(dalloc(&c->U32, nc * c->ldu));
+  if (cfg->flags & GREST_FLAG_CHECK) IK(dalloc(&c->Rres, nc * c->ldu));
   const int cm = c->cmax, mm = c->mmax;
   IK(dalloc(&c->Cm, 64 * 64)); IK(dalloc(&c->Cv, (int64_t)64 * (cm + 64))); IK(dalloc(&c->G, (int64_t)cm * cm));
   IK(dalloc(&c->T, (int64_t)cm * cm)); IK(dalloc(&c->H, (int64_t)mm * mm)); IK(dalloc(&c->F, (int64_t)mm * 64));
@@ -691,7 +840,10 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
     IK(cudaMemcpyAsync(c->theta, theta0, sizeof(double) * c->K, cudaMemcpyHostToDevice, s));
     IK(cudaStreamSynchronize(s));
   }
-  k_fill_identity<<<(unsigned)((c->q * c->q + 255) / 256), 256, 0, s>>>(c->Id, c->ldq, c->q);
+  if (c->esz == sizeof(double))
+    k_fill_identity<double><<<(unsigned)((c->q * c->q + 255) / 256), 256, 0, s>>>(static_cast<double*>(c->Idv), c->ldq, c->q);
+  else
+    k_fill_identity<float><<<(unsigned)((c->q * c->q + 255) / 256), 256, 0, s>>>(static_cast<float*>(c->Idv), c->ldq, c->q);
   (void)graph_refresh_derived(g, w, n, s);
   IK(cudaGetLastError());
   IK(cudaStreamSynchronize(s));
@@ -774,12 +926,13 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   c->g.n = N + S;
   c->launches += graph_refresh_derived(c->g, c->gw, N + S, s);
   c->stats.rank_y = 0;
-  st = fp64_step(c, bd, N, S, u->n_del_nodes > 0);
+  st = c->cfg.precision == GREST_MIXED ? step_t<float>(c, N, S, u->n_del_nodes > 0)
+                                       : step_t<double>(c, N, S, u->n_del_nodes > 0);
   CK(cudaGetLastError());
   if (st != GREST_OK) return st;
   ++c->step;
   if (c->cfg.flags & GREST_FLAG_CHECK) run_checks(c, N + S);
-  CK(cudaMemcpyAsync(c->h_info, c->info, sizeof(double) * 48, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_info, c->info, sizeof(double) * 64, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->h_scal, c->g.arena_top, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   c->last_ritz.resize(c->last_m);
   CK(cudaMemcpyAsync(c->last_ritz.data(), c->ritz, sizeof(double) * c->last_m, cudaMemcpyDeviceToHost, s));
@@ -806,13 +959,14 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
     S_.max_residual = th1 > 0 ? mr / th1 : mr;
     S_.galerkin = th1 > 0 ? c->h_info[37] / th1 : c->h_info[37];
   }
-  S_.ms_total = ev_ms(c->ev[0], c->ev[7]);
+  S_.ms_total = ev_ms(c->ev[0], c->ev[8]);
   S_.ms_graph = ev_ms(c->ev[0], c->ev[1]);
   S_.ms_spmm = ev_ms(c->ev[1], c->ev[2]);
   S_.ms_basis = ev_ms(c->ev[2], c->ev[4]);
   S_.ms_project = ev_ms(c->ev[4], c->ev[5]);
   S_.ms_eig = ev_ms(c->ev[5], c->ev[6]);
   S_.ms_lift = ev_ms(c->ev[6], c->ev[7]);
+  S_.ms_refine = ev_ms(c->ev[7], c->ev[8]);
   if (stats) *stats = S_;
   return GREST_OK;
 }

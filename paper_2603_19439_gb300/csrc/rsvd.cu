@@ -50,7 +50,8 @@ __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, d
   z1 = r * sn;
 }
 
-__global__ void k_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step) {
+template <typename T>
+__global__ void k_omega(T* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step) {
   const int64_t total = S * q;
   const int64_t nblk = (total + 3) / 4;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
@@ -62,19 +63,26 @@ __global__ void k_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed,
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       int64_t e = 4 * b + t;
-      if (e < total) Om[(e / q) * ld + (e % q)] = z[t];
+      if (e < total) Om[(e / q) * ld + (e % q)] = (T)z[t];
     }
   }
 }
 
 }  // namespace
 
-void gaussian_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s) {
+template <typename T>
+void gaussian_omega_t(T* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s) {
   int64_t nblk = (S * q + 3) / 4;
   if (nblk <= 0) return;
   int64_t g = (nblk + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  k_omega<<<(unsigned)g, 256, 0, s>>>(Om, ld, S, q, seed, step);
+  k_omega<T><<<(unsigned)g, 256, 0, s>>>(Om, ld, S, q, seed, step);
+}
+void gaussian_omega(double* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s) {
+  gaussian_omega_t(Om, ld, S, q, seed, step, s);
+}
+void gaussian_omega(float* Om, int64_t ld, int64_t S, int q, uint64_t seed, uint64_t step, cudaStream_t s) {
+  gaussian_omega_t(Om, ld, S, q, seed, step, s);
 }
 
 }  // namespace grest

@@ -23,9 +23,9 @@ struct Acc {
   T v[NCH];
 };
 
-template <typename T, int NCH, bool HASVAL>
+template <typename Tx, typename T, int NCH, bool HASVAL>
 __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, const double* __restrict__ val,
-                                             int64_t beg, int64_t end, const OpParams& op, const T* __restrict__ X,
+                                             int64_t beg, int64_t end, const OpParams& op, const Tx* __restrict__ X,
                                              int64_t ldx, int w, int64_t col_lo, int lane, Acc<T, NCH>& acc) {
   const bool nl = op.op == GREST_OP_NLAP;
   for (int64_t j0 = beg; j0 < end; j0 += 32) {
@@ -45,15 +45,15 @@ __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, co
       int32_t c2 = __shfl_sync(0xffffffffu, mc, k + 2), c3 = __shfl_sync(0xffffffffu, mc, k + 3);
       T a0 = __shfl_sync(0xffffffffu, ma, k), a1 = __shfl_sync(0xffffffffu, ma, k + 1);
       T a2 = __shfl_sync(0xffffffffu, ma, k + 2), a3 = __shfl_sync(0xffffffffu, ma, k + 3);
-      const T* x0 = X + (int64_t)(c0 - col_lo) * ldx;
-      const T* x1 = X + (int64_t)(c1 - col_lo) * ldx;
-      const T* x2 = X + (int64_t)(c2 - col_lo) * ldx;
-      const T* x3 = X + (int64_t)(c3 - col_lo) * ldx;
+      const Tx* x0 = X + (int64_t)(c0 - col_lo) * ldx;
+      const Tx* x1 = X + (int64_t)(c1 - col_lo) * ldx;
+      const Tx* x2 = X + (int64_t)(c2 - col_lo) * ldx;
+      const Tx* x3 = X + (int64_t)(c3 - col_lo) * ldx;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
         int c = ch * 32 + lane;
         if (c < w) {
-          T y0 = __ldg(x0 + c), y1 = __ldg(x1 + c), y2 = __ldg(x2 + c), y3 = __ldg(x3 + c);
+          T y0 = (T)__ldg(x0 + c), y1 = (T)__ldg(x1 + c), y2 = (T)__ldg(x2 + c), y3 = (T)__ldg(x3 + c);
           acc.v[ch] += a0 * y0 + a1 * y1 + a2 * y2 + a3 * y3;
         }
       }
@@ -61,11 +61,11 @@ __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, co
     for (; k < cnt; ++k) {
       int32_t c0 = __shfl_sync(0xffffffffu, mc, k);
       T a0 = __shfl_sync(0xffffffffu, ma, k);
-      const T* x0 = X + (int64_t)(c0 - col_lo) * ldx;
+      const Tx* x0 = X + (int64_t)(c0 - col_lo) * ldx;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
         int c = ch * 32 + lane;
-        if (c < w) acc.v[ch] += a0 * __ldg(x0 + c);
+        if (c < w) acc.v[ch] += a0 * (T)__ldg(x0 + c);
       }
     }
   }
@@ -87,10 +87,10 @@ __device__ __forceinline__ void diag_terms(const OpParams& op, int64_t r, double
   else if (op.op == GREST_OP_NLAP) { dcoef = 1.0; scale = op.dis[r]; }
 }
 
-template <typename T, int NCH, bool HASVAL>
+template <typename Tx, typename T, int NCH, bool HASVAL>
 __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
-                                                   OpParams op, const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                   OpParams op, const Tx* __restrict__ X, int64_t ldx, T* __restrict__ Y,
                                                    int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -112,17 +112,17 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ r
     Acc<T, NCH> acc;
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) acc.v[ch] = 0;
-    gather_range<T, NCH, HASVAL>(col, val, s, end, op, X, ldx, w, col_lo, lane, acc);
+    gather_range<Tx, T, NCH, HASVAL>(col, val, s, end, op, X, ldx, w, col_lo, lane, acc);
     double dcoef, scale;
     diag_terms(op, r, dcoef, scale);
     const bool has_diag = dcoef != 0.0 && r >= col_lo;
-    const T* xr = X + (r - col_lo) * ldx;
+    const Tx* xr = X + (r - col_lo) * ldx;
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
       int c = ch * 32 + lane;
       if (c < w) {
         T y = (T)scale * acc.v[ch];
-        if (has_diag) y += (T)dcoef * xr[c];
+        if (has_diag) y += (T)dcoef * (T)xr[c];
         yr[c] = y;
       }
     }
@@ -130,11 +130,11 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ r
 }
 
 // one block (8 warps) per long row; fixed-order reduction in shared memory
-template <typename T, int NCH, bool HASVAL>
+template <typename Tx, typename T, int NCH, bool HASVAL>
 __global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                                    OpParams op, const int32_t* __restrict__ rows,
-                                                   const int64_t* __restrict__ n_rows, const T* __restrict__ X,
+                                                   const int64_t* __restrict__ n_rows, const Tx* __restrict__ X,
                                                    int64_t ldx, T* __restrict__ Y, int64_t ldy, int w, int64_t r0,
                                                    int64_t r1) {
   __shared__ T part[8][NCH * 32];
@@ -155,27 +155,27 @@ __global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ r
     Acc<T, NCH> acc;
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) acc.v[ch] = 0;
-    if (s < e) gather_range<T, NCH, HASVAL>(col, val, s, e, op, X, ldx, w, 0, lane, acc);
+    if (s < e) gather_range<Tx, T, NCH, HASVAL>(col, val, s, e, op, X, ldx, w, 0, lane, acc);
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) part[wid][ch * 32 + lane] = acc.v[ch];
     __syncthreads();
     double dcoef, scale;
     diag_terms(op, r, dcoef, scale);
-    const T* xr = X + r * ldx;
+    const Tx* xr = X + r * ldx;
     for (int c = threadIdx.x; c < w; c += blockDim.x) {
       T sum = 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) sum += part[q][c];
       T y = (T)scale * sum;
-      if (dcoef != 0.0) y += (T)dcoef * xr[c];
+      if (dcoef != 0.0) y += (T)dcoef * (T)xr[c];
       yr[c] = y;
     }
     __syncthreads();
   }
 }
 
-template <typename T, int NCH>
-void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const T* X,
+template <typename Tx, typename T, int NCH>
+void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const Tx* X,
                 int64_t ldx, T* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo, cudaStream_t s) {
   const int64_t rows = r1 - r0;
   int64_t blocks = (rows + 7) / 8;
@@ -183,34 +183,34 @@ void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, cons
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   if (g.val) {
-    k_spmm_rows<T, NCH, true><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, X, ldx, Y, ldy,
-                                                               w, r0, r1, col_lo);
+    k_spmm_rows<Tx, T, NCH, true><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, X, ldx, Y,
+                                                                   ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<T, NCH, true><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows, n_long_dev,
-                                                         X, ldx, Y, ldy, w, r0, r1);
+      k_spmm_long<Tx, T, NCH, true><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows,
+                                                             n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   } else {
-    k_spmm_rows<T, NCH, false><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, X, ldx, Y,
-                                                                ldy, w, r0, r1, col_lo);
+    k_spmm_rows<Tx, T, NCH, false><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, X, ldx,
+                                                                    Y, ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<T, NCH, false><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
-                                                          n_long_dev, X, ldx, Y, ldy, w, r0, r1);
+      k_spmm_long<Tx, T, NCH, false><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
+                                                              n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   }
 }
 
-template <typename T>
-void spmm_dispatch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const T* X,
+template <typename Tx, typename T>
+void spmm_dispatch(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const Tx* X,
                    int64_t ldx, T* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo, cudaStream_t s) {
   if (r1 <= r0 || w <= 0) return;
   switch ((w + 31) / 32) {
-    case 1: launch_nch<T, 1>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 2: launch_nch<T, 2>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 3: launch_nch<T, 3>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 4: launch_nch<T, 4>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 5: launch_nch<T, 5>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 6: launch_nch<T, 6>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 7: launch_nch<T, 7>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    case 8: launch_nch<T, 8>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
-    default: launch_nch<T, 9>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 1: launch_nch<Tx, T, 1>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 2: launch_nch<Tx, T, 2>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 3: launch_nch<Tx, T, 3>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 4: launch_nch<Tx, T, 4>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 5: launch_nch<Tx, T, 5>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 6: launch_nch<Tx, T, 6>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 7: launch_nch<Tx, T, 7>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    case 8: launch_nch<Tx, T, 8>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
+    default: launch_nch<Tx, T, 9>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s); break;
   }
 }
 
@@ -219,13 +219,19 @@ void spmm_dispatch(const Csr& g, const OpParams& op, const int32_t* long_rows, c
 void spmm_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
               const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
               cudaStream_t s) {
-  spmm_dispatch<double>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
+  spmm_dispatch<double, double>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
 }
 
 void spmm_f32(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
               const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
               cudaStream_t s) {
-  spmm_dispatch<float>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
+  spmm_dispatch<float, float>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
+}
+
+void spmm_f32_f64(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev,
+                  const float* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1, int64_t col_lo,
+                  cudaStream_t s) {
+  spmm_dispatch<float, double>(g, op, long_rows, n_long_dev, X, ldx, Y, ldy, w, r0, r1, col_lo, s);
 }
 
 }  // namespace grest
