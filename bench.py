@@ -319,10 +319,14 @@ def run_grest(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         return tt.item()
 
-    t64, lat64, prof64, last64, clk64 = timed(tr64)
-    t64 = max_over_ranks(t64)
+    if args.mixed_only:
+        t64 = lat64 = prof64 = last64 = clk64 = None
+        main = None
+    else:
+        t64, lat64, prof64, last64, clk64 = timed(tr64)
+        t64 = max_over_ranks(t64)
+        main = dict(t=t64, lat=lat64, prof=prof64, last=last64, clk=clk64, tr=None, precision="fp64")
     tr64.close()
-    main = dict(t=t64, lat=lat64, prof=prof64, last=last64, clk=clk64, tr=None, precision="fp64")
     res32 = None
     if tr32 is not None:
         t32, lat32, prof32, last32, clk32 = timed(tr32)
@@ -375,7 +379,7 @@ def run_grest(args):
         "latency_ms": {"p50": float(np.percentile(main["lat"], 50)), "p99": float(np.percentile(main["lat"], 99)),
                        "min": main["lat"][0], "max": main["lat"][-1]},
         "mixed": summary(res32) if res32 else None,
-        "fp64": summary(dict(t=t64, lat=lat64, prof=prof64, last=last64)),
+        "fp64": summary(dict(t=t64, lat=lat64, prof=prof64, last=last64)) if t64 else None,
         "e2e": {"value": world * steps / t_e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
                 "d2h_bytes_per_step": d2h // steps, "precision": main["precision"]},
         "gpu_launches": int(main["prof"]["launches"]),
@@ -406,6 +410,7 @@ def main():
     ap.add_argument("--impl", choices=["grest", "reference"], default="grest")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")
+    ap.add_argument("--mixed-only", action="store_true", help="skip the FP64 path")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

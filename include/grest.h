@@ -228,6 +228,19 @@ grest_status grest_gram(grest_ctx *ctx, const double *X, int64_t ldx, int32_t a,
                         int32_t b, int64_t n, double *C, int64_t ldc);
 
 /*
+ * C = X^T Y for FP32 device blocks (X n x a, Y n x b, row-major, ldx, ldy),
+ * FP64 result C (a x b, ldc), a, b <= 256: the Gram kernel of the
+ * mixed-precision step.  On sm_100-class GPUs it runs on the tensor cores
+ * (tcgen05 kind::tf32, each value split into two TF32 parts, three products,
+ * FP32 accumulation over at most 256 rows, FP64 partial sums); blocks whose
+ * base address or leading dimension is not 16-byte aligned use a CUDA-core
+ * kernel with the same accumulation rule.  Runs on the context's stream and
+ * uses its scratch; returns when C is complete.
+ */
+grest_status grest_gram_f32(grest_ctx *ctx, const float *X, int64_t ldx, int32_t a, const float *Y, int64_t ldy,
+                            int32_t b, int64_t n, double *C, int64_t ldc);
+
+/*
  * grest_gram_noalloc -- the same product as grest_gram, C = X^T Y, for
  * callers that cannot allocate device memory: a host application that hands
  * all of the GPU's memory to its own pool (a cudaMalloc would fail or break

@@ -23,9 +23,30 @@ enum DevErr : int32_t {
   DERR_WEIGHT = 8,       // weight not positive and finite
   DERR_CAPACITY = 9,     // edge arena exhausted
   DERR_NUMERIC = 10,     // Cholesky breakdown / rank below K
+  DERR_TIMEOUT = 11,     // a bounded device-side wait expired
 };
 
 __device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
+
+// Largest dynamic shared memory a launch of `kernel` may request on the
+// current device (opt-in limit minus the kernel's static shared memory), and
+// raise the kernel's limit to `bytes` when that fits.  Returns false (and
+// changes nothing) when it does not fit.
+template <typename K>
+inline bool reserve_dynamic_smem(K kernel, size_t bytes) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
+  if (bytes > 48 * 1024 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                               cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
 
 // ---------------------------------------------------------------- CSR state
 // Slack CSR: row r occupies col[row_off[r] .. row_off[r] + row_len[r]) sorted
@@ -148,6 +169,15 @@ void gram_f32(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, i
               int64_t ldc, double* part, bool symmetric, cudaStream_t s);
 void gemm_nn_f32(int64_t n, int a, int c, double alpha, const float* X, int64_t ldx, const double* B, int64_t ldb,
                  double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, cudaStream_t s);
+// sum of per-chunk partials into C: part[chunk][a][b], or part[chunk][b][a] when transposed
+void gram_reduce_launch(const double* part, int64_t chunks, int a, int b, double* C, int64_t ldc, cudaStream_t s,
+                        bool transposed = false);
+
+// tc_gram.cu: tensor-core (tcgen05, 3xTF32) Gram C = X^T Y of FP32 blocks, FP64 output.
+bool gram_tc_supported(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b);
+// returns 0 when launched, -1 when the shapes or the partial buffer do not allow it
+int gram_f32_tc(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+                int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s);
 void convert_f32_to_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
 void convert_f64_to_f32(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
 void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,

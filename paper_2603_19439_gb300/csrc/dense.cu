@@ -20,14 +20,17 @@ constexpr int TM = 64, TN = 64, TK = 32;  // CTA tile (outputs) and row slab
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// partial Gram of one (ta, tb) tile over rows [rbeg, rend)
+// partial Gram of one (ta, tb) tile over rows [rbeg, rend); (TMv/4) x (TNv/4)
+// threads, 4 x 4 outputs each
+template <int TMv, int TNv>
 __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ X, int64_t ldx, int a,
                                                    const double* __restrict__ Y, int64_t ldy, int b, int64_t n,
                                                    int64_t rows_per_chunk, bool upper, double* __restrict__ part) {
-  __shared__ double Xs[TK][TM + 1];
-  __shared__ double Ys[TK][TN + 1];
+  __shared__ double Xs[TK][TMv + 1];
+  __shared__ double Ys[TK][TNv + 1];
+  constexpr int NT = (TMv / 4) * (TNv / 4);
   // tile (ta, tb) from the block index; upper-triangular enumeration when symmetric
-  const int ntb = (b + TN - 1) / TN;
+  const int ntb = (b + TNv - 1) / TNv;
   int bid = blockIdx.x, ta = 0, tb;
   if (!upper) {
     ta = bid / ntb;
@@ -36,18 +39,22 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ X,
     while (bid >= ntb - ta) { bid -= ntb - ta; ++ta; }
     tb = ta + bid;
   }
-  const int i0 = ta * TM, j0 = tb * TN;
+  const int i0 = ta * TMv, j0 = tb * TNv;
   const int64_t chunk = blockIdx.y;
   const int64_t rbeg = chunk * rows_per_chunk;
   int64_t rend = rbeg + rows_per_chunk;
   if (rend > n) rend = n;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+  const int tx = threadIdx.x % (TNv / 4), ty = threadIdx.x / (TNv / 4);
   double acc[4][4] = {};
   for (int64_t r0 = rbeg; r0 < rend; r0 += TK) {
-    for (int e = threadIdx.x; e < TK * TM; e += 256) {
-      int rr = e / TM, cc = e % TM;
+    for (int e = threadIdx.x; e < TK * TMv; e += NT) {
+      int rr = e / TMv, cc = e % TMv;
       int64_t r = r0 + rr;
       Xs[rr][cc] = (r < rend && i0 + cc < a) ? X[r * ldx + i0 + cc] : 0.0;
+    }
+    for (int e = threadIdx.x; e < TK * TNv; e += NT) {
+      int rr = e / TNv, cc = e % TNv;
+      int64_t r = r0 + rr;
       Ys[rr][cc] = (r < rend && j0 + cc < b) ? Y[r * ldy + j0 + cc] : 0.0;
     }
     __syncthreads();
@@ -78,12 +85,14 @@ __global__ void __launch_bounds__(256) k_gram_part(const double* __restrict__ X,
 
 // FP32 inputs: products and 32-row slab sums in FP32, slab sums added into
 // FP64 accumulators, partials written in FP64.
+template <int TMv, int TNv>
 __global__ void __launch_bounds__(256) k_gram_part_f32(const float* __restrict__ X, int64_t ldx, int a,
                                                        const float* __restrict__ Y, int64_t ldy, int b, int64_t n,
                                                        int64_t rows_per_chunk, bool upper, double* __restrict__ part) {
-  __shared__ float Xs[TK][TM + 4];
-  __shared__ float Ys[TK][TN + 4];
-  const int ntb = (b + TN - 1) / TN;
+  __shared__ float Xs[TK][TMv + 4];
+  __shared__ float Ys[TK][TNv + 4];
+  constexpr int NT = (TMv / 4) * (TNv / 4);
+  const int ntb = (b + TNv - 1) / TNv;
   int bid = blockIdx.x, ta = 0, tb;
   if (!upper) {
     ta = bid / ntb;
@@ -92,22 +101,27 @@ __global__ void __launch_bounds__(256) k_gram_part_f32(const float* __restrict__
     while (bid >= ntb - ta) { bid -= ntb - ta; ++ta; }
     tb = ta + bid;
   }
-  const int i0 = ta * TM, j0 = tb * TN;
+  const int i0 = ta * TMv, j0 = tb * TNv;
   const int64_t chunk = blockIdx.y;
   const int64_t rbeg = chunk * rows_per_chunk;
   int64_t rend = rbeg + rows_per_chunk;
   if (rend > n) rend = n;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % (TNv / 4), ty = threadIdx.x / (TNv / 4);
   double acc[4][4] = {};
+  float sl[4][4] = {};
+  int slabs = 0;
   for (int64_t r0 = rbeg; r0 < rend; r0 += TK) {
-    for (int e = threadIdx.x; e < TK * TM; e += 256) {
-      int rr = e / TM, cc = e % TM;
+    for (int e = threadIdx.x; e < TK * TMv; e += NT) {
+      int rr = e / TMv, cc = e % TMv;
       int64_t r = r0 + rr;
       Xs[rr][cc] = (r < rend && i0 + cc < a) ? X[r * ldx + i0 + cc] : 0.f;
+    }
+    for (int e = threadIdx.x; e < TK * TNv; e += NT) {
+      int rr = e / TNv, cc = e % TNv;
+      int64_t r = r0 + rr;
       Ys[rr][cc] = (r < rend && j0 + cc < b) ? Y[r * ldy + j0 + cc] : 0.f;
     }
     __syncthreads();
-    float sl[4][4] = {};
 #pragma unroll 8
     for (int k = 0; k < TK; ++k) {
       float xa[4], yb[4];
@@ -121,12 +135,23 @@ __global__ void __launch_bounds__(256) k_gram_part_f32(const float* __restrict__
 #pragma unroll
         for (int v = 0; v < 4; ++v) sl[u][v] = fmaf(xa[u], yb[v], sl[u][v]);
     }
+    // FP32 sums of 4 slabs (128 rows), then FP64: the FP64 pipe is 1/64 of FP32 here
+    if (++slabs == 4) {
+      slabs = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] += (double)sl[u][v];
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v] += (double)sl[u][v];
+          sl[u][v] = 0.f;
+        }
+    }
     __syncthreads();
   }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] += (double)sl[u][v];
   double* P = part + chunk * (int64_t)a * b;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -138,34 +163,36 @@ __global__ void __launch_bounds__(256) k_gram_part_f32(const float* __restrict__
 }
 
 __global__ void k_gram_reduce(const double* __restrict__ part, int64_t chunks, int a, int b, double* C, int64_t ldc,
-                              bool symmetric) {
+                              bool symmetric, int tm, int tn) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)a * b) return;
   int i = (int)(e / b), j = (int)(e % b);
   int si = i, sj = j;
-  if (symmetric && (i / TM) > (j / TN)) { si = j; sj = i; }  // only upper tiles were computed
+  if (symmetric && (i / tm) > (j / tn)) { si = j; sj = i; }  // only upper tiles were computed
   double s = 0.0;
   for (int64_t c = 0; c < chunks; ++c) s += part[c * (int64_t)a * b + (int64_t)si * b + sj];
   C[(int64_t)i * ldc + j] = s;
 }
 
+template <int TNv>
 __global__ void __launch_bounds__(256) k_gemm_nn(int64_t n, int a, int c, double alpha, const double* __restrict__ X,
                                                  int64_t ldx, const double* __restrict__ B, int64_t ldb, double beta,
                                                  const double* Cin, int64_t ldc, double* Out, int64_t ldo) {
   __shared__ double Xs[TM][TK + 1];
-  __shared__ double Bs[TK][TN + 1];
+  __shared__ double Bs[TK][TNv + 1];
+  constexpr int NT = (TM / 4) * (TNv / 4);
   const int64_t r0 = blockIdx.x * (int64_t)TM;
-  const int j0 = blockIdx.y * TN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int j0 = blockIdx.y * TNv;
+  const int tx = threadIdx.x % (TNv / 4), ty = threadIdx.x / (TNv / 4);
   double acc[4][4] = {};
   for (int k0 = 0; k0 < a; k0 += TK) {
-    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+    for (int e = threadIdx.x; e < TM * TK; e += NT) {
       int rr = e / TK, kk = e % TK;
       int64_t r = r0 + rr;
       Xs[rr][kk] = (r < n && k0 + kk < a) ? X[r * ldx + k0 + kk] : 0.0;
     }
-    for (int e = threadIdx.x; e < TK * TN; e += 256) {
-      int kk = e / TN, cc = e % TN;
+    for (int e = threadIdx.x; e < TK * TNv; e += NT) {
+      int kk = e / TNv, cc = e % TNv;
       Bs[kk][cc] = (k0 + kk < a && j0 + cc < c) ? B[(int64_t)(k0 + kk) * ldb + j0 + cc] : 0.0;
     }
     __syncthreads();
@@ -200,23 +227,25 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t n, int a, int c, double
 }
 
 // FP32 tall-skinny update: Out = beta Cin + alpha X B with B given in FP64
+template <int TNv>
 __global__ void __launch_bounds__(256) k_gemm_nn_f32(int64_t n, int a, int c, float alpha, const float* __restrict__ X,
                                                      int64_t ldx, const double* __restrict__ B, int64_t ldb, float beta,
                                                      const float* Cin, int64_t ldc, float* Out, int64_t ldo) {
   __shared__ float Xs[TM][TK + 1];
-  __shared__ float Bs[TK][TN + 4];
+  __shared__ float Bs[TK][TNv + 4];
+  constexpr int NT = (TM / 4) * (TNv / 4);
   const int64_t r0 = blockIdx.x * (int64_t)TM;
-  const int j0 = blockIdx.y * TN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int j0 = blockIdx.y * TNv;
+  const int tx = threadIdx.x % (TNv / 4), ty = threadIdx.x / (TNv / 4);
   float acc[4][4] = {};
   for (int k0 = 0; k0 < a; k0 += TK) {
-    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+    for (int e = threadIdx.x; e < TM * TK; e += NT) {
       int rr = e / TK, kk = e % TK;
       int64_t r = r0 + rr;
       Xs[rr][kk] = (r < n && k0 + kk < a) ? X[r * ldx + k0 + kk] : 0.f;
     }
-    for (int e = threadIdx.x; e < TK * TN; e += 256) {
-      int kk = e / TN, cc = e % TN;
+    for (int e = threadIdx.x; e < TK * TNv; e += NT) {
+      int kk = e / TNv, cc = e % TNv;
       Bs[kk][cc] = (k0 + kk < a && j0 + cc < c) ? (float)B[(int64_t)(k0 + kk) * ldb + j0 + cc] : 0.f;
     }
     __syncthreads();
@@ -372,6 +401,121 @@ __global__ void __launch_bounds__(1024) k_pchol(double* G, int64_t ld, int c, do
   }
 }
 
+// Shared-memory variant: the upper triangle of G is packed row by row in
+// shared memory (element (i, j >= i) at off(i) + j - i, off(i) = i c - i(i-1)/2),
+// which holds c <= 237 in FP64.  Same pivoting and drop rule as k_pchol.
+__device__ __forceinline__ int poff(int i, int c) { return i * c - (i * (i - 1)) / 2; }
+__device__ __forceinline__ double& pat(double* A, int i, int j, int c) { return A[poff(i, c) + (j - i)]; }
+
+__global__ void __launch_bounds__(1024) k_pchol_smem(const double* G, int64_t ld, int c, double drop_tol,
+                                                     double abs_ref, const double* abs_ref_ptr, double* T,
+                                                     int64_t ldt, double* info) {
+  extern __shared__ double A[];  // packed upper triangle, then perm (ints)
+  int* perm = reinterpret_cast<int*>(A + (c * (c + 1)) / 2);
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ double ref, rkk;
+  __shared__ int piv, rank_s, stop;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < c; i += nth) {
+    perm[i] = i;
+    for (int j = i; j < c; ++j) pat(A, i, j, c) = G[(int64_t)i * ld + j];
+  }
+  if (tid == 0) { rank_s = c; stop = 0; ref = 0.0; }
+  __syncthreads();
+  double kept_min = 1.0, dropped_max = 0.0;
+  for (int k = 0; k < c; ++k) {
+    double bv = -1.0;
+    int bi = c;
+    for (int i = k + tid; i < c; i += nth) {
+      double d = A[poff(i, c)];
+      if (d > bv || (d == bv && i < bi)) { bv = d; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { sval[wid] = bv; sidx[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double v = sval[0];
+      int idx = sidx[0];
+      for (int w = 1; w < (nth + 31) / 32; ++w)
+        if (sval[w] > v || (sval[w] == v && sidx[w] < idx)) { v = sval[w]; idx = sidx[w]; }
+      if (k == 0) {
+        double a = abs_ref_ptr ? fabs(*abs_ref_ptr) : abs_ref;
+        ref = fmax(v, a * a);
+      }
+      if (!(v > 0.0) || !(v > drop_tol * drop_tol * ref) || !isfinite(v)) {
+        stop = 1;
+        rank_s = k;
+      }
+      piv = idx;
+      rkk = sqrt(v > 0.0 ? v : 0.0);
+    }
+    __syncthreads();
+    if (stop) {
+      double v = piv < c ? A[poff(piv, c)] : 0.0;
+      dropped_max = (ref > 0.0 && v > 0.0) ? sqrt(v / ref) : 0.0;
+      break;
+    }
+    const int p = piv;
+    if (p != k) {
+      // symmetric swap of indices k and p in the packed upper triangle
+      for (int j = tid; j < c; j += nth) {
+        if (j < k) {
+          double t = pat(A, j, k, c); pat(A, j, k, c) = pat(A, j, p, c); pat(A, j, p, c) = t;
+        } else if (j > k && j < p) {
+          double t = pat(A, k, j, c); pat(A, k, j, c) = pat(A, j, p, c); pat(A, j, p, c) = t;
+        } else if (j > p) {
+          double t = pat(A, k, j, c); pat(A, k, j, c) = pat(A, p, j, c); pat(A, p, j, c) = t;
+        } else if (j == k) {
+          double t = pat(A, k, k, c); pat(A, k, k, c) = pat(A, p, p, c); pat(A, p, p, c) = t;
+          int q = perm[k]; perm[k] = perm[p]; perm[p] = q;
+        }
+      }
+      __syncthreads();
+    }
+    const double r = rkk;
+    kept_min = ref > 0.0 ? r / sqrt(ref) : 0.0;
+    for (int j = k + 1 + tid; j < c; j += nth) pat(A, k, j, c) /= r;
+    if (tid == 0) pat(A, k, k, c) = r;
+    __syncthreads();
+    // trailing update of the upper triangle: A[i][j] -= R[k][i] R[k][j], k < i <= j
+    const int m = c - k - 1;
+    const double* Rk = A + poff(k, c) - k;  // Rk[j] = R[k][j]
+    for (int i = k + 1 + wid; i < c; i += nth / 32) {
+      const double rki = Rk[i];
+      double* Ai = A + poff(i, c) - i;
+      for (int j = i + lane; j < c; j += 32) Ai[j] = fma(-rki, Rk[j], Ai[j]);
+    }
+    (void)m;
+    __syncthreads();
+  }
+  __syncthreads();
+  const int rk = rank_s;
+  for (int64_t e = tid; e < (int64_t)c * c; e += nth) T[(e / c) * ldt + (e % c)] = 0.0;
+  __syncthreads();
+  // T = P R^-1: thread j solves R x = e_j (x_j = 1/R_jj, x_i = -(sum_{l=i+1..j} R_il x_l)/R_ii)
+  for (int j = tid; j < rk; j += nth) {
+    T[(int64_t)perm[j] * ldt + j] = 1.0 / pat(A, j, j, c);
+    for (int i = j - 1; i >= 0; --i) {
+      double s2 = 0.0;
+      const double* Ri = A + poff(i, c) - i;
+      for (int l = i + 1; l <= j; ++l) s2 = fma(Ri[l], T[(int64_t)perm[l] * ldt + j], s2);
+      T[(int64_t)perm[i] * ldt + j] = -s2 / Ri[i];
+    }
+  }
+  if (tid == 0) {
+    info[0] = rk;
+    info[1] = rk > 0 ? kept_min : 0.0;
+    info[2] = dropped_max;
+    info[3] = 0.0;
+  }
+}
+
 __global__ void k_symmetrize(double* H, int64_t ld, int m) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)m * m) return;
@@ -506,56 +650,106 @@ int64_t gram_chunks(int64_t n, int ntiles) {
 
 }  // namespace
 
+// tile shape: 32-wide tiles for widths <= 32 (K-wide products), else 64
+inline int tile_of(int w) { return w <= 32 ? 32 : 64; }
+
 int64_t gram_parts(int64_t n, int a, int b) {
-  int nt = (int)(cdiv(a, TM) * cdiv(b, TN));
+  int nt = (int)(cdiv(a, tile_of(a)) * cdiv(b, tile_of(b)));
   return gram_chunks(n, nt);
 }
 
-void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
-              int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
+template <typename T>
+void launch_gram_part(dim3 grid, int tm, int tn, const T* X, int64_t ldx, int a, const T* Y, int64_t ldy, int b,
+                      int64_t n, int64_t rpc, bool upper, double* part, cudaStream_t s) {
+  const int nthr = (tm / 4) * (tn / 4);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (tm == 32 && tn == 32) k_gram_part<32, 32><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else if (tm == 32) k_gram_part<32, 64><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else if (tn == 32) k_gram_part<64, 32><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else k_gram_part<64, 64><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+  } else {
+    if (tm == 32 && tn == 32) k_gram_part_f32<32, 32><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else if (tm == 32) k_gram_part_f32<32, 64><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else if (tn == 32) k_gram_part_f32<64, 32><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+    else k_gram_part_f32<64, 64><<<grid, nthr, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, upper, part);
+  }
+}
+
+template <typename T>
+void gram_t(const T* X, int64_t ldx, int a, const T* Y, int64_t ldy, int b, int64_t n, double* C, int64_t ldc,
+            double* part, bool symmetric, int64_t part_cap, cudaStream_t s) {
   if (a <= 0 || b <= 0) return;
   if (n <= 0) {
     for (int i = 0; i < a; ++i) cudaMemsetAsync(C + (int64_t)i * ldc, 0, sizeof(double) * b, s);
     return;
   }
   symmetric = symmetric && (X == Y) && (a == b) && (ldx == ldy);
-  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
+  int tm = tile_of(a), tn = tile_of(b);
+  if (symmetric) tm = tn = tile_of(a);
+  const int nta = (int)cdiv(a, tm), ntb = (int)cdiv(b, tn);
   const int nt = symmetric ? nta * (nta + 1) / 2 : nta * ntb;
   int64_t chunks = gram_chunks(n, nta * ntb);
+  if (part_cap > 0 && chunks > part_cap / ((int64_t)a * b)) chunks = part_cap / ((int64_t)a * b);
   int64_t rpc = cdiv(n, chunks);
   chunks = cdiv(n, rpc);
   dim3 grid((unsigned)nt, (unsigned)chunks);
-  k_gram_part<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, symmetric, part);
+  launch_gram_part<T>(grid, tm, tn, X, ldx, a, Y, ldy, b, n, rpc, symmetric, part, s);
   int64_t tot = (int64_t)a * b;
-  k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric);
+  k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric, tm, tn);
+}
+
+__global__ void k_gram_reduce_t(const double* __restrict__ partT, int64_t chunks, int a, int b, double* C,
+                                int64_t ldc) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a * b) return;
+  int j = (int)(e / a), i = (int)(e % a);  // consecutive threads read consecutive rows of a partial
+  double s = 0.0;
+  for (int64_t c = 0; c < chunks; ++c) s += partT[(c * b + j) * (int64_t)a + i];
+  C[(int64_t)i * ldc + j] = s;
+}
+
+void gram_reduce_launch(const double* part, int64_t chunks, int a, int b, double* C, int64_t ldc, cudaStream_t s,
+                        bool transposed) {
+  int64_t tot = (int64_t)a * b;
+  if (transposed)
+    k_gram_reduce_t<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc);
+  else
+    k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, false, 64, 64);
+}
+
+void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
+              int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
+  gram_t<double>(X, ldx, a, Y, ldy, b, n, C, ldc, part, symmetric, 0, s);
 }
 
 int gram_f64_capped(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
                     int64_t ldc, double* part, int64_t part_cap, cudaStream_t s) {
   if (a <= 0 || b <= 0 || n <= 0) return -1;
-  const int64_t per_chunk = (int64_t)a * b;
-  if (per_chunk > part_cap) return -1;
-  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
-  int64_t chunks = gram_chunks(n, nta * ntb);
-  if (chunks > part_cap / per_chunk) chunks = part_cap / per_chunk;
-  int64_t rpc = cdiv(n, chunks);
-  chunks = cdiv(n, rpc);
-  dim3 grid((unsigned)(nta * ntb), (unsigned)chunks);
-  k_gram_part<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, false, part);
-  k_gram_reduce<<<(unsigned)cdiv(per_chunk, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, false);
+  if ((int64_t)a * b > part_cap) return -1;
+  gram_t<double>(X, ldx, a, Y, ldy, b, n, C, ldc, part, false, part_cap, s);
   return 0;
 }
 
 void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B, int64_t ldb,
                  double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo, cudaStream_t s) {
   if (n <= 0 || c <= 0) return;
-  dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
-  k_gemm_nn<<<grid, 256, 0, s>>>(n, a, c, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo);
+  if (c <= 32) {
+    dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, 32));
+    k_gemm_nn<32><<<grid, (TM / 4) * 8, 0, s>>>(n, a, c, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo);
+  } else {
+    dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
+    k_gemm_nn<64><<<grid, 256, 0, s>>>(n, a, c, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo);
+  }
 }
 
 void pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
                    double* T, int64_t ldt, double* info, cudaStream_t s) {
-  k_pchol<<<1, 1024, sizeof(int) * (c + 1), s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
+  const size_t smem = sizeof(double) * ((size_t)c * (c + 1) / 2) + sizeof(int) * (c + 1) + 16;
+  if (reserve_dynamic_smem(k_pchol_smem, smem)) {
+    k_pchol_smem<<<1, 1024, smem, s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
+  } else {
+    k_pchol<<<1, 1024, sizeof(int) * (c + 1), s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
+  }
 }
 
 void symmetrize(double* H, int64_t ld, int m, cudaStream_t s) {
@@ -605,28 +799,19 @@ void sign_normalize(float* X, int64_t ldx, int w, int64_t n, double* part, int64
 
 void gram_f32(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
               int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
-  if (a <= 0 || b <= 0) return;
-  if (n <= 0) {
-    for (int i = 0; i < a; ++i) cudaMemsetAsync(C + (int64_t)i * ldc, 0, sizeof(double) * b, s);
-    return;
-  }
-  symmetric = symmetric && (X == Y) && (a == b) && (ldx == ldy);
-  const int nta = (int)cdiv(a, TM), ntb = (int)cdiv(b, TN);
-  const int nt = symmetric ? nta * (nta + 1) / 2 : nta * ntb;
-  int64_t chunks = gram_chunks(n, nta * ntb);
-  int64_t rpc = cdiv(n, chunks);
-  chunks = cdiv(n, rpc);
-  dim3 grid((unsigned)nt, (unsigned)chunks);
-  k_gram_part_f32<<<grid, 256, 0, s>>>(X, ldx, a, Y, ldy, b, n, rpc, symmetric, part);
-  int64_t tot = (int64_t)a * b;
-  k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, symmetric);
+  gram_t<float>(X, ldx, a, Y, ldy, b, n, C, ldc, part, symmetric, 0, s);
 }
 
 void gemm_nn_f32(int64_t n, int a, int c, double alpha, const float* X, int64_t ldx, const double* B, int64_t ldb,
                  double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, cudaStream_t s) {
   if (n <= 0 || c <= 0) return;
-  dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
-  k_gemm_nn_f32<<<grid, 256, 0, s>>>(n, a, c, (float)alpha, X, ldx, B, ldb, (float)beta, Cin, ldc, Out, ldo);
+  if (c <= 32) {
+    dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, 32));
+    k_gemm_nn_f32<32><<<grid, (TM / 4) * 8, 0, s>>>(n, a, c, (float)alpha, X, ldx, B, ldb, (float)beta, Cin, ldc, Out, ldo);
+  } else {
+    dim3 grid((unsigned)cdiv(n, TM), (unsigned)cdiv(c, TN));
+    k_gemm_nn_f32<64><<<grid, 256, 0, s>>>(n, a, c, (float)alpha, X, ldx, B, ldb, (float)beta, Cin, ldc, Out, ldo);
+  }
 }
 
 void convert_f32_to_f64(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s) {

@@ -113,6 +113,81 @@ __global__ void __launch_bounds__(1024) k_tridiag(double* H, int64_t ld, int m, 
   }
 }
 
+// Shared-memory variant of step 1: the upper triangle of H is packed row by
+// row (element (i, j >= i) at off(i) + j - i, off(i) = i m - i(i-1)/2), so the
+// reduction runs out of shared memory for m <= 235.  Reflectors go to H's rows.
+__device__ __forceinline__ int poff(int i, int m) { return i * m - (i * (i - 1)) / 2; }
+
+__global__ void __launch_bounds__(1024) k_tridiag_smem(double* H, int64_t ld, int m, double* work, int mmax) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  EigWork L = eig_layout(work, mmax);
+  double* A = sm;
+  double* v = sm + (m * (m + 1)) / 2;
+  double* p = v + m;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  for (int i = wid; i < m; i += nw)
+    for (int j = i + lane; j < m; j += 32) A[poff(i, m) + j - i] = H[(int64_t)i * ld + j];
+  __syncthreads();
+  for (int j = 0; j + 2 < m; ++j) {
+    const int n = m - j - 1;
+    const double* x = A + poff(j, m) + 1;  // row j right of the diagonal
+    double s = 0.0;
+    for (int i = tid; i < n; i += nth) s = fma(x[i], x[i], s);
+    const double nrm2 = block_sum(s, red);
+    const double x0 = x[0];
+    const double alpha = nrm2 > 0.0 ? -copysign(sqrt(nrm2), x0) : 0.0;
+    const double beta = nrm2 > 0.0 ? 1.0 / (nrm2 - alpha * x0) : 0.0;
+    for (int i = tid; i < n; i += nth) v[i] = (i == 0) ? x0 - alpha : x[i];
+    if (tid == 0) {
+      L.d[j] = A[poff(j, m)];
+      L.e[j] = alpha;
+      L.beta[j] = beta;
+    }
+    __syncthreads();
+    const int b0 = j + 1;  // B = trailing block, B(i, l) = A(b0 + min, b0 + max)
+    if (beta != 0.0) {
+      for (int i = wid; i < n; i += nw) {
+        const int gi = b0 + i;
+        double a = 0.0;
+        for (int l = lane; l < n; l += 32) {
+          const int gl = b0 + l;
+          const double bil = l >= i ? A[poff(gi, m) + gl - gi] : A[poff(gl, m) + gi - gl];
+          a = fma(bil, v[l], a);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) p[i] = beta * a;
+      }
+      __syncthreads();
+      double t = 0.0;
+      for (int i = tid; i < n; i += nth) t = fma(p[i], v[i], t);
+      const double K = 0.5 * beta * block_sum(t, red);
+      for (int i = tid; i < n; i += nth) p[i] -= K * v[i];  // p becomes w
+      __syncthreads();
+      for (int i = wid; i < n; i += nw) {
+        const int gi = b0 + i;
+        double* row = A + poff(gi, m) - gi;
+        const double vi = v[i], wi = p[i];
+        for (int l = i + lane; l < n; l += 32) row[b0 + l] -= vi * p[l] + wi * v[l];
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) H[(int64_t)j * ld + j + 1 + i] = v[i];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      L.d[m - 2] = A[poff(m - 2, m)];
+      L.d[m - 1] = A[poff(m - 1, m)];
+      L.e[m - 2] = A[poff(m - 2, m) + 1];
+    } else if (m == 1) {
+      L.d[0] = A[0];
+    }
+    L.e[m - 1] = 0.0;
+  }
+}
+
 __device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
   int c = 0;
   double q = d[0] - x;
@@ -237,11 +312,13 @@ __global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, doub
   // inverse iteration on T - lambda I, one thread per selected pair
   if (tid < k) {
     const int t = tid;
-    double* a = L.scr + (int64_t)t * 5 * mmax;  // diagonal of U
-    double* c = a + mmax;                      // first super-diagonal of U
-    double* c2 = c + mmax;                     // second super-diagonal (fill-in)
-    double* l = c2 + mmax;                     // multipliers
-    double* y = l + mmax;
+    // per-thread arrays interleaved across threads (coalesced): element i at [i * kMaxK]
+    struct Strided {
+      double* b;
+      __device__ double& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
+    };
+    const Strided a{L.scr + t}, c{L.scr + (int64_t)mmax * kMaxK + t}, c2{L.scr + (int64_t)2 * mmax * kMaxK + t},
+        l{L.scr + (int64_t)3 * mmax * kMaxK + t}, y{L.scr + (int64_t)4 * mmax * kMaxK + t};
     const double lm = lam[t];
     const double eps = DBL_EPSILON * fmax(tnorm, DBL_MIN);
     for (int i = 0; i < m; ++i) {
@@ -273,7 +350,7 @@ __global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, doub
       }
     }
     if (a[m - 1] == 0.0) a[m - 1] = eps;
-    double* flags = L.scr + (int64_t)kMaxK * 5 * mmax + (int64_t)t * mmax;
+    const Strided flags{L.scr + (int64_t)5 * mmax * kMaxK + t};
     for (int i = 0; i < m; ++i) flags[i] = y[i];
     for (int i = 0; i < m; ++i) y[i] = hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7);
     for (int it = 0; it < 3; ++it) {
@@ -299,25 +376,39 @@ __global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, doub
     for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = y[i];
   }
   __syncthreads();
-  // clusters of close selected values: modified Gram-Schmidt in ascending order
+  // clusters of close selected values: block classical Gram-Schmidt, applied
+  // twice, in ascending order; all projections of one vector run in parallel
+  // (one warp per earlier cluster member), so a cluster of c vectors costs
+  // O(c) block synchronizations instead of O(c^2)
+  __shared__ double dots[kMaxK];
   const double ortol = 1e-3 * tnorm;
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   for (int a = 1; a < k; ++a) {
     const int ta = sel_sorted[a];
     int b0 = a;
     while (b0 > 0 && lam[sel_sorted[b0]] - lam[sel_sorted[b0 - 1]] < ortol) --b0;
     if (b0 == a) continue;
-    for (int b = b0; b < a; ++b) {
-      const int tb = sel_sorted[b];
-      double s = 0.0;
-      for (int i = tid; i < m; i += nth) s = fma(F[(int64_t)i * ldf + tb], F[(int64_t)i * ldf + ta], s);
-      s = block_sum(s, red);
-      for (int i = tid; i < m; i += nth) F[(int64_t)i * ldf + ta] -= s * F[(int64_t)i * ldf + tb];
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int b = b0 + wid; b < a; b += nw) {
+        const int tb = sel_sorted[b];
+        double d = 0.0;
+        for (int i = lane; i < m; i += 32) d = fma(F[(int64_t)i * ldf + tb], F[(int64_t)i * ldf + ta], d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) dots[b - b0] = d;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += nth) {
+        double y = F[(int64_t)i * ldf + ta];
+        for (int b = b0; b < a; ++b) y = fma(-dots[b - b0], F[(int64_t)i * ldf + sel_sorted[b]], y);
+        F[(int64_t)i * ldf + ta] = y;
+      }
       __syncthreads();
     }
-    double s = 0.0;
-    for (int i = tid; i < m; i += nth) s = fma(F[(int64_t)i * ldf + ta], F[(int64_t)i * ldf + ta], s);
-    s = block_sum(s, red);
-    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    double s2 = 0.0;
+    for (int i = tid; i < m; i += nth) s2 = fma(F[(int64_t)i * ldf + ta], F[(int64_t)i * ldf + ta], s2);
+    s2 = block_sum(s2, red);
+    const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
     for (int i = tid; i < m; i += nth) F[(int64_t)i * ldf + ta] *= inv;
     __syncthreads();
   }
@@ -357,7 +448,12 @@ size_t eig_work_doubles(int mmax) { return (size_t)5 * mmax + (size_t)kMaxK * 6 
 void sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
                     double* info, double* work, cudaStream_t s) {
   const int mmax = m;
-  k_tridiag<<<1, 1024, sizeof(double) * 2 * (m + 1), s>>>(H, ld, m, work, mmax);
+  const size_t smem = sizeof(double) * ((size_t)m * (m + 1) / 2 + 2 * (size_t)m + 2);
+  if (reserve_dynamic_smem(k_tridiag_smem, smem)) {
+    k_tridiag_smem<<<1, 1024, smem, s>>>(H, ld, m, work, mmax);
+  } else {
+    k_tridiag<<<1, 1024, sizeof(double) * 2 * (m + 1), s>>>(H, ld, m, work, mmax);
+  }
   k_multisect<<<(m + 7) / 8, 256, 0, s>>>(m, work, mmax);
   k_select_invit<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, F, ldf, ritz, info);
   k_backtransform<<<(k + 7) / 8, 256, sizeof(double) * 8 * m, s>>>(H, ld, m, k, work, mmax, F, ldf);

@@ -123,6 +123,7 @@ grest_status map_dev_err(int32_t e) {
     case DERR_NONE: return GREST_OK;
     case DERR_CAPACITY: return GREST_ERR_CAPACITY;
     case DERR_NUMERIC: return GREST_ERR_NUMERIC;
+    case DERR_TIMEOUT: return GREST_ERR_TIMEOUT;
     default: return GREST_ERR_INVALID_UPDATE;
   }
 }
@@ -293,7 +294,10 @@ void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, in
 void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
           int64_t ldc, bool sym) {
   int p = prof_begin(c);
-  gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+  bool done = false;
+  if (n > 0 && gram_tc_supported(X, ldx, a, Y, ldy, b))
+    done = gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) == 0;
+  if (!done) gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
   prof_end(c, p, 1, 2.0 * n * a * b);
 }
@@ -361,6 +365,7 @@ grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n
   if (read_rank) {
     grest_status st = read_back(c, info_slot + 4);
     if (st != GREST_OK) return st;
+    if (*c->h_err) return map_dev_err(*c->h_err);
     rank = (int)c->h_info[info_slot];
   }
   if (rank > 0) gemm(c, n, w, rank, 1.0, X, ldx, c->T, w, 0.0, static_cast<const T*>(nullptr), 0, Out, ldo);
@@ -810,7 +815,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&c->XtM, (int64_t)64 * c->ldq)); IK(dalloc(&c->Gs, (int64_t)c->q * c->q));
   IK(dalloc(&c->Uh, (int64_t)c->q * c->q)); IK(dalloc(&c->ritz, mm)); IK(dalloc(&c->th_new, 64));
   IK(dalloc(&c->tmpk, 256)); IK(dalloc(&c->info, 64)); IK(dalloc(&c->resn, 64));
-  c->part_cap = 3'200'000;
+  c->part_cap = 8'000'000;  // FP64 partial sums of the split-K Gram kernels (64 MB)
   IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));
   IK(dalloc(&c->eigwork, eig_work_doubles(std::max(mm, c->q))));
   IK(dalloc(&c->err, 1));
@@ -933,11 +938,13 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   ++c->step;
   if (c->cfg.flags & GREST_FLAG_CHECK) run_checks(c, N + S);
   CK(cudaMemcpyAsync(c->h_info, c->info, sizeof(double) * 64, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->h_scal, c->g.arena_top, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   c->last_ritz.resize(c->last_m);
   CK(cudaMemcpyAsync(c->last_ritz.data(), c->ritz, sizeof(double) * c->last_m, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  if (*c->h_err) return map_dev_err(*c->h_err);
   grest_stats& S_ = c->stats;
   S_.step = c->step;
   S_.n_nodes = c->g.n;
@@ -1035,6 +1042,25 @@ grest_status grest_gram(grest_ctx* c, const double* X, int64_t ldx, int32_t a, c
   gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);
   CK(cudaGetLastError());
   return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+grest_status grest_gram_f32(grest_ctx* c, const float* X, int64_t ldx, int32_t a, const float* Y, int64_t ldy,
+                            int32_t b, int64_t n, double* C, int64_t ldc) {
+  if (!c || !X || !Y || !C || a < 1 || b < 1 || a > 256 || b > 256 || n < 0 || ldx < a || ldy < b || ldc < b)
+    return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+  bool done = false;
+  if (n > 0 && gram_tc_supported(X, ldx, a, Y, ldy, b))
+    done = gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) == 0;
+  if (!done) {
+    if (gram_parts(n, a, b) * (int64_t)a * b > c->part_cap) return GREST_ERR_CAPACITY;
+    gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return *c->h_err ? map_dev_err(*c->h_err) : GREST_OK;
 }
 
 void grest_destroy(grest_ctx* c) {

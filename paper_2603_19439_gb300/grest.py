@@ -70,7 +70,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
            "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
-           "grest_gram_noalloc", "grest_destroy", "grest_status_str"]
+           "grest_gram_f32", "grest_gram_noalloc", "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -95,6 +95,7 @@ def load_library(path=None):
     lib.grest_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.grest_apply_operator.argtypes = [vp, vp, i64, vp, i64, i32]
     lib.grest_gram.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
+    lib.grest_gram_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
     lib.grest_gram_noalloc.argtypes = [vp, i64, i32, vp, i64, i32, i64, vp, i64, vp]
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
@@ -234,6 +235,13 @@ class Tracker:
                                  X.shape[0], C.data_ptr(), C.stride(0))
         if st != 0:
             raise GrestError(st, "grest_gram")
+
+    def gram_f32(self, X, Y, C):
+        """C (float64) = X^T Y for torch CUDA float32 tensors (row-major)."""
+        st = self.lib.grest_gram_f32(self.h, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(), Y.stride(0),
+                                     Y.shape[1], X.shape[0], C.data_ptr(), C.stride(0))
+        if st != 0:
+            raise GrestError(st, "grest_gram_f32")
 
     def sync(self):
         st = self.lib.grest_sync(self.h)

@@ -229,3 +229,38 @@ def test_gram_entry_point(cuda):
         ref = X.T @ Y
         assert np.abs(Cd.cpu().numpy() - ref).max() <= 1e-12 * max(1.0, np.abs(X).max() * np.abs(Y).max() * n)
     tr.close()
+
+
+def test_gram_f32_tensor_core_entry_point(cuda):
+    """grest_gram_f32 (tcgen05, 3xTF32, FP32 accumulation over <= 256 rows,
+    FP64 partial sums) against a float64 product of the same FP32 inputs; the
+    bound is relative to |X|^T |Y| (the scale of the accumulated terms).
+    Includes ragged row counts, widths 1..256 and a misaligned view that must
+    fall back to the CUDA-core kernel."""
+    torch = cuda
+    g, _ = wl.sbm_graph(200, 2, 0.1, 0.02, 71)
+    rp, col, _ = g.csr()
+    tr = G.Tracker(g.n, rp, col, None, np.linalg.qr(np.random.default_rng(0).standard_normal((200, 4)))[0],
+                   np.ones(4), 4)
+    rng = np.random.default_rng(72)
+    cases = [(1, 1, 1), (33, 7, 9), (100_003, 32, 200), (250_001, 232, 232), (70_000, 200, 32), (4097, 256, 256),
+             (65_536, 132, 164), (1000, 129, 17)]
+    for n, a, b in cases:
+        X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
+        Y = torch.tensor(rng.standard_normal((n, b)), dtype=torch.float32, device="cuda")
+        C = torch.empty((a, b), dtype=torch.float64, device="cuda")
+        tr.gram_f32(X, Y, C)
+        Xh, Yh = X.double().cpu().numpy(), Y.double().cpu().numpy()
+        ref = Xh.T @ Yh
+        bound = np.abs(Xh).T @ np.abs(Yh)
+        err = np.abs(C.cpu().numpy() - ref)
+        assert np.all(err <= 2e-6 * bound + 1e-30), (n, a, b, float((err / np.maximum(bound, 1e-30)).max()))
+    # misaligned base pointer (column offset 1): CUDA-core fallback, same rule
+    Z = torch.tensor(rng.standard_normal((5000, 40)), dtype=torch.float32, device="cuda")
+    X, Y = Z[:, 1:33], Z[:, 3:40]
+    C = torch.empty((32, 37), dtype=torch.float64, device="cuda")
+    tr.gram_f32(X, Y, C)
+    Xh, Yh = X.double().cpu().numpy(), Y.double().cpu().numpy()
+    err = np.abs(C.cpu().numpy() - Xh.T @ Yh)
+    assert np.all(err <= 2e-6 * (np.abs(Xh).T @ np.abs(Yh)))
+    tr.close()
