@@ -742,14 +742,19 @@ void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t
   }
 }
 
-void pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
-                   double* T, int64_t ldt, double* info, cudaStream_t s) {
+bool pchol_cluster(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                   double* T, int64_t ldt, int* piv, double* info, cudaStream_t s);
+
+int pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                  double* T, int64_t ldt, int* piv, double* info, cudaStream_t s) {
+  if (pchol_cluster(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, piv, info, s)) return 2;
   const size_t smem = sizeof(double) * ((size_t)c * (c + 1) / 2) + sizeof(int) * (c + 1) + 16;
   if (reserve_dynamic_smem(k_pchol_smem, smem)) {
     k_pchol_smem<<<1, 1024, smem, s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
   } else {
     k_pchol<<<1, 1024, sizeof(int) * (c + 1), s>>>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, info);
   }
+  return 1;
 }
 
 void symmetrize(double* H, int64_t ld, int m, cudaStream_t s) {

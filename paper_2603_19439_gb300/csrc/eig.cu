@@ -22,19 +22,28 @@ namespace {
 
 constexpr int kMaxK = 256;  // selected pairs per call (RSVD basis: L <= 256)
 
+constexpr int kMaxM = 512;  // largest projected problem (K + 2 (L + P) <= 576 is rejected earlier)
+
 struct EigWork {
-  double *d, *e, *beta, *ev, *scr;
-  int* ord;
+  double *d, *e, *ds, *e2, *beta, *ev, *lam, *tnorm, *scr;
+  int *ord, *sel;
 };
 
+// d, e, scaled d, scaled e^2, beta, ev: mmax each; ord: mmax ints; lam: kMaxK;
+// sel: kMaxK ints; tnorm[8]; then the inverse-iteration scratch (6 mmax kMaxK).
 __device__ __host__ inline EigWork eig_layout(double* w, int mmax) {
   EigWork L;
   L.d = w;
   L.e = w + mmax;
-  L.beta = w + 2 * mmax;
-  L.ev = w + 3 * mmax;
-  L.ord = reinterpret_cast<int*>(w + 4 * mmax);
-  L.scr = w + 5 * mmax;
+  L.ds = w + 2 * mmax;
+  L.e2 = w + 3 * mmax;
+  L.beta = w + 4 * mmax;
+  L.ev = w + 5 * mmax;
+  L.ord = reinterpret_cast<int*>(w + 6 * mmax);
+  L.lam = w + 7 * mmax;
+  L.sel = reinterpret_cast<int*>(w + 7 * mmax + kMaxK);
+  L.tnorm = w + 7 * mmax + 2 * kMaxK;
+  L.scr = w + 7 * mmax + 2 * kMaxK + 8;
   return L;
 }
 
@@ -188,51 +197,105 @@ __global__ void __launch_bounds__(1024) k_tridiag_smem(double* H, int64_t ld, in
   }
 }
 
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
-  int c = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  c += q < 0.0;
-  for (int t = 1; t < m; ++t) {
-    double et = e[t - 1];
-    q = (d[t] - x) - et * et / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+// Sturm count: the number of eigenvalues of T below x equals the number of
+// sign changes in p_0 = 1, p_1, ..., p_m with p_t = (d_t - x) p_{t-1} -
+// e_{t-1}^2 p_{t-2} (the leading principal minors of T - x I).  This
+// product form needs no division, which matters on GB300, where one FP64
+// warp instruction costs ~68 clocks and a division about ten of them.  T is
+// pre-scaled by a power of two to norm ~1, an exact zero p_t is replaced by
+// -floor_q p_{t-1} (the minor ratio q_t = p_t / p_{t-1} pushed just below
+// zero), and the pair (p_t, p_{t-1}) is rescaled by a power of two (exact)
+// whenever p_t leaves [2^-400, 2^400].
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int m, double x, double floor_q) {
+  double pm2 = 0.0, pm1 = 1.0;
+  int cnt = 0;
+  bool neg_prev = false;
+  for (int t = 0; t < m; ++t) {
+    double pt = fma(-(t > 0 ? e2[t - 1] : 0.0), pm2, (d[t] - x) * pm1);
+    if (((__double2hiint(pt) & 0x7fffffff) | __double2loint(pt)) == 0) pt = -floor_q * pm1;
+    const int hw = __double2hiint(pt);
+    const bool neg = hw < 0;
+    cnt += neg != neg_prev;
+    neg_prev = neg;
+    const int ex = (hw >> 20) & 0x7ff;
+    if (ex > 1023 + 400 || ex < 1023 - 400) {
+      const int field = max(2046 - ex, 1);  // 2^(1023 - ex)
+      const double sc = __hiloint2double(field << 20, 0);
+      pt *= sc;
+      pm1 *= sc;
+    }
+    pm2 = pm1;
+    pm1 = pt;
   }
-  return c;
+  return cnt;
 }
 
-// --- 2. eigenvalue number i (ascending) by 32-way multisection, one warp each
-__global__ void __launch_bounds__(256) k_multisect(int m, double* work, int mmax) {
+// Gershgorin bounds of T and the exact power-of-two scaling used by the
+// multisection: ds = s d, e2 = (s e)^2, tnorm[1..4] = s gl, s gu, 1/s, s ||T||.
+__global__ void __launch_bounds__(256) k_sturm_prep(int m, double* work, int mmax) {
+  __shared__ double rlo[32], rhi[32];
+  __shared__ double bs[2];
   EigWork L = eig_layout(work, mmax);
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= m) return;
-  double gl = DBL_MAX, gu = -DBL_MAX, emax2 = 0.0;
-  for (int t = lane; t < m; t += 32) {
-    double r = (t > 0 ? fabs(L.e[t - 1]) : 0.0) + (t + 1 < m ? fabs(L.e[t]) : 0.0);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  double gl = DBL_MAX, gu = -DBL_MAX;
+  for (int t = tid; t < m; t += blockDim.x) {
+    const double r = (t > 0 ? fabs(L.e[t - 1]) : 0.0) + (t + 1 < m ? fabs(L.e[t]) : 0.0);
     gl = fmin(gl, L.d[t] - r);
     gu = fmax(gu, L.d[t] + r);
-    if (t + 1 < m) emax2 = fmax(emax2, L.e[t] * L.e[t]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    gl = fmin(gl, __shfl_xor_sync(0xffffffffu, gl, o));
-    gu = fmax(gu, __shfl_xor_sync(0xffffffffu, gu, o));
-    emax2 = fmax(emax2, __shfl_xor_sync(0xffffffffu, emax2, o));
+    gl = fmin(gl, __shfl_down_sync(0xffffffffu, gl, o));
+    gu = fmax(gu, __shfl_down_sync(0xffffffffu, gu, o));
   }
-  const double tnorm = fmax(fabs(gl), fabs(gu));
-  const double pivmin = DBL_MIN * fmax(1.0, emax2);
-  double lo = gl - 2.0 * DBL_EPSILON * tnorm - pivmin, hi = gu + 2.0 * DBL_EPSILON * tnorm + pivmin;
-  for (int it = 0; it < 40; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+  if (lane == 0) {
+    rlo[wid] = gl;
+    rhi[wid] = gu;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < nw; ++w) {
+      gl = fmin(gl, rlo[w]);
+      gu = fmax(gu, rhi[w]);
+    }
+    const double tn = fmax(fmax(fabs(gl), fabs(gu)), DBL_MIN);
+    const int E = min(((__double2hiint(tn) >> 20) & 0x7ff) - 1023, 1022);
+    const double sc = __hiloint2double((1023 - E) << 20, 0);  // 2^-E
+    bs[0] = sc;
+    L.tnorm[1] = gl * sc;
+    L.tnorm[2] = gu * sc;
+    L.tnorm[3] = __hiloint2double((1023 + E) << 20, 0);  // 2^E
+    L.tnorm[4] = tn * sc;
+  }
+  __syncthreads();
+  const double sc = bs[0];
+  for (int t = tid; t < m; t += blockDim.x) {
+    L.ds[t] = L.d[t] * sc;
+    const double es = L.e[t] * sc;
+    L.e2[t] = es * es;
+  }
+}
+
+// --- 2. eigenvalue number i (ascending) by 32-way multisection on the scaled
+// T; one warp per block so the warps land on separate SM sub-partitions.  The
+// bracket is refined to an absolute width of 4 eps ||T||.
+__global__ void __launch_bounds__(32) k_multisect(int m, double* work, int mmax) {
+  EigWork L = eig_layout(work, mmax);
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x;
+  if (i >= m) return;
+  const double tnorm = L.tnorm[4];
+  const double floor_q = DBL_EPSILON * DBL_EPSILON * tnorm;
+  const double tol = 4.0 * DBL_EPSILON * tnorm;
+  double lo = L.tnorm[1] - tol, hi = L.tnorm[2] + tol;
+  for (int it = 0; it < 40 && hi - lo > tol; ++it) {
     const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int c = sturm_count(L.d, L.e, m, x, pivmin);
+    const int c = sturm_count(L.ds, L.e2, m, x, floor_q);
     // first probe holding more than i eigenvalues below it
-    unsigned above = __ballot_sync(0xffffffffu, c > i);
+    const unsigned above = __ballot_sync(0xffffffffu, c > i);
     double nlo = lo, nhi = hi;
     if (above) {
-      int f = __ffs(above) - 1;
+      const int f = __ffs(above) - 1;
       nhi = __shfl_sync(0xffffffffu, x, f);
       if (f > 0) nlo = __shfl_sync(0xffffffffu, x, f - 1);
     } else {
@@ -241,16 +304,74 @@ __global__ void __launch_bounds__(256) k_multisect(int m, double* work, int mmax
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) L.ev[i] = 0.5 * (lo + hi);
+  if (lane == 0) L.ev[i] = 0.5 * (lo + hi) * L.tnorm[3];
 }
 
-__device__ __forceinline__ double order_key_cmp(double a, int ia, double b, int ib, int op) {
-  // returns < 0 when (a, ia) precedes (b, ib) in tracking order
-  if (op == GREST_OP_ADJ) {
-    if (fabs(a) != fabs(b)) return fabs(a) > fabs(b) ? -1.0 : 1.0;
+// Order-preserving integer image of a double (-0 and +0 equal).
+__device__ __forceinline__ long long ord_key(double x) {
+  long long b = __double_as_longlong(x);
+  if ((b & 0x7fffffffffffffffll) == 0) return 0;
+  return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
+}
+
+// --- 3. tracking order (|theta| descending for the adjacency, theta
+// descending otherwise, lower index first on ties), the K leading values, the
+// boundary gap, and the selected values sorted ascending and pulled apart by
+// at least 10 eps ||T|| for the inverse iteration.
+__global__ void __launch_bounds__(256) k_select(int m, int k, int op, double* work, int mmax, double* theta,
+                                                double* ritz, double* info) {
+  __shared__ long long k1[kMaxM], k2[kMaxM];
+  __shared__ int sel_i[kMaxK];
+  EigWork L = eig_layout(work, mmax);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < m; i += nth) {
+    const double a = L.ev[i];
+    k1[i] = op == GREST_OP_ADJ ? ord_key(fabs(a)) : 0;
+    k2[i] = ord_key(a);
   }
-  if (a != b) return a > b ? -1.0 : 1.0;
-  return ia < ib ? -1.0 : (ia > ib ? 1.0 : 0.0);
+  __syncthreads();
+  for (int i = tid; i < m; i += nth) {
+    int pos = 0;
+    const long long a1 = k1[i], a2 = k2[i];
+    for (int j = 0; j < m; ++j) {
+      const long long b1 = k1[j], b2 = k2[j];
+      pos += (b1 > a1) || (b1 == a1 && (b2 > a2 || (b2 == a2 && j < i)));
+    }
+    L.ord[pos] = i;
+    ritz[pos] = L.ev[i];
+  }
+  __syncthreads();
+  // selected indices sorted ascending by value = ascending by index (ev is
+  // ascending in its index up to the bracket width)
+  for (int t = tid; t < k; t += nth) {
+    const int it = L.ord[t];
+    int pos = 0;
+    for (int u = 0; u < k; ++u) pos += L.ord[u] < it;
+    sel_i[pos] = t;
+  }
+  for (int t = tid; t < k; t += nth) theta[t] = L.ev[L.ord[t]];
+  __syncthreads();
+  if (tid == 0) {
+    const double tnorm = fmax(fabs(L.ev[0]), fabs(L.ev[m - 1]));
+    if (m > k) {
+      const double a = L.ev[L.ord[k - 1]], b = L.ev[L.ord[k]];
+      const double g = op == GREST_OP_ADJ ? fabs(fabs(a) - fabs(b)) : fabs(a - b);
+      info[0] = tnorm > 0.0 ? g / tnorm : 0.0;
+    } else {
+      info[0] = INFINITY;
+    }
+    const double sep = 10.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    double prev = -DBL_MAX;
+    for (int a = 0; a < k; ++a) {
+      const int t = sel_i[a];
+      double v = L.ev[L.ord[t]];
+      if (a > 0 && v < prev + sep) v = prev + sep;
+      L.lam[t] = v;
+      L.sel[a] = t;
+      prev = v;
+    }
+    L.tnorm[0] = tnorm;
+  }
 }
 
 __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
@@ -263,134 +384,107 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
   return ((double)h / 4294967296.0) - 0.5;
 }
 
-// --- 3 + 4. order, select, inverse iteration, cluster re-orthogonalization
-__global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, double* work, int mmax, double* theta,
-                                                      double* F, int64_t ldf, double* ritz, double* info) {
-  __shared__ double lam[kMaxK];
-  __shared__ int sel_sorted[kMaxK];
+// --- 4. eigenvectors of T by inverse iteration (tridiagonal LU with partial
+// pivoting, three solves from a fixed pseudo-random start), one thread per
+// selected pair and one warp per block: the chains are serial, so the warps
+// are spread over the SM sub-partitions.  The reciprocal of each U pivot is
+// formed once in the LU and reused by the solves.
+__global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mmax, double* F, int64_t ldf) {
+  EigWork L = eig_layout(work, mmax);
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  if (t >= k) return;
+  // per-thread arrays interleaved across threads (coalesced): element i at [i * kMaxK]
+  struct Strided {
+    double* b;
+    __device__ double& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
+  };
+  const Strided ur{L.scr + t}, c{L.scr + (int64_t)mmax * kMaxK + t}, c2{L.scr + (int64_t)2 * mmax * kMaxK + t},
+      l{L.scr + (int64_t)3 * mmax * kMaxK + t}, y{L.scr + (int64_t)4 * mmax * kMaxK + t},
+      flags{L.scr + (int64_t)5 * mmax * kMaxK + t};
+  const double lm = L.lam[t];
+  const double eps = DBL_EPSILON * fmax(L.tnorm[0], DBL_MIN);
+  // LU of T - lambda I with partial pivoting; ur[i] = 1 / U_ii
+  double ai = L.d[0] - lm;  // running diagonal entry of the active row
+  double ci = m > 1 ? L.e[0] : 0.0;
+  for (int i = 0; i + 1 < m; ++i) {
+    const double b = L.e[i];  // sub-diagonal entry below a_i
+    const double an = L.d[i + 1] - lm;
+    const double cn = i + 2 < m ? L.e[i + 1] : 0.0;
+    if (fabs(ai) >= fabs(b)) {
+      if (ai == 0.0) ai = eps;
+      const double r = 1.0 / ai;
+      ur[i] = r;
+      const double f = b * r;
+      l[i] = f;
+      c[i] = ci;
+      c2[i] = 0.0;
+      flags[i] = 0.0;
+      ai = an - f * ci;
+      ci = cn;
+    } else {
+      const double r = 1.0 / b;
+      ur[i] = r;
+      const double f = ai * r;
+      l[i] = f;
+      c[i] = an;
+      c2[i] = cn;
+      flags[i] = 1.0;
+      ai = ci - f * an;
+      ci = -f * cn;
+    }
+  }
+  if (ai == 0.0) ai = eps;
+  ur[m - 1] = 1.0 / ai;
+  c[m - 1] = 0.0;
+  c2[m - 1] = 0.0;
+  for (int i = 0; i < m; ++i) y[i] = hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7);
+  for (int it = 0; it < 3; ++it) {
+    // forward: apply L with row swaps
+    for (int i = 0; i + 1 < m; ++i) {
+      if (flags[i] != 0.0) {
+        const double t1 = y[i];
+        y[i] = y[i + 1];
+        y[i + 1] = t1 - l[i] * y[i];
+      } else {
+        y[i + 1] -= l[i] * y[i];
+      }
+    }
+    // backward: U y = rhs
+    double y1 = y[m - 1] * ur[m - 1], y2 = 0.0;
+    y[m - 1] = y1;
+    for (int i = m - 2; i >= 0; --i) {
+      const double yi = (y[i] - c[i] * y1 - c2[i] * y2) * ur[i];
+      y[i] = yi;
+      y2 = y1;
+      y1 = yi;
+    }
+    double nr = 0.0;
+    for (int i = 0; i < m; ++i) nr = fma(y[i], y[i], nr);
+    nr = 1.0 / sqrt(nr);
+    for (int i = 0; i < m; ++i) y[i] *= nr;
+  }
+  for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = y[i];
+}
+
+// --- clusters of close selected values: block classical Gram-Schmidt, applied
+// twice, in ascending order; all projections of one vector run in parallel
+// (one warp per earlier cluster member), so a cluster of c vectors costs
+// O(c) block synchronizations instead of O(c^2).
+__global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work, int mmax, double* F,
+                                                      int64_t ldf) {
+  __shared__ double dots[kMaxK];
   __shared__ double red[32];
   EigWork L = eig_layout(work, mmax);
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < m; i += nth) {
-    double a = L.ev[i];
-    int pos = 0;
-    for (int j = 0; j < m; ++j)
-      if (order_key_cmp(L.ev[j], j, a, i, op) < 0) ++pos;
-    L.ord[pos] = i;
-    ritz[pos] = a;
-  }
-  __syncthreads();
-  double tnorm = 0.0;
-  for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(L.ev[i]));
-  if (tid == 0) {
-    for (int t = 0; t < k; ++t) theta[t] = L.ev[L.ord[t]];
-    if (m > k) {
-      double a = L.ev[L.ord[k - 1]], b = L.ev[L.ord[k]];
-      double g = op == GREST_OP_ADJ ? fabs(fabs(a) - fabs(b)) : fabs(a - b);
-      info[0] = tnorm > 0.0 ? g / tnorm : 0.0;
-    } else {
-      info[0] = INFINITY;
-    }
-    // selected values sorted ascending, pulled apart by at least 10 eps ||T||
-    for (int t = 0; t < k; ++t) sel_sorted[t] = t;
-    for (int a = 1; a < k; ++a) {
-      int x = sel_sorted[a], b = a - 1;
-      while (b >= 0 && L.ev[L.ord[sel_sorted[b]]] > L.ev[L.ord[x]]) {
-        sel_sorted[b + 1] = sel_sorted[b];
-        --b;
-      }
-      sel_sorted[b + 1] = x;
-    }
-    const double sep = 10.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN);
-    for (int a = 0; a < k; ++a) {
-      double v = L.ev[L.ord[sel_sorted[a]]];
-      if (a > 0 && v < lam[sel_sorted[a - 1]] + sep) v = lam[sel_sorted[a - 1]] + sep;
-      lam[sel_sorted[a]] = v;
-    }
-  }
-  __syncthreads();
-  // inverse iteration on T - lambda I, one thread per selected pair
-  if (tid < k) {
-    const int t = tid;
-    // per-thread arrays interleaved across threads (coalesced): element i at [i * kMaxK]
-    struct Strided {
-      double* b;
-      __device__ double& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
-    };
-    const Strided a{L.scr + t}, c{L.scr + (int64_t)mmax * kMaxK + t}, c2{L.scr + (int64_t)2 * mmax * kMaxK + t},
-        l{L.scr + (int64_t)3 * mmax * kMaxK + t}, y{L.scr + (int64_t)4 * mmax * kMaxK + t};
-    const double lm = lam[t];
-    const double eps = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-    for (int i = 0; i < m; ++i) {
-      a[i] = L.d[i] - lm;
-      c[i] = (i + 1 < m) ? L.e[i] : 0.0;
-      c2[i] = 0.0;
-    }
-    // LU with partial pivoting (row swaps recorded in y, then moved to `flags`)
-    for (int i = 0; i + 1 < m; ++i) {
-      const double b = L.e[i];  // sub-diagonal entry below a[i]
-      if (fabs(a[i]) >= fabs(b)) {
-        if (a[i] == 0.0) a[i] = eps;
-        const double f = b / a[i];
-        l[i] = f;
-        a[i + 1] -= f * c[i];
-        y[i] = 0.0;  // not swapped
-      } else {
-        const double f = a[i] / b;
-        l[i] = f;
-        a[i] = b;
-        const double t1 = a[i + 1];
-        a[i + 1] = c[i] - f * t1;
-        if (i + 2 < m) {
-          c2[i] = c[i + 1];
-          c[i + 1] = -f * c[i + 1];
-        }
-        c[i] = t1;
-        y[i] = 1.0;  // swapped
-      }
-    }
-    if (a[m - 1] == 0.0) a[m - 1] = eps;
-    const Strided flags{L.scr + (int64_t)5 * mmax * kMaxK + t};
-    for (int i = 0; i < m; ++i) flags[i] = y[i];
-    for (int i = 0; i < m; ++i) y[i] = hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7);
-    for (int it = 0; it < 3; ++it) {
-      // forward: apply L with row swaps
-      for (int i = 0; i + 1 < m; ++i) {
-        if (flags[i] != 0.0) {
-          const double t1 = y[i];
-          y[i] = y[i + 1];
-          y[i + 1] = t1 - l[i] * y[i];
-        } else {
-          y[i + 1] -= l[i] * y[i];
-        }
-      }
-      // backward: U y = rhs
-      y[m - 1] /= a[m - 1];
-      if (m >= 2) y[m - 2] = (y[m - 2] - c[m - 2] * y[m - 1]) / a[m - 2];
-      for (int i = m - 3; i >= 0; --i) y[i] = (y[i] - c[i] * y[i + 1] - c2[i] * y[i + 2]) / a[i];
-      double nr = 0.0;
-      for (int i = 0; i < m; ++i) nr = fma(y[i], y[i], nr);
-      nr = 1.0 / sqrt(nr);
-      for (int i = 0; i < m; ++i) y[i] *= nr;
-    }
-    for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = y[i];
-  }
-  __syncthreads();
-  // clusters of close selected values: block classical Gram-Schmidt, applied
-  // twice, in ascending order; all projections of one vector run in parallel
-  // (one warp per earlier cluster member), so a cluster of c vectors costs
-  // O(c) block synchronizations instead of O(c^2)
-  __shared__ double dots[kMaxK];
-  const double ortol = 1e-3 * tnorm;
-  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const double ortol = 1e-3 * L.tnorm[0];
   for (int a = 1; a < k; ++a) {
-    const int ta = sel_sorted[a];
+    const int ta = L.sel[a];
     int b0 = a;
-    while (b0 > 0 && lam[sel_sorted[b0]] - lam[sel_sorted[b0 - 1]] < ortol) --b0;
+    while (b0 > 0 && L.lam[L.sel[b0]] - L.lam[L.sel[b0 - 1]] < ortol) --b0;
     if (b0 == a) continue;
     for (int pass = 0; pass < 2; ++pass) {
       for (int b = b0 + wid; b < a; b += nw) {
-        const int tb = sel_sorted[b];
+        const int tb = L.sel[b];
         double d = 0.0;
         for (int i = lane; i < m; i += 32) d = fma(F[(int64_t)i * ldf + tb], F[(int64_t)i * ldf + ta], d);
 #pragma unroll
@@ -400,7 +494,7 @@ __global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, doub
       __syncthreads();
       for (int i = tid; i < m; i += nth) {
         double y = F[(int64_t)i * ldf + ta];
-        for (int b = b0; b < a; ++b) y = fma(-dots[b - b0], F[(int64_t)i * ldf + sel_sorted[b]], y);
+        for (int b = b0; b < a; ++b) y = fma(-dots[b - b0], F[(int64_t)i * ldf + L.sel[b]], y);
         F[(int64_t)i * ldf + ta] = y;
       }
       __syncthreads();
@@ -414,13 +508,16 @@ __global__ void __launch_bounds__(256) k_select_invit(int m, int k, int op, doub
   }
 }
 
-// --- 5. F = Q Y, Q = P_0 P_1 ... P_{m-3}; one warp per selected vector
-__global__ void __launch_bounds__(256) k_backtransform(const double* H, int64_t ld, int m, int k, double* work,
-                                                       int mmax, double* F, int64_t ldf) {
-  extern __shared__ double xs[];  // 8 warps x m
+// --- 5. F = Q Y, Q = P_0 P_1 ... P_{m-3}; one warp per selected vector, four
+// warps per block (one per SM sub-partition).
+constexpr int kBtWarps = 4;
+
+__global__ void __launch_bounds__(kBtWarps * 32) k_backtransform(const double* H, int64_t ld, int m, int k,
+                                                                double* work, int mmax, double* F, int64_t ldf) {
+  extern __shared__ double xs[];  // kBtWarps x m
   EigWork L = eig_layout(work, mmax);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int t = blockIdx.x * 8 + wid;
+  const int t = blockIdx.x * kBtWarps + wid;
   if (t >= k) return;
   double* x = xs + wid * m;
   for (int i = lane; i < m; i += 32) x[i] = F[(int64_t)i * ldf + t];
@@ -443,20 +540,30 @@ __global__ void __launch_bounds__(256) k_backtransform(const double* H, int64_t 
 
 }  // namespace
 
-size_t eig_work_doubles(int mmax) { return (size_t)5 * mmax + (size_t)kMaxK * 6 * mmax + 64; }
+size_t eig_work_doubles(int mmax) { return (size_t)7 * mmax + 2 * kMaxK + 8 + (size_t)kMaxK * 6 * mmax + 64; }
 
-void sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
-                    double* info, double* work, cudaStream_t s) {
+bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, cudaStream_t s);
+
+int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
+                   double* info, double* work, cudaStream_t s) {
   const int mmax = m;
-  const size_t smem = sizeof(double) * ((size_t)m * (m + 1) / 2 + 2 * (size_t)m + 2);
-  if (reserve_dynamic_smem(k_tridiag_smem, smem)) {
-    k_tridiag_smem<<<1, 1024, smem, s>>>(H, ld, m, work, mmax);
-  } else {
-    k_tridiag<<<1, 1024, sizeof(double) * 2 * (m + 1), s>>>(H, ld, m, work, mmax);
+  EigWork L = eig_layout(work, mmax);
+  if (!tridiag_cluster(H, ld, m, L.d, L.e, L.beta, s)) {
+    const size_t smem = sizeof(double) * ((size_t)m * (m + 1) / 2 + 2 * (size_t)m + 2);
+    if (reserve_dynamic_smem(k_tridiag_smem, smem)) {
+      k_tridiag_smem<<<1, 1024, smem, s>>>(H, ld, m, work, mmax);
+    } else {
+      k_tridiag<<<1, 1024, sizeof(double) * 2 * (m + 1), s>>>(H, ld, m, work, mmax);
+    }
   }
-  k_multisect<<<(m + 7) / 8, 256, 0, s>>>(m, work, mmax);
-  k_select_invit<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, F, ldf, ritz, info);
-  k_backtransform<<<(k + 7) / 8, 256, sizeof(double) * 8 * m, s>>>(H, ld, m, k, work, mmax, F, ldf);
+  k_sturm_prep<<<1, 256, 0, s>>>(m, work, mmax);
+  k_multisect<<<m, 32, 0, s>>>(m, work, mmax);
+  k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info);
+  k_invit<<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+  k_cluster_orth<<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
+  k_backtransform<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(
+      H, ld, m, k, work, mmax, F, ldf);
+  return 7;
 }
 
 }  // namespace grest

@@ -71,6 +71,7 @@ struct grest_ctx {
   double* part = nullptr;
   int64_t part_cap = 0;
   int64_t* ipart = nullptr;
+  int* piv = nullptr;    // pivot order of the pivoted Cholesky (cmax + K ints)
   double* eigwork = nullptr;
   int32_t* err = nullptr;
   // batch staging
@@ -137,7 +138,7 @@ void free_ctx(grest_ctx* c) {
                   c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
                   c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
-                  c->ipart, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+                  c->ipart, c->piv, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_info) cudaFreeHost(c->h_info);
@@ -321,8 +322,7 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, 
 void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf,
          double* ritz, double* info) {
   int p = prof_begin(c);
-  sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, c->stream);
-  c->launches += 4;
+  c->launches += sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, c->stream);
   prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
@@ -358,8 +358,7 @@ grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n
                          int* rank_out) {
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
   int p = prof_begin(c);
-  pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->info + info_slot, c->stream);
-  c->launches += 1;
+  c->launches += pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot, c->stream);
   prof_end(c, p, 3, (double)w * w * w / 3.0 + (double)w * w * w / 3.0);
   int rank = w;
   if (read_rank) {
@@ -491,10 +490,10 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   spmm(c, c->U32, c->ldu, MU, c->ldu, K, 0, N2, 0);
   gram(c, U64, c->ldu, K, MU, c->ldu, K, N2, c->H, K, false);
   int p = prof_begin(c);
-  pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
+  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, s);
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
   symmetrize(c->Uh, K, K, s);
-  c->launches += 3;
+  c->launches += 2;
   prof_end(c, p, 3, 4.0 * K * K * K);
   eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48);
   k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
@@ -818,6 +817,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   c->part_cap = 8'000'000;  // FP64 partial sums of the split-K Gram kernels (64 MB)
   IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));
   IK(dalloc(&c->eigwork, eig_work_doubles(std::max(mm, c->q))));
+  IK(dalloc(&c->piv, std::max(mm, c->q) + 8));
   IK(dalloc(&c->err, 1));
   IK(cudaMallocHost((void**)&c->h_info, sizeof(double) * 64));
   IK(cudaMallocHost((void**)&c->h_err, sizeof(int32_t)));

@@ -1,0 +1,430 @@
+// Small dense FP64 factorizations spread over a thread-block cluster.
+//
+// The projected problems of a G-REST step are m x m with m ~ 30..320
+// (H = Z^T M Z of Eq. main2, the CholQR Gram matrices of the orthonormal
+// bases, the RSVD Gram B_s B_s^T of Sec. 3.5).  On GB300 one SM retires only
+// about two FP64 FMAs per clock (one warp instruction per ~68 clocks on each
+// of its four sub-partitions), so a single-CTA factorization is bound by one
+// SM's FP64 pipe.  Here the rows of the symmetric matrix are dealt
+// cyclically over the CTAs of a cluster (row i lives in CTA i mod C); every
+// CTA keeps its rows in shared memory, reads the few vectors it needs from
+// the others through distributed shared memory, and applies the rank-1 / 2
+// updates to its own rows.  Scalars (norms, pivots, reflector coefficients)
+// are computed redundantly and identically in every CTA from the same data
+// in the same order, so no broadcast step is needed.
+//
+//   k_tridiag_cl : Householder reduction to tridiagonal form (Alg. 1, first
+//                  step of the eigensolve of H), two cluster barriers per
+//                  column.
+//   k_pchol_cl   : Cholesky with symmetric (diagonal) pivoting of a Gram
+//                  matrix, with the drop rule of the orthonormalization
+//                  (CholQR with pivoting), one cluster barrier per pivot.
+//   k_trinv      : T = P R^{-1}, one warp per column (right-looking back
+//                  substitution), spread over many SMs.
+#include <cooperative_groups.h>
+#include <float.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace grest {
+
+namespace {
+
+constexpr int kClThreads = 256;
+
+// Fixed-order block sum (lane 0 of each warp, then warp 0); the result is
+// returned to every thread.  Identical inputs give identical results in every
+// CTA of the cluster.
+__device__ double cl_block_sum(double v, double* red, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) *out = s;
+  }
+  __syncthreads();
+  return *out;
+}
+
+// --- Householder tridiagonalization, rows cyclic over the cluster.
+// Input: H (m x m, ld), only the upper triangle is read (mirrored).
+// Output: d[0..m), e[0..m) (e[m-1] = 0), beta[0..m-2); the reflector of
+// column j (v with v_0 = x_0 - alpha) is stored in row j of H right of the
+// diagonal, as the back-transformation expects.
+__global__ void __launch_bounds__(kClThreads) k_tridiag_cl(double* H, int64_t ld, int m, double* d_out,
+                                                           double* e_out, double* beta_out) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int nl = (m + C - 1) / C;
+  extern __shared__ double sm[];
+  double* A = sm;                     // nl x m: local row li is global row r + C li
+  double* v = A + (size_t)nl * m;     // reflector (global column index)
+  double* w = v + m;                  // p, then w = p - K v
+  double* pl = w + m;                 // p_i of the owned rows
+  __shared__ double red[32];
+  __shared__ double bc[4];
+  for (int li = wid; li < nl; li += nw) {
+    const int i = r + C * li;
+    if (i >= m) break;
+    for (int l = lane; l < m; l += 32) A[(size_t)li * m + l] = i <= l ? H[(int64_t)i * ld + l] : H[(int64_t)l * ld + i];
+  }
+  for (int j = 0; j + 2 < m; ++j) {
+    cl.sync();  // row j final; every CTA done with the previous step's p
+    const int o = j % C;
+    const double* Aj = cl.map_shared_rank(A, o) + (size_t)(j / C) * m;
+    double s = 0.0;
+    for (int l = j + 1 + tid; l < m; l += nth) {
+      const double x = Aj[l];
+      v[l] = x;
+      s = fma(x, x, s);
+    }
+    const double nrm2 = cl_block_sum(s, red, bc);
+    if (tid == 0) {
+      const double x0 = v[j + 1];
+      const double alpha = nrm2 > 0.0 ? -copysign(sqrt(nrm2), x0) : 0.0;
+      const double beta = nrm2 > 0.0 ? 1.0 / (nrm2 - alpha * x0) : 0.0;
+      v[j + 1] = x0 - alpha;
+      bc[1] = alpha;
+      bc[2] = beta;
+    }
+    __syncthreads();
+    const double beta = bc[2];
+    if (r == o) {
+      for (int l = j + 1 + tid; l < m; l += nth) H[(int64_t)j * ld + l] = v[l];
+      if (tid == 0) {
+        d_out[j] = A[(size_t)(j / C) * m + j];
+        e_out[j] = bc[1];
+        beta_out[j] = beta;
+      }
+    }
+    if (beta == 0.0) continue;  // same decision in every CTA
+    // p_i = beta (B v)_i for the owned rows i > j, one warp per row
+    const int f = j + 1 - r;
+    const int li0 = f <= 0 ? 0 : (f + C - 1) / C;
+    for (int li = li0 + wid; li < nl; li += nw) {
+      if (r + C * li >= m) break;
+      const double* row = A + (size_t)li * m;
+      double a = 0.0;
+      for (int l = j + 1 + lane; l < m; l += 32) a = fma(row[l], v[l], a);
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) a += __shfl_down_sync(0xffffffffu, a, o2);
+      if (lane == 0) pl[li] = beta * a;
+    }
+    cl.sync();  // all p_i written
+    double t = 0.0;
+    for (int i = j + 1 + tid; i < m; i += nth) {
+      const double pi = cl.map_shared_rank(pl, i % C)[i / C];
+      w[i] = pi;
+      t = fma(pi, v[i], t);
+    }
+    const double K = 0.5 * beta * cl_block_sum(t, red, bc);
+    for (int i = j + 1 + tid; i < m; i += nth) w[i] -= K * v[i];
+    __syncthreads();
+    // rank-2 update of the owned rows: B -= v w^T + w v^T
+    for (int li = li0 + wid; li < nl; li += nw) {
+      const int i = r + C * li;
+      if (i >= m) break;
+      double* row = A + (size_t)li * m;
+      const double vi = v[i], wi = w[i];
+      for (int l = j + 1 + lane; l < m; l += 32) row[l] -= vi * w[l] + wi * v[l];
+    }
+  }
+  cl.sync();
+  if (tid == 0) {
+    if (m >= 2) {
+      if ((m - 2) % C == r) {
+        d_out[m - 2] = A[(size_t)((m - 2) / C) * m + m - 2];
+        e_out[m - 2] = A[(size_t)((m - 2) / C) * m + m - 1];
+      }
+      if ((m - 1) % C == r) d_out[m - 1] = A[(size_t)((m - 1) / C) * m + m - 1];
+    } else if (r == 0) {
+      d_out[0] = A[0];
+    }
+    if (r == 0) e_out[m - 1] = 0.0;
+  }
+}
+
+// Order-preserving integer image of a non-negative double (negative values,
+// which cannot win a pivot search, map to -1).
+__device__ __forceinline__ long long pivot_key(double x) { return x >= 0.0 ? __double_as_longlong(x) : -1ll; }
+
+// --- Cholesky with diagonal pivoting of the Gram matrix G (c x c, upper
+// triangle read), rows cyclic over the cluster.  Pivot k is the largest
+// remaining Schur-complement diagonal (lowest index on ties); factorization
+// stops at the first pivot with R_kk^2 <= drop_tol^2 max(R_00^2, abs_ref^2)
+// (|abs_ref_ptr[0]| if given).  No rows are swapped: the Schur row of pivot
+// k stays in its owner's shared memory and becomes row k of R.
+// Output: Rt (in place of G): Rt[t][k] = R_{k,t} for k < t < rank and
+// Rt[k][k] = 1 / R_kk (pivot order); piv[0..c) (kept pivots first, then the
+// dropped indices ascending); info[0..3] = rank, kept_min, dropped_max, 0.
+__global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, int c, double drop_tol,
+                                                         double abs_ref, const double* abs_ref_ptr, int* piv_out,
+                                                         double* info) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int nl = (c + C - 1) / C;
+  extern __shared__ double sm[];
+  double* A = sm;                        // nl x c Schur rows (original index space)
+  double* Rk = A + (size_t)nl * c;       // current row of R (original index space)
+  double* rinv = Rk + c;                 // 1 / R_kk
+  int* piv = reinterpret_cast<int*>(rinv + c);
+  int* done = piv + c;                   // pivoted already
+  __shared__ long long slot_key[2];
+  __shared__ int slot_idx[2];
+  __shared__ double s_ref, s_rinv, s_kept, s_dropped;
+  __shared__ int s_p, s_stop, s_rank;
+  for (int li = wid; li < nl; li += nw) {
+    const int i = r + C * li;
+    if (i >= c) break;
+    for (int l = lane; l < c; l += 32) A[(size_t)li * c + l] = i <= l ? G[(int64_t)i * ld + l] : G[(int64_t)l * ld + i];
+  }
+  for (int l = tid; l < c; l += nth) done[l] = 0;
+  if (tid == 0) {
+    s_rank = c;
+    s_kept = 0.0;
+    s_dropped = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < c; ++k) {
+    // local candidate: largest diagonal of the owned, not yet pivoted rows
+    if (wid == 0) {
+      long long bk = -2;
+      int bi = c;
+      for (int li = lane; li < nl; li += 32) {
+        const int i = r + C * li;
+        if (i < c && !done[i]) {
+          const long long key = pivot_key(A[(size_t)li * c + i]);
+          if (key > bk || (key == bk && i < bi)) { bk = key; bi = i; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+      }
+      if (lane == 0) {
+        slot_key[k & 1] = bk;
+        slot_idx[k & 1] = bi;
+      }
+    }
+    cl.sync();  // candidates posted; the previous step's updates are complete
+    if (wid == 0) {
+      long long bk = -2;
+      int bi = c;
+      if (lane < C) {
+        bk = cl.map_shared_rank(slot_key, lane)[k & 1];
+        bi = cl.map_shared_rank(slot_idx, lane)[k & 1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+      }
+      if (lane == 0) {
+        const double v = bk >= 0 ? __longlong_as_double(bk) : -1.0;
+        if (k == 0) {
+          const double a = abs_ref_ptr ? fabs(*abs_ref_ptr) : abs_ref;
+          s_ref = fmax(v, a * a);
+        }
+        const double ref = s_ref;
+        if (bi >= c || !(v > 0.0) || !(v > drop_tol * drop_tol * ref) || !isfinite(v)) {
+          s_stop = 1;
+          s_rank = k;
+          s_dropped = (ref > 0.0 && v > 0.0) ? sqrt(v / ref) : 0.0;
+        } else {
+          s_stop = 0;
+          const double rkk = sqrt(v);
+          s_rinv = 1.0 / rkk;
+          s_kept = ref > 0.0 ? rkk / sqrt(ref) : 0.0;
+          s_p = bi;
+          piv[k] = bi;
+          rinv[k] = s_rinv;
+          done[bi] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;  // same decision in every CTA
+    const int p = s_p;
+    const double ri = s_rinv;
+    const double* Ap = cl.map_shared_rank(A, p % C) + (size_t)(p / C) * c;
+    for (int l = tid; l < c; l += nth) Rk[l] = done[l] ? 0.0 : Ap[l] * ri;
+    __syncthreads();
+    // Schur update of the owned rows that are not pivoted yet
+    for (int li = wid; li < nl; li += nw) {
+      const int i = r + C * li;
+      if (i >= c) break;
+      if (done[i]) continue;
+      const double rki = Rk[i];
+      double* row = A + (size_t)li * c;
+      for (int l = lane; l < c; l += 32) row[l] = fma(-rki, Rk[l], row[l]);
+    }
+    __syncthreads();
+  }
+  cl.sync();  // no CTA leaves while its rows may still be read
+  const int rk = s_rank;
+  // dropped indices (ascending) complete the permutation
+  if (tid == 0) {
+    int t = rk;
+    for (int l = 0; l < c; ++l)
+      if (!done[l]) piv[t++] = l;
+  }
+  __syncthreads();
+  // Rt[t][k] = R_{k,t} = S_k[piv[t]] / R_kk for the rows k this CTA owns
+  for (int k = 0; k < rk; ++k) {
+    const int p = piv[k];
+    if (p % C != r) continue;
+    const double* Sk = A + (size_t)(p / C) * c;
+    for (int t = k + tid; t < rk; t += nth) G[(int64_t)t * ld + k] = t == k ? rinv[k] : Sk[piv[t]] * rinv[k];
+  }
+  if (r == 0) {
+    for (int l = tid; l < c; l += nth) piv_out[l] = piv[l];
+    if (tid == 0) {
+      info[0] = rk;
+      info[1] = rk > 0 ? s_kept : 0.0;
+      info[2] = s_dropped;
+      info[3] = 0.0;
+    }
+  }
+}
+
+// --- T = P R^{-1} (c x c, zero columns >= rank): warp j solves R x = e_j by
+// a right-looking back substitution, x_j = 1/R_jj, and for t = j..1 the
+// partial sums s_i += R_{i,t} x_t (i < t) give x_{t-1} = -s_{t-1} / R_{t-1,t-1}.
+// Rt holds R transposed with reciprocal diagonal (k_pchol_cl).
+constexpr int kTrinvWarps = 4;
+
+__global__ void __launch_bounds__(kTrinvWarps * 32) k_trinv(const double* Rt, int64_t ld, const int* piv,
+                                                            const double* info, int c, double* T, int64_t ldt) {
+  extern __shared__ double xs[];  // kTrinvWarps x c
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int j = blockIdx.x * kTrinvWarps + wid;
+  if (j >= c) return;
+  const int rk = (int)info[0];
+  if (j >= rk) {
+    for (int i = lane; i < c; i += 32) T[(int64_t)i * ldt + j] = 0.0;
+    return;
+  }
+  double* s = xs + (size_t)wid * c;
+  for (int i = lane; i < j; i += 32) s[i] = 0.0;
+  double xt = Rt[(int64_t)j * ld + j];
+  if (lane == 0) s[j] = xt;
+  __syncwarp();
+  for (int t = j; t >= 1; --t) {
+    const double* col = Rt + (int64_t)t * ld;  // col[i] = R_{i,t}, i < t
+    for (int i = lane; i < t; i += 32) s[i] = fma(col[i], xt, s[i]);
+    __syncwarp();
+    xt = -s[t - 1] * Rt[(int64_t)(t - 1) * ld + (t - 1)];
+    __syncwarp();
+    if (lane == 0) s[t - 1] = xt;
+    __syncwarp();
+  }
+  for (int i = lane; i < c; i += 32) T[(int64_t)piv[i] * ldt + j] = i <= j ? s[i] : 0.0;
+}
+
+// True when `kern` can be launched as one cluster of C CTAs with `smem` bytes
+// of dynamic shared memory each (answers are cached per kernel, size, C).
+template <typename K>
+bool cluster_ok(K kern, size_t smem, int C) {
+  struct Entry {
+    const void* k;
+    size_t smem;
+    int C;
+    bool ok;
+  };
+  static Entry cache[128];
+  static int n_cache = 0;
+  for (int i = 0; i < n_cache; ++i)
+    if (cache[i].k == (const void*)kern && cache[i].smem == smem && cache[i].C == C) return cache[i].ok;
+  bool ok = false;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, kern) == cudaSuccess && smem + fa.sharedSizeBytes <= (size_t)optin &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+      (C <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
+  }
+  cudaGetLastError();
+  if (n_cache < 128) cache[n_cache++] = Entry{(const void*)kern, smem, C, ok};
+  return ok;
+}
+
+template <typename K, typename... Args>
+bool launch_cl(K kern, int C, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, kern, args...) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+int want_cluster(int m) { return m >= 96 ? 16 : 8; }
+
+}  // namespace
+
+bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, cudaStream_t s) {
+  if (m < 1) return true;
+  for (int C = want_cluster(m); C >= 2; C >>= 1) {
+    const int nl = (m + C - 1) / C;
+    const size_t smem = sizeof(double) * ((size_t)nl * m + 2 * (size_t)m + nl);
+    if (!cluster_ok(k_tridiag_cl, smem, C)) continue;
+    if (launch_cl(k_tridiag_cl, C, smem, s, H, ld, m, d, e, beta)) return true;
+  }
+  return false;
+}
+
+bool pchol_cluster(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                   double* T, int64_t ldt, int* piv, double* info, cudaStream_t s) {
+  if (c < 1) return false;
+  const size_t tsmem = sizeof(double) * kTrinvWarps * (size_t)c;
+  if (!reserve_dynamic_smem(k_trinv, tsmem)) return false;
+  for (int C = want_cluster(c); C >= 2; C >>= 1) {
+    const int nl = (c + C - 1) / C;
+    const size_t smem = sizeof(double) * ((size_t)nl * c + 2 * (size_t)c) + sizeof(int) * 2 * (size_t)c;
+    if (!cluster_ok(k_pchol_cl, smem, C)) continue;
+    if (!launch_cl(k_pchol_cl, C, smem, s, G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, piv, info)) continue;
+    k_trinv<<<(unsigned)((c + kTrinvWarps - 1) / kTrinvWarps), kTrinvWarps * 32, tsmem, s>>>(G, ldg, piv, info, c,
+                                                                                               T, ldt);
+    return true;
+  }
+  return false;
+}
+
+}  // namespace grest
