@@ -241,6 +241,26 @@ grest_status grest_gram_f32(grest_ctx *ctx, const float *X, int64_t ldx, int32_t
                             int32_t b, int64_t n, double *C, int64_t ldc);
 
 /*
+ * Out = beta Cin + alpha X B for FP32 device blocks: X (n x a, ldx), Cin and
+ * Out (n x c, ldc, ldo), row-major; B (a x c, ldb) FP64 on the device, c <=
+ * 256 for the tensor-core path.  This is the block update of the
+ * mixed-precision step (the projections X - U (U^T X), the CholQR products
+ * V T, the lift Z F_K of Alg. 2).  On sm_100-class GPUs it runs on the tensor
+ * cores (tcgen05 kind::tf32 with X and B each split into two TF32 parts,
+ * three products, FP32 accumulation over the a columns); shapes or
+ * alignments the tensor-core kernel does not take (X not 16-byte aligned, ldx
+ * not a multiple of 4, c > 256, a > 512) use a CUDA-core FP32 kernel.  Cin
+ * may equal Out (in-place update); X must not overlap Out.  Cin is not read
+ * when beta == 0.  Runs on the context's stream and uses its scratch;
+ * returns when Out is complete.  Errors: GREST_ERR_INVALID_ARG for null
+ * pointers or leading dimensions smaller than the widths,
+ * GREST_ERR_TIMEOUT if a device-side wait of the tensor-core kernel gave up.
+ */
+grest_status grest_gemm_f32(grest_ctx *ctx, int64_t n, int32_t a, int32_t c, double alpha, const float *X,
+                            int64_t ldx, const double *B, int64_t ldb, double beta, const float *Cin, int64_t ldc,
+                            float *Out, int64_t ldo);
+
+/*
  * grest_gram_noalloc -- the same product as grest_gram, C = X^T Y, for
  * callers that cannot allocate device memory: a host application that hands
  * all of the GPU's memory to its own pool (a cudaMalloc would fail or break

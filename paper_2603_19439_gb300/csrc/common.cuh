@@ -184,6 +184,15 @@ void convert_f64_to_f32(const double* src, int64_t lds, float* dst, int64_t ldd,
 void residual_norms(const double* MX, const double* X, int64_t ld, int w, const double* theta, int64_t n,
                     double* part, double* out, cudaStream_t s);
 
+// tc_gemm.cu: tensor-core (3xTF32) Out = beta Cin + alpha X B, X n x a FP32
+// row-major, B a x c FP64 row-major (c <= 256).  img: device scratch of at
+// least gemm_tc_img_bytes(a, c) bytes.  Returns 0 when enqueued (two kernels),
+// -1 when the shape or alignment is not supported (nothing enqueued).
+size_t gemm_tc_img_bytes(int a, int c);
+int gemm_f32_tc(int64_t n, int a, int c, double alpha, const float* X, int64_t ldx, const double* B, int64_t ldb,
+                double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, uint8_t* img, size_t img_cap,
+                int32_t* err, cudaStream_t s);
+
 // eig.cu
 // Symmetric eigensolver for H (m x m row-major, ld; overwritten).  Writes the
 // k leading pairs in tracking order: theta[k], F (m x k row-major, ldf), all m

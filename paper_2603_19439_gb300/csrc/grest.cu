@@ -72,6 +72,8 @@ struct grest_ctx {
   int64_t part_cap = 0;
   int64_t* ipart = nullptr;
   int* piv = nullptr;    // pivot order of the pivoted Cholesky (cmax + K ints)
+  uint8_t* gemm_img = nullptr;  // tensor-core GEMM: B^T operand images
+  size_t gemm_img_cap = 0;
   double* eigwork = nullptr;
   int32_t* err = nullptr;
   // batch staging
@@ -138,7 +140,7 @@ void free_ctx(grest_ctx* c) {
                   c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
                   c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
-                  c->ipart, c->piv, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+                  c->ipart, c->piv, c->gemm_img, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_info) cudaFreeHost(c->h_info);
@@ -314,8 +316,13 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X,
 void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, int64_t ldx, const double* B,
           int64_t ldb, double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo) {
   int p = prof_begin(c);
-  gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
-  if (n > 0 && cc > 0) c->launches += 1;
+  if (n > 0 && cc > 0 && gemm_f32_tc(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->gemm_img,
+                                     c->gemm_img_cap, c->err, c->stream) == 0) {
+    c->launches += 2;
+  } else {
+    gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
+    if (n > 0 && cc > 0) c->launches += 1;
+  }
   prof_end(c, p, 2, 2.0 * n * a * cc);
 }
 
@@ -818,6 +825,8 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));
   IK(dalloc(&c->eigwork, eig_work_doubles(std::max(mm, c->q))));
   IK(dalloc(&c->piv, std::max(mm, c->q) + 8));
+  c->gemm_img_cap = gemm_tc_img_bytes(512, 256);
+  IK(dalloc(&c->gemm_img, c->gemm_img_cap));
   IK(dalloc(&c->err, 1));
   IK(cudaMallocHost((void**)&c->h_info, sizeof(double) * 64));
   IK(cudaMallocHost((void**)&c->h_err, sizeof(int32_t)));
@@ -1057,6 +1066,24 @@ grest_status grest_gram_f32(grest_ctx* c, const float* X, int64_t ldx, int32_t a
     if (gram_parts(n, a, b) * (int64_t)a * b > c->part_cap) return GREST_ERR_CAPACITY;
     gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);
   }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return *c->h_err ? map_dev_err(*c->h_err) : GREST_OK;
+}
+
+grest_status grest_gemm_f32(grest_ctx* c, int64_t n, int32_t a, int32_t cc, double alpha, const float* X, int64_t ldx,
+                            const double* B, int64_t ldb, double beta, const float* Cin, int64_t ldc, float* Out,
+                            int64_t ldo) {
+  if (!c || !X || !B || !Out || a < 1 || cc < 1 || n < 0 || ldx < a || ldb < cc || ldo < cc ||
+      (beta != 0.0 && (!Cin || ldc < cc)))
+    return GREST_ERR_INVALID_ARG;
+  if (n == 0) return GREST_OK;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
+  if (gemm_f32_tc(n, a, cc, alpha, X, ldx, B, ldb, beta, beta != 0.0 ? Cin : nullptr, ldc, Out, ldo, c->gemm_img,
+                  c->gemm_img_cap, c->err, c->stream) != 0)
+    gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, beta != 0.0 ? Cin : nullptr, ldc, Out, ldo, c->stream);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -5,150 +5,158 @@
 // Precision: each FP32 value x is split into x_hi = tf32(x) and
 // x_lo = tf32(x - x_hi) (round to nearest), and x y ~ x_hi y_hi + x_hi y_lo +
 // x_lo y_hi (three kind::tf32 MMAs), which keeps products at about 2^-22
-// relative error; the FP32 accumulator in tensor memory is drained into FP64
-// partial sums every kFlushChunks x 32 rows.
+// relative error.  The FP32 accumulator in tensor memory spans 256 rows; it
+// is then added into double-float (FP32 hi + lo, two-sum) accumulators held
+// in registers, and each CTA's result is written once as FP64.
 //
-// Per CTA: one 128-column tile of X (rows of the MMA's M) against all of Y
-// (N <= 256), over a contiguous range of rows (the MMA's K).  TMA copies raw
-// 32-row tiles of X and Y into a ring of staging buffers; the CTA's threads
-// transpose them into K-major, 128B-swizzled hi / lo operand tiles; one
-// thread issues the MMAs and commits them to mbarriers.  Every wait on an
-// mbarrier is bounded; on timeout the kernel records an error and leaves.
-#include <cuda.h>
-
-#include "common.cuh"
+// Each CTA owns a 128 x 128 tile of C (the upper tiles only when X = Y) and a
+// contiguous range of rows (the MMA's K).  The contraction runs over rows, so
+// the operands (K-major: each operand row is one column of X or Y with its
+// rows contiguous) are transposes of the row-major blocks; kind::tf32 takes
+// K-major operands only (a transposed-operand descriptor produced no result
+// on this part), so the transpose is done in shared memory, pipelined:
+//   warp 0     TMA producer: raw 32-row tiles of X and Y into a ring
+//   warp 1     tensor-memory owner and MMA issuer (one thread)
+//   warps 2-9  transpose + hi / lo split of each raw tile into a ring of
+//              128B-swizzled operand tiles; every 256 rows, drain the
+//              previous span's accumulator (double-buffered in tensor
+//              memory) into the double-float registers
+// Every mbarrier wait is bounded; on a timeout the kernel records an error,
+// waits (bounded) for its own copies and MMAs in flight, frees its tensor
+// memory and returns.
+#include "tc_util.cuh"
 
 namespace grest {
 
+using namespace tc;
+
 namespace {
 
-constexpr int kRows = 32;         // rows (MMA K) per chunk: 128 B of TF32 per operand row
-constexpr int kFlushChunks = 8;   // FP32 accumulation spans 256 rows before the FP64 flush
-constexpr int kThreads = 128;
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of element (row, k) in a K-major tile with 128-byte rows, 128B swizzle
-__device__ __forceinline__ uint32_t sw128(int row, int kbyte) {
-  return (row >> 3) * 1024 + (row & 7) * 128 + ((((kbyte >> 4) ^ (row & 7)) & 7) << 4) + (kbyte & 15);
-}
-
-// tcgen05 shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
-  return d;
-}
-
-// instruction descriptor: D F32, A and B TF32, both K-major, M x N
-__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-  }
-  return done != 0;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-               :: "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-               :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                 "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-constexpr int kMaxStages = 6;
+constexpr int kRows = 32;          // rows (MMA K) per chunk: 128 B of TF32 per operand row
+constexpr int kSpan = 8;           // chunks per FP32 accumulation span (256 rows)
+constexpr int kTileG = 128;        // C tile edge
+constexpr int kGramThreads = 320;  // 10 warps
+constexpr int kOpBytes = 128 * 128;  // one 128-row K-major operand tile (32 TF32 per row), swizzled
+constexpr int kMaxRaw = 4, kMaxOp = 2;
 constexpr int kSmemBudget = 225 * 1024;
 
-// Convert 16-row half h of a staged raw tile (rows x `pitch` floats, row-major)
-// into the hi / lo K-major swizzled operand tiles: operand row r = raw column r.
-__device__ __forceinline__ void convert_half(const float* __restrict__ raw, int pitch, int rows_op, int r_begin,
-                                             int r_step, int h, uint8_t* __restrict__ hi_t, uint8_t* __restrict__ lo_t) {
-  for (int r = r_begin; r < rows_op; r += r_step) {
+struct GramArgs {
+  int a, b, n_tiles_m, sym;
+  int bxw, byw;          // TMA box widths (columns) of X and Y
+  int N;                 // MMA N (multiple of 16, <= 128)
+  int raw_stages, op_stages;
+  int64_t n, rows_per_split;
+  double* partT;         // [split][col][row]: b x a doubles per split
+  int32_t* err;
+};
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += e;
+}
+
+// Transpose + split one raw tile (kRows rows x w columns, row-major) into the
+// hi / lo operand tiles: operand row r = raw column r, K = raw row.
+template <int Q0, int Q1>
+__device__ __forceinline__ void convert_tile(const float* __restrict__ raw, int w, int r, uint8_t* __restrict__ hi_t,
+                                             uint8_t* __restrict__ lo_t) {
+  if (r >= w) return;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int kq = 4 * h + q;
-      float4 hi, lo;
-      const float v0 = raw[(4 * kq + 0) * pitch + r], v1 = raw[(4 * kq + 1) * pitch + r];
-      const float v2 = raw[(4 * kq + 2) * pitch + r], v3 = raw[(4 * kq + 3) * pitch + r];
-      hi.x = tf32_rna(v0); lo.x = tf32_rna(v0 - hi.x);
-      hi.y = tf32_rna(v1); lo.y = tf32_rna(v1 - hi.y);
-      hi.z = tf32_rna(v2); lo.z = tf32_rna(v2 - hi.z);
-      hi.w = tf32_rna(v3); lo.w = tf32_rna(v3 - hi.w);
-      *(float4*)(hi_t + sw128(r, 16 * kq)) = hi;
-      *(float4*)(lo_t + sw128(r, 16 * kq)) = lo;
-    }
+  for (int q = Q0; q < Q1; ++q) {
+    float4 hi, lo;
+    const float v0 = raw[(4 * q + 0) * w + r], v1 = raw[(4 * q + 1) * w + r];
+    const float v2 = raw[(4 * q + 2) * w + r], v3 = raw[(4 * q + 3) * w + r];
+    hi.x = tf32_rna(v0); lo.x = tf32_rna(v0 - hi.x);
+    hi.y = tf32_rna(v1); lo.y = tf32_rna(v1 - hi.y);
+    hi.z = tf32_rna(v2); lo.z = tf32_rna(v2 - hi.z);
+    hi.w = tf32_rna(v3); lo.w = tf32_rna(v3 - hi.w);
+    *(float4*)(hi_t + sw128(r, 16 * q)) = hi;
+    *(float4*)(lo_t + sw128(r, 16 * q)) = lo;
   }
 }
 
-// partT[chunk][j][i] (b x a doubles per chunk, transposed so that lanes, which
-// own rows i, store contiguously) receives the CTA's partial X^T Y.
-//
-// Shared memory: `stages` raw TMA buffers of kRows x (bx + by) floats (a ring,
-// refilled as soon as a chunk has been converted), then the hi / lo operand
-// tiles A (128 x 128 B) and B (by x 128 B).  Each 32-row chunk is converted and
-// multiplied in two 16-row halves (16-byte chunks 0-3 and 4-7 of the swizzled
-// 128-byte operand rows), so converting one half overlaps the MMAs of the
-// other; threads 0-127 convert X, threads 128-255 convert Y.
-__global__ void __launch_bounds__(2 * kThreads, 1)
-    k_gram_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, int a, int b,
-              int bx, int by, int stages, int64_t n, int64_t rows_per_cta, double* __restrict__ partT, int32_t* err) {
+// Add span sp's FP32 accumulator (buffer sp & 1) into the double-float
+// accumulators of this thread's C row and 64 columns.
+__device__ __forceinline__ bool drain_span(int sp, uint32_t tmem, int N, int quarter, int colhalf, int lane,
+                                           uint64_t* accf, uint64_t* acce, float (&hi)[64], float (&lo)[64]) {
+  const int b = sp & 1;
+  if (!mbar_wait(&accf[b], (uint32_t)((sp >> 1) & 1))) return false;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (colhalf * 64 < N) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * N + colhalf * 64), v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]));
+    if (colhalf * 64 + 32 < N) {
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * N + colhalf * 64 + 32), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) two_sum_acc(hi[32 + j], lo[32 + j], __uint_as_float(v[j]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&acce[b]);
+  return true;
+}
+
+__global__ void __launch_bounds__(kGramThreads, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, const GramArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[kMaxStages];
-  __shared__ __align__(8) uint64_t mma_bar[2];
+  __shared__ __align__(8) uint64_t raw_full[kMaxRaw], raw_empty[kMaxRaw], op_full[kMaxOp], op_empty[kMaxOp];
+  __shared__ __align__(8) uint64_t accf[2], acce[2], donebar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ta = blockIdx.x;
-  const int64_t chunk = blockIdx.y;
-  const int64_t r0 = chunk * rows_per_cta;
-  int64_t r1 = r0 + rows_per_cta;
-  if (r1 > n) r1 = n;
+  // tile of C
+  int tm = 0, tn = 0;
+  {
+    int t = blockIdx.x;
+    if (p.sym) {
+      // upper-triangular enumeration: row tm holds tiles tm..T-1
+      const int T = p.n_tiles_m;
+      while (t >= T - tm) { t -= T - tm; ++tm; }
+      tn = tm + t;
+    } else {
+      tm = t % p.n_tiles_m;
+      tn = t / p.n_tiles_m;
+    }
+  }
+  const int m0 = tm * kTileG, n0 = tn * kTileG;
+  const bool diag = p.sym && tm == tn;  // X = Y and the same columns: load and convert X only
+  const int64_t r0 = (int64_t)blockIdx.y * p.rows_per_split;
+  int64_t r1 = r0 + p.rows_per_split;
+  if (r1 > p.n) r1 = p.n;
   const int nloc = r1 > r0 ? (int)((r1 - r0 + kRows - 1) / kRows) : 0;
-  const int ncols = by <= 32 ? 32 : by <= 64 ? 64 : by <= 128 ? 128 : 256;
-  const int raw_stage = kRows * (bx + by) * 4;
-  const int raw_total = ((stages * raw_stage + 1023) / 1024) * 1024;
-  uint8_t* Ahi = sm + raw_total;
-  uint8_t* Alo = Ahi + 128 * 128;
-  uint8_t* Bhi = Alo + 128 * 128;
-  uint8_t* Blo = Bhi + by * 128;
+  const int R = p.raw_stages, S = p.op_stages, N = p.N;
+  const int raw_bytes = kRows * (p.bxw + p.byw) * 4;
+  const int raw_stride = ((raw_bytes + 1023) / 1024) * 1024;
+  const int op_b_bytes = N * 128;
+  const int op_stride = 2 * kOpBytes + 2 * op_b_bytes;
+  uint8_t* raw0 = sm;
+  uint8_t* op0 = sm + (size_t)R * raw_stride;
   if (tid == 0) {
-    for (int q = 0; q < stages; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[q])));
-    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[q])));
+    for (int q = 0; q < R; ++q) {
+      mbar_init(&raw_full[q], 1);
+      mbar_init(&raw_empty[q], 8);
+    }
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&op_full[q], 8);
+      mbar_init(&op_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], 8);
+    }
+    mbar_init(&donebar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
-  if (warp == 0) {
+  const uint32_t ncols = N <= 64 ? 128u : 256u;
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tmem_base)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -156,100 +164,183 @@ __global__ void __launch_bounds__(2 * kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_tf32(128, by);
-  const uint32_t tx_bytes = (uint32_t)raw_stage;
-  // prologue: fill the ring
-  if (tid == 0) {
-    for (int i = 0; i < stages && i < nloc; ++i) {
-      uint8_t* dst = sm + i * raw_stage;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(tx_bytes)
-                   : "memory");
-      tma_load_2d(dst, &mapX, ta * 128, (int)(r0 + (int64_t)i * kRows), &full[i]);
-      tma_load_2d(dst + kRows * bx * 4, &mapY, 0, (int)(r0 + (int64_t)i * kRows), &full[i]);
+  const int nspans = (nloc + kSpan - 1) / kSpan;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0 && nloc > 0) {
+      int issued = 0;
+      for (int q = 0; q < nloc; ++q) {
+        const int st = q % R;
+        if (q >= R && !mbar_wait(&raw_empty[st], (uint32_t)(((q / R) - 1) & 1))) { abort_flag = 1; break; }
+        if (abort_flag) break;
+        uint8_t* dst = raw0 + (size_t)st * raw_stride;
+        const int y = (int)(r0 + (int64_t)q * kRows);
+        mbar_expect_tx(&raw_full[st], (uint32_t)(diag ? kRows * p.bxw * 4 : raw_bytes));
+        tma_load_2d(dst, &mapX, m0, y, &raw_full[st]);
+        if (!diag) tma_load_2d(dst + kRows * p.bxw * 4, &mapY, n0, y, &raw_full[st]);
+        issued = q + 1;
+      }
+      for (int q = issued - R > 0 ? issued - R : 0; q < issued; ++q)
+        mbar_wait(&raw_full[q % R], (uint32_t)((q / R) & 1));
     }
-  }
-  bool first_flush = true;
-  for (int i = 0; i < nloc; ++i) {
-    const int s = i % stages;
-    const float* rawx = (const float*)(sm + s * raw_stage);
-    const float* rawy = rawx + kRows * bx;
-    if (!mbar_wait(&full[s], (uint32_t)((i / stages) & 1))) abort_flag = 1;
-    for (int h = 0; h < 2; ++h) {
-      // this half of the operand tiles is free once its MMAs of the previous chunk are done
-      if (i > 0 && !mbar_wait(&mma_bar[h], (uint32_t)((i - 1) & 1))) abort_flag = 1;
-      if (tid < kThreads)
-        convert_half(rawx, bx, bx, tid, kThreads, h, Ahi, Alo);
-      else
-        convert_half(rawy, by, by, tid - kThreads, kThreads, h, Bhi, Blo);
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0 && nloc > 0) {
+      const uint32_t idesc = idesc_tf32(128, N);
+      bool ok = true;
+      for (int q = 0; ok && q < nloc; ++q) {
+        const int sp = q / kSpan, b = sp & 1;
+        if (q % kSpan == 0 && sp >= 2 && !mbar_wait(&acce[b], (uint32_t)(((sp - 2) >> 1) & 1))) { ok = false; break; }
+        const int st = q % S;
+        if (!mbar_wait(&op_full[st], (uint32_t)((q / S) & 1)) || abort_flag) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        uint8_t* op = op0 + (size_t)st * op_stride;
+        const uint32_t ah = smem_u32(op), al = ah + kOpBytes;
+        const uint32_t bh = diag ? ah : al + kOpBytes, bl = diag ? al : bh + op_b_bytes;
+        const uint32_t d = tmem + (uint32_t)(b * N);
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          mma_tf32(d, sdesc(ah + 32 * k4), sdesc(bh + 32 * k4), idesc, (q % kSpan != 0 || k4 > 0) ? 1u : 0u);
+          mma_tf32(d, sdesc(ah + 32 * k4), sdesc(bl + 32 * k4), idesc, 1u);
+          mma_tf32(d, sdesc(al + 32 * k4), sdesc(bh + 32 * k4), idesc, 1u);
+        }
+        mma_commit(&op_empty[st]);
+        if (q % kSpan == kSpan - 1 || q == nloc - 1) mma_commit(&accf[b]);
+      }
+      if (!ok) abort_flag = 1;
+      mma_commit(&donebar);
+      mbar_wait(&donebar, 0);
+    }
+  } else {
+    // ---------------- transpose / split, then drain spans into double-float registers
+    const int ct = tid - 64;                 // 0..255
+    const int half = ct >> 7, r = ct & 127;  // half 0: X -> A, half 1: Y -> B
+    const int quarter = warp & 3, colhalf = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;     // C row within the tile (TMEM lane)
+    float hi[64], lo[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    bool ok = true;
+    for (int q = 0; ok && q < nloc; ++q) {
+      const int rs = q % R, os = q % S;
+      if (!mbar_wait(&raw_full[rs], (uint32_t)((q / R) & 1))) { ok = false; break; }
+      if (q >= S && !mbar_wait(&op_empty[os], (uint32_t)(((q / S) - 1) & 1))) { ok = false; break; }
+      if (abort_flag) { ok = false; break; }
+      const float* raw = (const float*)(raw0 + (size_t)rs * raw_stride);
+      uint8_t* op = op0 + (size_t)os * op_stride;
+      if (diag) {
+        // one operand serves as A and B: both halves convert X, each half of the K range
+        if (half == 0)
+          convert_tile<0, kRows / 8>(raw, p.bxw, r, op, op + kOpBytes);
+        else
+          convert_tile<kRows / 8, kRows / 4>(raw, p.bxw, r, op, op + kOpBytes);
+      } else if (half == 0) {
+        convert_tile<0, kRows / 4>(raw, p.bxw, r, op, op + kOpBytes);
+      } else if (r < N) {
+        convert_tile<0, kRows / 4>(raw + kRows * p.bxw, p.byw, r, op + 2 * kOpBytes, op + 2 * kOpBytes + op_b_bytes);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
-        const uint32_t acc0 = (h == 1 || (i % kFlushChunks) != 0) ? 1u : 0u;
-        const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&raw_empty[rs]);
+        mbar_arrive(&op_full[os]);
+      }
+      if (q % kSpan == kSpan - 1 && q / kSpan >= 1) ok = drain_span(q / kSpan - 1, tmem, N, quarter, colhalf, lane, accf, acce, hi, lo);
+    }
+    if (ok && nspans >= 2 && (nloc % kSpan) != 0)  // the span before a partial last one
+      ok = drain_span(nspans - 2, tmem, N, quarter, colhalf, lane, accf, acce, hi, lo);
+    if (ok && nspans >= 1) ok = drain_span(nspans - 1, tmem, N, quarter, colhalf, lane, accf, acce, hi, lo);
+    if (!ok) abort_flag = 1;
+    // write this CTA's partial tile (zeros for an empty row range)
+    const int col0 = n0 + colhalf * 64;
+    const int ci = m0 + row;
+    if (ci < p.a) {
+      double* out = p.partT + (int64_t)blockIdx.y * p.b * p.a;
 #pragma unroll
-        for (int kk = 2 * h; kk < 2 * h + 2; ++kk) {
-          mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), idesc, kk == 2 * h ? acc0 : 1u);
-          mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), idesc, 1u);
-          mma_tf32(tmem, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), idesc, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(&mma_bar[h])) : "memory");
-        if (h == 1 && i + stages < nloc) {
-          // raw stage s is fully converted: refill it with chunk i + stages
-          uint8_t* dst = sm + s * raw_stage;
-          const int y = (int)(r0 + (int64_t)(i + stages) * kRows);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&full[s])),
-                       "r"(tx_bytes) : "memory");
-          tma_load_2d(dst, &mapX, ta * 128, y, &full[s]);
-          tma_load_2d(dst + kRows * bx * 4, &mapY, 0, y, &full[s]);
-        }
+      for (int j = 0; j < 64; ++j) {
+        const int cj = col0 + j;
+        if (cj < p.b && cj < n0 + kTileG) out[(int64_t)cj * p.a + ci] = (double)hi[j] + (double)lo[j];
       }
     }
-    if (abort_flag) break;
-    if ((i + 1) % kFlushChunks == 0 || i + 1 == nloc) {
-      // drain the FP32 accumulator into the FP64 partial sums (all MMAs so far
-      // are complete once the last commit of this chunk has arrived)
-      if (!mbar_wait(&mma_bar[1], (uint32_t)(i & 1))) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int quarter = warp & 3, half = warp >> 2;
-      const int row = ta * 128 + quarter * 32 + lane;
-      for (int c0 = 32 * half; c0 < by; c0 += 64) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r);
-        if (row < a) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = c0 + j;
-            if (col < b) {
-              double* q = partT + (chunk * (int64_t)b + col) * a + row;
-              *q = (first_flush ? 0.0 : *q) + (double)__uint_as_float(r[j]);
-            }
-          }
-        }
-      }
-      first_flush = false;
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-    }
   }
-  if (nloc == 0) {
-    for (int row = ta * 128 + tid; row < a && row < ta * 128 + 128; row += 2 * kThreads)
-      for (int col = 0; col < b; ++col) partT[(chunk * (int64_t)b + col) * a + row] = 0.0;
-  }
-  if (abort_flag && tid == 0) atomicCAS(err, 0, DERR_TIMEOUT);
-  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols));
+  if (abort_flag && tid == 0) atomicCAS(p.err, 0, DERR_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols));
 }
 
-// ---- host: tensor maps through the driver entry point (no link-time libcuda dependency)
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// C[i][j] = sum over splits of the partial tiles; with sym, tiles below the
+// diagonal were not computed and are read mirrored.
+__global__ void k_gram_tc_reduce(const double* __restrict__ partT, int64_t splits, int a, int b, int sym, double* C,
+                                 int64_t ldc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a * b) return;
+  const int j = (int)(e / a), i = (int)(e % a);  // consecutive threads read consecutive rows of a partial
+  const bool mirror = sym && (i / kTileG) > (j / kTileG);
+  const int64_t off = mirror ? (int64_t)i * a + j : (int64_t)j * a + i;
+  double s = 0.0;
+  for (int64_t c = 0; c < splits; ++c) s += partT[c * (int64_t)a * b + off];
+  C[(int64_t)i * ldc + j] = s;
+}
+
+}  // namespace
+
+bool gram_tc_supported(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b) {
+  if (a < 1 || b < 1 || a > 256 || b > 256) return false;
+  if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || (ldx & 3) || (ldy & 3)) return false;
+  return encode_fn() != nullptr;
+}
+
+int gram_f32_tc(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+                int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s) {
+  if (n <= 0 || !gram_tc_supported(X, ldx, a, Y, ldy, b)) return -1;
+  GramArgs p;
+  p.a = a;
+  p.b = b;
+  p.sym = (X == Y && a == b && ldx == ldy) ? 1 : 0;
+  const int tma = (a + kTileG - 1) / kTileG, tnb = (b + kTileG - 1) / kTileG;
+  p.n_tiles_m = tma;
+  const int ntiles = p.sym ? tma * (tma + 1) / 2 : tma * tnb;
+  p.bxw = a >= kTileG ? kTileG : ((a + 3) / 4) * 4;
+  p.byw = b >= kTileG ? kTileG : ((b + 3) / 4) * 4;
+  p.N = b >= kTileG ? kTileG : ((b + 15) / 16) * 16;
+  const int raw_stride = ((kRows * (p.bxw + p.byw) * 4 + 1023) / 1024) * 1024;
+  const int op_stride = 2 * kOpBytes + 2 * p.N * 128;
+  p.op_stages = kMaxOp;
+  int R = (kSmemBudget - 1024 - kMaxOp * op_stride) / raw_stride;
+  if (R > kMaxRaw) R = kMaxRaw;
+  if (R < 2) return -1;
+  p.raw_stages = R;
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // one CTA per SM (shared memory): all tiles x splits in a single wave
+  int64_t splits = nsm / ntiles > 0 ? nsm / ntiles : 1;
+  const int64_t cap_splits = part_cap / ((int64_t)a * b);
+  if (splits > cap_splits) splits = cap_splits;
+  const int64_t max_chunks = (n + kRows - 1) / kRows;
+  if (splits > max_chunks) splits = max_chunks;
+  if (splits < 1) return -1;
+  int64_t rows = (n + splits - 1) / splits;
+  rows = ((rows + kRows - 1) / kRows) * kRows;
+  splits = (n + rows - 1) / rows;
+  p.n = n;
+  p.rows_per_split = rows;
+  p.partT = part;
+  p.err = err;
+  CUtensorMap mx, my;
+  if (!make_map_f32(&mx, X, n, a, ldx, p.bxw, kRows, false) || !make_map_f32(&my, Y, n, b, ldy, p.byw, kRows, false))
+    return -1;
+  const size_t smem = (size_t)R * raw_stride + (size_t)kMaxOp * op_stride + 1024;
+  if (!reserve_dynamic_smem(k_gram_tc, smem)) return -1;
+  dim3 grid((unsigned)ntiles, (unsigned)splits);
+  k_gram_tc<<<grid, kGramThreads, smem, s>>>(mx, my, p);
+  const int64_t tot = (int64_t)a * b;
+  k_gram_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, splits, a, b, p.sym, C, ldc);
+  return 0;
+}
+
+namespace tc {
 
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
@@ -267,54 +358,19 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const float* base, int64_t rows, int cols, int64_t ld, int box_cols) {
+bool make_map_f32(CUtensorMap* m, const float* base, int64_t rows, int cols, int64_t ld, int box_cols, int box_rows,
+                  bool swizzle128) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)kRows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-bool gram_tc_supported(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b) {
-  if (a < 1 || b < 1 || a > 256 || b > 256) return false;
-  if (((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || (ldx & 3) || (ldy & 3)) return false;
-  return encode_fn() != nullptr;
-}
-
-int gram_f32_tc(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
-                int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s) {
-  if (n <= 0) return -1;
-  const int by = ((b + 15) / 16) * 16;               // MMA N, multiple of 16
-  const int nta = (a + 127) / 128;
-  const int bx = nta > 1 ? 128 : ((a + 15) / 16) * 16;  // TMA box width of the X tile
-  const int operands = 2 * 128 * 128 + 2 * by * 128;
-  const int raw_stage = kRows * (bx + by) * 4;
-  int stages = (kSmemBudget - operands - 1024) / raw_stage;
-  if (stages > kMaxStages) stages = kMaxStages;
-  if (stages < 2) return -1;
-  CUtensorMap mx, my;
-  if (!make_map(&mx, X, n, a, ldx, bx) || !make_map(&my, Y, n, b, ldy, by)) return -1;
-  int64_t per_ta = (152 + nta - 1) / nta;
-  const int64_t cap_chunks = part_cap / ((int64_t)a * b);
-  if (per_ta > cap_chunks) per_ta = cap_chunks;
-  const int64_t max_chunks = (n + kRows - 1) / kRows;
-  if (per_ta > max_chunks) per_ta = max_chunks;
-  if (per_ta < 1) return -1;
-  int64_t rows = (n + per_ta - 1) / per_ta;
-  rows = ((rows + kRows - 1) / kRows) * kRows;
-  const int64_t chunks = (n + rows - 1) / rows;
-  const size_t smem = (size_t)((stages * raw_stage + 1023) / 1024) * 1024 + operands + 1024;
-  if (!reserve_dynamic_smem(k_gram_tc, smem)) return -1;
-  dim3 grid((unsigned)nta, (unsigned)chunks);
-  k_gram_tc<<<grid, 2 * kThreads, smem, s>>>(mx, my, a, b, bx, by, stages, n, rows, part, err);
-  gram_reduce_launch(part, chunks, a, b, C, ldc, s, true);
-  return 0;
-}
+}  // namespace tc
 
 }  // namespace grest

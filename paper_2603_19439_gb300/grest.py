@@ -70,7 +70,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
            "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
-           "grest_gram_f32", "grest_gram_noalloc", "grest_destroy", "grest_status_str"]
+           "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load_library(path=None):
     lib.grest_apply_operator.argtypes = [vp, vp, i64, vp, i64, i32]
     lib.grest_gram.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
     lib.grest_gram_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
+    lib.grest_gemm_f32.argtypes = [vp, i64, i32, i32, C.c_double, vp, i64, vp, i64, C.c_double, vp, i64, vp, i64]
     lib.grest_gram_noalloc.argtypes = [vp, i64, i32, vp, i64, i32, i64, vp, i64, vp]
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
@@ -242,6 +243,15 @@ class Tracker:
                                      Y.shape[1], X.shape[0], C.data_ptr(), C.stride(0))
         if st != 0:
             raise GrestError(st, "grest_gram_f32")
+
+    def gemm_f32(self, X, B, Out, alpha=1.0, beta=0.0, Cin=None):
+        """Out = beta Cin + alpha X B for torch CUDA float32 X, Cin, Out and
+        float64 B (row-major); Cin may be Out itself."""
+        cin, ldc = (Cin.data_ptr(), Cin.stride(0)) if Cin is not None else (None, 0)
+        st = self.lib.grest_gemm_f32(self.h, X.shape[0], X.shape[1], B.shape[1], alpha, X.data_ptr(), X.stride(0),
+                                     B.data_ptr(), B.stride(0), beta, cin, ldc, Out.data_ptr(), Out.stride(0))
+        if st != 0:
+            raise GrestError(st, "grest_gemm_f32")
 
     def sync(self):
         st = self.lib.grest_sync(self.h)
