@@ -193,6 +193,19 @@ int gemm_f32_tc(int64_t n, int a, int c, double alpha, const float* X, int64_t l
                 double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo, uint8_t* img, size_t img_cap,
                 int32_t* err, cudaStream_t s);
 
+// refine.cu: double-float (FP32 hi + lo) products of the mixed refinement.
+// spmm_df: (Yh + Yl) = M X for FP32 X (n x w, w <= 64), all rows.
+// gram_df: C (k x k) = X^T (Yh + Yl) (Yl may be null), k <= 64.
+// lift_df: Out (FP64) = X S, S k x k FP64 row-major (ld k).
+// sign_normalize_fast: FP64 X, columns flipped so that the entry of largest
+// magnitude (lowest row on ties) is positive.  Each returns its launch count.
+int spmm_df(const Csr& g, const OpParams& op, const int32_t* long_rows, const int64_t* n_long_dev, const float* X,
+            int64_t ldx, float* Yh, float* Yl, int64_t ldy, int w, int64_t n, cudaStream_t s);
+int gram_df(const float* X, int64_t ldx, const float* Yh, const float* Yl, int64_t ldy, int k, int64_t n, double* C,
+            int64_t ldc, double* part, int64_t part_cap, cudaStream_t s);
+int lift_df(const float* X, int64_t ldx, const double* S, int k, int64_t n, double* Out, int64_t ldo, cudaStream_t s);
+int sign_normalize_fast(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s);
+
 // eig.cu
 // Symmetric eigensolver for H (m x m row-major, ld; overwritten).  Writes the
 // k leading pairs in tracking order: theta[k], F (m x k row-major, ldf), all m

@@ -485,18 +485,25 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b) {
 // Mixed path, A11: FP64 Rayleigh-Ritz in span(U32).  With G = U^T U, the
 // pivoted Cholesky gives T with (U T)^T (U T) = I; the K x K problem
 // T^T (U^T M U) T F'' = F'' Theta is solved in FP64 and X = U (T F'').  The
-// products with U read its exact FP32 values and accumulate in FP64.
+// N x K products read U's exact FP32 values and are carried in double-float
+// (FP32 hi + lo, about 48 bits; refine.cu), which on this GPU runs on the
+// FP32 pipes at many times the FP64 rate; their K x K results are FP64.
 grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   cudaStream_t s = c->stream;
   const int K = c->K;
-  double* U64 = c->Un;  // exact FP64 copy of the FP32 Ritz vectors
-  convert_f32_to_f64(c->U32, c->ldu, U64, c->ldu, N2, K, s);
-  c->launches += 1;
-  gram(c, U64, c->ldu, K, U64, c->ldu, K, N2, c->G, K, true);
-  double* MU = c->U;  // the previous embedding is no longer needed
-  spmm(c, c->U32, c->ldu, MU, c->ldu, K, 0, N2, 0);
-  gram(c, U64, c->ldu, K, MU, c->ldu, K, N2, c->H, K, false);
+  float* MUh = reinterpret_cast<float*>(c->Un);  // Un (n_cap x ldu doubles) holds M U as hi / lo floats
+  float* MUl = MUh + (size_t)c->g.n_cap * c->ldu;
   int p = prof_begin(c);
+  c->launches += gram_df(c->U32, c->ldu, c->U32, nullptr, c->ldu, K, N2, c->G, K, c->part, c->part_cap, s);
+  prof_end(c, p, 1, 2.0 * N2 * K * K);
+  p = prof_begin(c);
+  c->launches += spmm_df(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, c->U32, c->ldu, MUh, MUl, c->ldu,
+                         K, N2, s);
+  prof_end(c, p, 0, 12.0 * N2 + (c->g.val ? 12.0 : 4.0) * c->nnz + K * (8.0 * N2 + 4.0 * N2));
+  p = prof_begin(c);
+  c->launches += gram_df(c->U32, c->ldu, MUh, MUl, c->ldu, K, N2, c->H, K, c->part, c->part_cap, s);
+  prof_end(c, p, 1, 2.0 * N2 * K * K);
+  p = prof_begin(c);
   c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, s);
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
   symmetrize(c->Uh, K, K, s);
@@ -505,9 +512,10 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48);
   k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
   c->launches += 1;
-  gemm(c, N2, K, K, 1.0, U64, c->ldu, c->Gs, K, 0.0, static_cast<const double*>(nullptr), 0, c->U, c->ldu);
-  sign_normalize(c->U, c->ldu, K, N2, c->part, c->ipart, s);
-  c->launches += 3;
+  p = prof_begin(c);
+  c->launches += lift_df(c->U32, c->ldu, c->Gs, K, N2, c->U, c->ldu, s);
+  c->launches += sign_normalize_fast(c->U, c->ldu, K, N2, c->part, c->ipart, s);
+  prof_end(c, p, 2, 2.0 * N2 * K * K);
   CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
   return GREST_OK;
 }
@@ -629,8 +637,7 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   // A10: X = Z F_K, sign normalization
   if constexpr (sizeof(T) == sizeof(double)) {
     gemm(c, N2, m, K, 1.0, Z, ldz, c->F, K, 0.0, static_cast<const T*>(nullptr), 0, c->Un, c->ldu);
-    sign_normalize(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
-    c->launches += 3;
+    c->launches += sign_normalize_fast(c->Un, c->ldu, K, N2, c->part, c->ipart, s);
     CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
     std::swap(c->U, c->Un);
     CK(cudaEventRecord(c->ev[7], s));
