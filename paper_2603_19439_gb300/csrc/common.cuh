@@ -155,9 +155,10 @@ void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t
 // Pivoted Cholesky with drop tolerance on G (c x c, row-major, ldg; overwritten).
 // Produces T (c x c row-major, ldt; columns >= rank zero) with V T orthonormal,
 // rank and pivot statistics in info[0..3] (rank, kept_min, dropped_max, status).
-// piv: device scratch of c ints.  Returns the number of kernels launched.
+// piv: device scratch of c ints.  f32: factor in FP32 arithmetic (storage
+// stays FP64).  Returns the number of kernels launched.
 int pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
-                  double* T, int64_t ldt, int* piv, double* info, cudaStream_t s);
+                  double* T, int64_t ldt, int* piv, double* info, bool f32, cudaStream_t s);
 void symmetrize(double* H, int64_t ld, int m, cudaStream_t s);
 void fill_f64(double* p, double v, int64_t n, cudaStream_t s);
 void copy_cols_f64(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t n, int w, cudaStream_t s);
@@ -209,10 +210,11 @@ int sign_normalize_fast(double* X, int64_t ldx, int w, int64_t n, double* part, 
 // eig.cu
 // Symmetric eigensolver for H (m x m row-major, ld; overwritten).  Writes the
 // k leading pairs in tracking order: theta[k], F (m x k row-major, ldf), all m
-// eigenvalues in tracking order to ritz[m], boundary gap to info[0].  Returns
-// the number of kernels launched.
+// eigenvalues in tracking order to ritz[m], boundary gap to info[0].  f32:
+// solve in FP32 arithmetic (storage stays FP64).  Returns the number of
+// kernels launched.
 int sym_eig_select(double* H, int64_t ld, int m, int k, int op_order, double* theta, double* F, int64_t ldf,
-                   double* ritz, double* info, double* work, cudaStream_t s);
+                   double* ritz, double* info, double* work, bool f32, cudaStream_t s);
 size_t eig_work_doubles(int mmax);
 
 // rsvd.cu

@@ -26,11 +26,13 @@ constexpr int kMaxM = 512;  // largest projected problem (K + 2 (L + P) <= 576 i
 
 struct EigWork {
   double *d, *e, *ds, *e2, *beta, *ev, *lam, *tnorm, *scr;
+  float *dsf, *e2f;  // FP32 copies of ds, e2 for the FP32 multisection
   int *ord, *sel;
 };
 
 // d, e, scaled d, scaled e^2, beta, ev: mmax each; ord: mmax ints; lam: kMaxK;
-// sel: kMaxK ints; tnorm[8]; then the inverse-iteration scratch (6 mmax kMaxK).
+// sel: kMaxK ints; tnorm[8]; FP32 copies of ds and e2 (mmax doubles); then the
+// inverse-iteration scratch (6 mmax kMaxK).
 __device__ __host__ inline EigWork eig_layout(double* w, int mmax) {
   EigWork L;
   L.d = w;
@@ -43,18 +45,21 @@ __device__ __host__ inline EigWork eig_layout(double* w, int mmax) {
   L.lam = w + 7 * mmax;
   L.sel = reinterpret_cast<int*>(w + 7 * mmax + kMaxK);
   L.tnorm = w + 7 * mmax + 2 * kMaxK;
-  L.scr = w + 7 * mmax + 2 * kMaxK + 8;
+  L.dsf = reinterpret_cast<float*>(w + 7 * mmax + 2 * kMaxK + 8);
+  L.e2f = L.dsf + mmax;
+  L.scr = w + 8 * mmax + 2 * kMaxK + 8;
   return L;
 }
 
-__device__ double block_sum(double v, double* red) {
+template <typename T>
+__device__ T block_sum(T v, T* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = 0;
   for (int i = 0; i < nw; ++i) s += red[i];  // fixed order
   return s;
 }
@@ -230,6 +235,32 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return cnt;
 }
 
+// The same count in FP32 (the projected problems of the mixed path): the
+// narrow FP32 exponent range calls for renormalizing p_t to [1, 2) at every
+// step (two FP32 multiplies by an exact power of two).
+__device__ __forceinline__ int sturm_count_f(const float* d, const float* e2, int m, float x, float floor_q) {
+  float pm2 = 0.f, pm1 = 1.f;
+  int cnt = 0;
+  bool neg_prev = false;
+  for (int t = 0; t < m; ++t) {
+    float pt = fmaf(-(t > 0 ? e2[t - 1] : 0.f), pm2, (d[t] - x) * pm1);
+    if ((__float_as_int(pt) & 0x7fffffff) == 0) pt = -floor_q * pm1;
+    const int bits = __float_as_int(pt);
+    const bool neg = bits < 0;
+    cnt += neg != neg_prev;
+    neg_prev = neg;
+    const int ex = (bits >> 23) & 0xff;
+    if (ex != 0) {
+      const float sc = __int_as_float(max(254 - ex, 1) << 23);  // 2^(127 - ex)
+      pt *= sc;
+      pm1 *= sc;
+    }
+    pm2 = pm1;
+    pm1 = pt;
+  }
+  return cnt;
+}
+
 // Gershgorin bounds of T and the exact power-of-two scaling used by the
 // multisection: ds = s d, e2 = (s e)^2, tnorm[1..4] = s gl, s gu, 1/s, s ||T||.
 __global__ void __launch_bounds__(256) k_sturm_prep(int m, double* work, int mmax) {
@@ -273,27 +304,35 @@ __global__ void __launch_bounds__(256) k_sturm_prep(int m, double* work, int mma
     L.ds[t] = L.d[t] * sc;
     const double es = L.e[t] * sc;
     L.e2[t] = es * es;
+    L.dsf[t] = (float)L.ds[t];
+    L.e2f[t] = (float)L.e2[t];
   }
 }
 
 // --- 2. eigenvalue number i (ascending) by 32-way multisection on the scaled
 // T; one warp per block so the warps land on separate SM sub-partitions.  The
-// bracket is refined to an absolute width of 4 eps ||T||.
+// bracket is refined to an absolute width of 4 eps ||T|| (eps of the
+// arithmetic type).
+template <typename T>
 __global__ void __launch_bounds__(32) k_multisect(int m, double* work, int mmax) {
   EigWork L = eig_layout(work, mmax);
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x;
   if (i >= m) return;
-  const double tnorm = L.tnorm[4];
-  const double floor_q = DBL_EPSILON * DBL_EPSILON * tnorm;
-  const double tol = 4.0 * DBL_EPSILON * tnorm;
-  double lo = L.tnorm[1] - tol, hi = L.tnorm[2] + tol;
+  constexpr bool F32 = sizeof(T) == 4;
+  const T eps = F32 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+  const T tnorm = (T)L.tnorm[4];
+  const T floor_q = F32 ? eps * T(1.0 / 1024.0) * tnorm : eps * eps * tnorm;
+  const T tol = T(4) * eps * tnorm;
+  T lo = (T)L.tnorm[1] - tol, hi = (T)L.tnorm[2] + tol;
   for (int it = 0; it < 40 && hi - lo > tol; ++it) {
-    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const int c = sturm_count(L.ds, L.e2, m, x, floor_q);
+    const T x = lo + (hi - lo) * (T)(lane + 1) / T(33);
+    int c;
+    if constexpr (F32) c = sturm_count_f(L.dsf, L.e2f, m, x, floor_q);
+    else c = sturm_count(L.ds, L.e2, m, x, floor_q);
     // first probe holding more than i eigenvalues below it
     const unsigned above = __ballot_sync(0xffffffffu, c > i);
-    double nlo = lo, nhi = hi;
+    T nlo = lo, nhi = hi;
     if (above) {
       const int f = __ffs(above) - 1;
       nhi = __shfl_sync(0xffffffffu, x, f);
@@ -304,7 +343,7 @@ __global__ void __launch_bounds__(32) k_multisect(int m, double* work, int mmax)
     lo = nlo;
     hi = nhi;
   }
-  if (lane == 0) L.ev[i] = 0.5 * (lo + hi) * L.tnorm[3];
+  if (lane == 0) L.ev[i] = 0.5 * ((double)lo + (double)hi) * L.tnorm[3];
 }
 
 // Order-preserving integer image of a double (-0 and +0 equal).
@@ -319,7 +358,7 @@ __device__ __forceinline__ long long ord_key(double x) {
 // boundary gap, and the selected values sorted ascending and pulled apart by
 // at least 10 eps ||T|| for the inverse iteration.
 __global__ void __launch_bounds__(256) k_select(int m, int k, int op, double* work, int mmax, double* theta,
-                                                double* ritz, double* info) {
+                                                double* ritz, double* info, double eps) {
   __shared__ long long k1[kMaxM], k2[kMaxM];
   __shared__ int sel_i[kMaxK];
   EigWork L = eig_layout(work, mmax);
@@ -360,7 +399,7 @@ __global__ void __launch_bounds__(256) k_select(int m, int k, int op, double* wo
     } else {
       info[0] = INFINITY;
     }
-    const double sep = 10.0 * DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    const double sep = 10.0 * eps * fmax(tnorm, DBL_MIN);
     double prev = -DBL_MAX;
     for (int a = 0; a < k; ++a) {
       const int t = sel_i[a];
@@ -389,60 +428,62 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
 // selected pair and one warp per block: the chains are serial, so the warps
 // are spread over the SM sub-partitions.  The reciprocal of each U pivot is
 // formed once in the LU and reused by the solves.
+template <typename T>
 __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mmax, double* F, int64_t ldf) {
   EigWork L = eig_layout(work, mmax);
   const int t = blockIdx.x * 32 + threadIdx.x;
   if (t >= k) return;
   // per-thread arrays interleaved across threads (coalesced): element i at [i * kMaxK]
   struct Strided {
-    double* b;
-    __device__ double& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
+    T* b;
+    __device__ T& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
   };
-  const Strided ur{L.scr + t}, c{L.scr + (int64_t)mmax * kMaxK + t}, c2{L.scr + (int64_t)2 * mmax * kMaxK + t},
-      l{L.scr + (int64_t)3 * mmax * kMaxK + t}, y{L.scr + (int64_t)4 * mmax * kMaxK + t},
-      flags{L.scr + (int64_t)5 * mmax * kMaxK + t};
-  const double lm = L.lam[t];
-  const double eps = DBL_EPSILON * fmax(L.tnorm[0], DBL_MIN);
+  T* scr = reinterpret_cast<T*>(L.scr);
+  const Strided ur{scr + t}, c{scr + (int64_t)mmax * kMaxK + t}, c2{scr + (int64_t)2 * mmax * kMaxK + t},
+      l{scr + (int64_t)3 * mmax * kMaxK + t}, y{scr + (int64_t)4 * mmax * kMaxK + t},
+      flags{scr + (int64_t)5 * mmax * kMaxK + t};
+  const T lm = (T)L.lam[t];
+  const T eps = (sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON) * (T)fmax(L.tnorm[0], DBL_MIN);
   // LU of T - lambda I with partial pivoting; ur[i] = 1 / U_ii
-  double ai = L.d[0] - lm;  // running diagonal entry of the active row
-  double ci = m > 1 ? L.e[0] : 0.0;
+  T ai = (T)L.d[0] - lm;  // running diagonal entry of the active row
+  T ci = m > 1 ? (T)L.e[0] : T(0);
   for (int i = 0; i + 1 < m; ++i) {
-    const double b = L.e[i];  // sub-diagonal entry below a_i
-    const double an = L.d[i + 1] - lm;
-    const double cn = i + 2 < m ? L.e[i + 1] : 0.0;
+    const T b = (T)L.e[i];  // sub-diagonal entry below a_i
+    const T an = (T)L.d[i + 1] - lm;
+    const T cn = i + 2 < m ? (T)L.e[i + 1] : T(0);
     if (fabs(ai) >= fabs(b)) {
-      if (ai == 0.0) ai = eps;
-      const double r = 1.0 / ai;
+      if (ai == T(0)) ai = eps;
+      const T r = T(1) / ai;
       ur[i] = r;
-      const double f = b * r;
+      const T f = b * r;
       l[i] = f;
       c[i] = ci;
-      c2[i] = 0.0;
-      flags[i] = 0.0;
+      c2[i] = 0;
+      flags[i] = 0;
       ai = an - f * ci;
       ci = cn;
     } else {
-      const double r = 1.0 / b;
+      const T r = T(1) / b;
       ur[i] = r;
-      const double f = ai * r;
+      const T f = ai * r;
       l[i] = f;
       c[i] = an;
       c2[i] = cn;
-      flags[i] = 1.0;
+      flags[i] = 1;
       ai = ci - f * an;
       ci = -f * cn;
     }
   }
-  if (ai == 0.0) ai = eps;
-  ur[m - 1] = 1.0 / ai;
-  c[m - 1] = 0.0;
-  c2[m - 1] = 0.0;
-  for (int i = 0; i < m; ++i) y[i] = hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7);
+  if (ai == T(0)) ai = eps;
+  ur[m - 1] = T(1) / ai;
+  c[m - 1] = 0;
+  c2[m - 1] = 0;
+  for (int i = 0; i < m; ++i) y[i] = (T)(hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7));
   for (int it = 0; it < 3; ++it) {
     // forward: apply L with row swaps
     for (int i = 0; i + 1 < m; ++i) {
-      if (flags[i] != 0.0) {
-        const double t1 = y[i];
+      if (flags[i] != T(0)) {
+        const T t1 = y[i];
         y[i] = y[i + 1];
         y[i + 1] = t1 - l[i] * y[i];
       } else {
@@ -450,30 +491,31 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
       }
     }
     // backward: U y = rhs
-    double y1 = y[m - 1] * ur[m - 1], y2 = 0.0;
+    T y1 = y[m - 1] * ur[m - 1], y2 = 0;
     y[m - 1] = y1;
     for (int i = m - 2; i >= 0; --i) {
-      const double yi = (y[i] - c[i] * y1 - c2[i] * y2) * ur[i];
+      const T yi = (y[i] - c[i] * y1 - c2[i] * y2) * ur[i];
       y[i] = yi;
       y2 = y1;
       y1 = yi;
     }
-    double nr = 0.0;
+    T nr = 0;
     for (int i = 0; i < m; ++i) nr = fma(y[i], y[i], nr);
-    nr = 1.0 / sqrt(nr);
+    nr = T(1) / sqrt(nr);
     for (int i = 0; i < m; ++i) y[i] *= nr;
   }
-  for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = y[i];
+  for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = (double)y[i];
 }
 
 // --- clusters of close selected values: block classical Gram-Schmidt, applied
 // twice, in ascending order; all projections of one vector run in parallel
 // (one warp per earlier cluster member), so a cluster of c vectors costs
 // O(c) block synchronizations instead of O(c^2).
+template <typename T>
 __global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work, int mmax, double* F,
                                                       int64_t ldf) {
-  __shared__ double dots[kMaxK];
-  __shared__ double red[32];
+  __shared__ T dots[kMaxK];
+  __shared__ T red[32];
   EigWork L = eig_layout(work, mmax);
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   const double ortol = 1e-3 * L.tnorm[0];
@@ -485,25 +527,25 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work
     for (int pass = 0; pass < 2; ++pass) {
       for (int b = b0 + wid; b < a; b += nw) {
         const int tb = L.sel[b];
-        double d = 0.0;
-        for (int i = lane; i < m; i += 32) d = fma(F[(int64_t)i * ldf + tb], F[(int64_t)i * ldf + ta], d);
+        T d = 0;
+        for (int i = lane; i < m; i += 32) d = fma((T)F[(int64_t)i * ldf + tb], (T)F[(int64_t)i * ldf + ta], d);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         if (lane == 0) dots[b - b0] = d;
       }
       __syncthreads();
       for (int i = tid; i < m; i += nth) {
-        double y = F[(int64_t)i * ldf + ta];
-        for (int b = b0; b < a; ++b) y = fma(-dots[b - b0], F[(int64_t)i * ldf + L.sel[b]], y);
-        F[(int64_t)i * ldf + ta] = y;
+        T y = (T)F[(int64_t)i * ldf + ta];
+        for (int b = b0; b < a; ++b) y = fma(-dots[b - b0], (T)F[(int64_t)i * ldf + L.sel[b]], y);
+        F[(int64_t)i * ldf + ta] = (double)y;
       }
       __syncthreads();
     }
-    double s2 = 0.0;
-    for (int i = tid; i < m; i += nth) s2 = fma(F[(int64_t)i * ldf + ta], F[(int64_t)i * ldf + ta], s2);
+    T s2 = 0;
+    for (int i = tid; i < m; i += nth) s2 = fma((T)F[(int64_t)i * ldf + ta], (T)F[(int64_t)i * ldf + ta], s2);
     s2 = block_sum(s2, red);
-    const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
-    for (int i = tid; i < m; i += nth) F[(int64_t)i * ldf + ta] *= inv;
+    const T inv = s2 > T(0) ? T(1) / sqrt(s2) : T(0);
+    for (int i = tid; i < m; i += nth) F[(int64_t)i * ldf + ta] = (double)((T)F[(int64_t)i * ldf + ta] * inv);
     __syncthreads();
   }
 }
@@ -512,43 +554,44 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work
 // warps per block (one per SM sub-partition).
 constexpr int kBtWarps = 4;
 
+template <typename T>
 __global__ void __launch_bounds__(kBtWarps * 32) k_backtransform(const double* H, int64_t ld, int m, int k,
                                                                 double* work, int mmax, double* F, int64_t ldf) {
-  extern __shared__ double xs[];  // kBtWarps x m
+  extern __shared__ __align__(16) unsigned char bt_raw[];  // kBtWarps x m
   EigWork L = eig_layout(work, mmax);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int t = blockIdx.x * kBtWarps + wid;
   if (t >= k) return;
-  double* x = xs + wid * m;
-  for (int i = lane; i < m; i += 32) x[i] = F[(int64_t)i * ldf + t];
+  T* x = reinterpret_cast<T*>(bt_raw) + wid * m;
+  for (int i = lane; i < m; i += 32) x[i] = (T)F[(int64_t)i * ldf + t];
   __syncwarp();
   for (int j = m - 3; j >= 0; --j) {
-    const double b = L.beta[j];
-    if (b == 0.0) continue;
+    const T b = (T)L.beta[j];
+    if (b == T(0)) continue;
     const double* v = H + (int64_t)j * ld + j + 1;
     const int n = m - j - 1;
-    double s = 0.0;
-    for (int i = lane; i < n; i += 32) s = fma(v[i], x[j + 1 + i], s);
+    T s = 0;
+    for (int i = lane; i < n; i += 32) s = fma((T)v[i], x[j + 1 + i], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     s *= b;
-    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * v[i];
+    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * (T)v[i];
     __syncwarp();
   }
-  for (int i = lane; i < m; i += 32) F[(int64_t)i * ldf + t] = x[i];
+  for (int i = lane; i < m; i += 32) F[(int64_t)i * ldf + t] = (double)x[i];
 }
 
 }  // namespace
 
-size_t eig_work_doubles(int mmax) { return (size_t)7 * mmax + 2 * kMaxK + 8 + (size_t)kMaxK * 6 * mmax + 64; }
+size_t eig_work_doubles(int mmax) { return (size_t)8 * mmax + 2 * kMaxK + 8 + (size_t)kMaxK * 6 * mmax + 64; }
 
-bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, cudaStream_t s);
+bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, bool f32, cudaStream_t s);
 
 int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
-                   double* info, double* work, cudaStream_t s) {
+                   double* info, double* work, bool f32, cudaStream_t s) {
   const int mmax = m;
   EigWork L = eig_layout(work, mmax);
-  if (!tridiag_cluster(H, ld, m, L.d, L.e, L.beta, s)) {
+  if (!tridiag_cluster(H, ld, m, L.d, L.e, L.beta, f32, s)) {
     const size_t smem = sizeof(double) * ((size_t)m * (m + 1) / 2 + 2 * (size_t)m + 2);
     if (reserve_dynamic_smem(k_tridiag_smem, smem)) {
       k_tridiag_smem<<<1, 1024, smem, s>>>(H, ld, m, work, mmax);
@@ -557,12 +600,21 @@ int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, d
     }
   }
   k_sturm_prep<<<1, 256, 0, s>>>(m, work, mmax);
-  k_multisect<<<m, 32, 0, s>>>(m, work, mmax);
-  k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info);
-  k_invit<<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
-  k_cluster_orth<<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
-  k_backtransform<<<(k + kBtWarps - 1) / kBtWarps, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(
-      H, ld, m, k, work, mmax, F, ldf);
+  const unsigned nbt = (unsigned)((k + kBtWarps - 1) / kBtWarps);
+  if (f32) {
+    k_multisect<float><<<m, 32, 0, s>>>(m, work, mmax);
+    k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, (double)FLT_EPSILON);
+    k_invit<float><<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+    k_cluster_orth<float><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
+    k_backtransform<float><<<nbt, kBtWarps * 32, sizeof(float) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F, ldf);
+  } else {
+    k_multisect<double><<<m, 32, 0, s>>>(m, work, mmax);
+    k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, DBL_EPSILON);
+    k_invit<double><<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+    k_cluster_orth<double><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
+    k_backtransform<double><<<nbt, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F,
+                                                                                       ldf);
+  }
   return 7;
 }
 

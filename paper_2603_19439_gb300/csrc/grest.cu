@@ -326,10 +326,12 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, 
   prof_end(c, p, 2, 2.0 * n * a * cc);
 }
 
+// f32: the projected problem's entries come from FP32 blocks (mixed path), so
+// it is solved in FP32 arithmetic; the refinement's K x K problem uses FP64
 void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf,
-         double* ritz, double* info) {
+         double* ritz, double* info, bool f32) {
   int p = prof_begin(c);
-  c->launches += sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, c->stream);
+  c->launches += sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, f32, c->stream);
   prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
@@ -365,7 +367,8 @@ grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n
                          int* rank_out) {
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
   int p = prof_begin(c);
-  c->launches += pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot, c->stream);
+  c->launches += pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot,
+                               sizeof(T) == sizeof(float), c->stream);
   prof_end(c, p, 3, (double)w * w * w / 3.0 + (double)w * w * w / 3.0);
   int rank = w;
   if (read_rank) {
@@ -504,12 +507,12 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   c->launches += gram_df(c->U32, c->ldu, MUh, MUl, c->ldu, K, N2, c->H, K, c->part, c->part_cap, s);
   prof_end(c, p, 1, 2.0 * N2 * K * K);
   p = prof_begin(c);
-  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, s);
+  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
   symmetrize(c->Uh, K, K, s);
   c->launches += 2;
   prof_end(c, p, 3, 4.0 * K * K * K);
-  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48);
+  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
   k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
   c->launches += 1;
   p = prof_begin(c);
@@ -598,7 +601,7 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
         // left singular vectors of B_s via eig(B_s B_s^T), L leading
         gram(c, EtM, ldq, rY, EtM, ldq, rY, S, c->Gs, rY, true);
         const int Lp = std::min(c->Lr, rY);
-        eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16);
+        eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16, sizeof(T) == sizeof(float));
         // S.4: R = M U_hat
         gemm(c, N2, rY, Lp, 1.0, Yr, ldq, c->Uh, Lp, 0.0, static_cast<const T*>(nullptr), 0, B, ldz);
         cb = Lp;
@@ -632,7 +635,7 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   c->launches += 1;
   CK(cudaEventRecord(c->ev[5], s));
   // A9: leading K eigenpairs of H (Alg. 1)
-  eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28);
+  eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, sizeof(T) == sizeof(float));
   CK(cudaEventRecord(c->ev[6], s));
   // A10: X = Z F_K, sign normalization
   if constexpr (sizeof(T) == sizeof(double)) {

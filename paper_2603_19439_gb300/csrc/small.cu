@@ -13,6 +13,12 @@
 // are computed redundantly and identically in every CTA from the same data
 // in the same order, so no broadcast step is needed.
 //
+// Storage (inputs, reflectors, R, T, d, e) is FP64 in every case; the
+// arithmetic type T is double for the FP64 path and float for the projected
+// problems of the mixed path, whose entries come from FP32 blocks and carry
+// FP32-level errors already (the FP64 Rayleigh-Ritz refinement that ends a
+// mixed step solves its K x K problem with T = double).
+//
 //   k_tridiag_cl : Householder reduction to tridiagonal form (Alg. 1, first
 //                  step of the eigensolve of H), two cluster barriers per
 //                  column.
@@ -37,14 +43,15 @@ constexpr int kClThreads = 256;
 // Fixed-order block sum (lane 0 of each warp, then warp 0); the result is
 // returned to every thread.  Identical inputs give identical results in every
 // CTA of the cluster.
-__device__ double cl_block_sum(double v, double* red, double* out) {
+template <typename T>
+__device__ T cl_block_sum(T v, T* red, T* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane == 0) red[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    double s = lane < nw ? red[lane] : 0.0;
+    T s = lane < nw ? red[lane] : T(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) *out = s;
@@ -58,82 +65,84 @@ __device__ double cl_block_sum(double v, double* red, double* out) {
 // Output: d[0..m), e[0..m) (e[m-1] = 0), beta[0..m-2); the reflector of
 // column j (v with v_0 = x_0 - alpha) is stored in row j of H right of the
 // diagonal, as the back-transformation expects.
+template <typename T>
 __global__ void __launch_bounds__(kClThreads) k_tridiag_cl(double* H, int64_t ld, int m, double* d_out,
                                                            double* e_out, double* beta_out) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   const int nl = (m + C - 1) / C;
-  extern __shared__ double sm[];
-  double* A = sm;                     // nl x m: local row li is global row r + C li
-  double* v = A + (size_t)nl * m;     // reflector (global column index)
-  double* w = v + m;                  // p, then w = p - K v
-  double* pl = w + m;                 // p_i of the owned rows
-  __shared__ double red[32];
-  __shared__ double bc[4];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* A = reinterpret_cast<T*>(sm_raw);  // nl x m: local row li is global row r + C li
+  T* v = A + (size_t)nl * m;           // reflector (global column index)
+  T* w = v + m;                        // p, then w = p - K v
+  T* pl = w + m;                       // p_i of the owned rows
+  __shared__ T red[32];
+  __shared__ T bc[4];
   for (int li = wid; li < nl; li += nw) {
     const int i = r + C * li;
     if (i >= m) break;
-    for (int l = lane; l < m; l += 32) A[(size_t)li * m + l] = i <= l ? H[(int64_t)i * ld + l] : H[(int64_t)l * ld + i];
+    for (int l = lane; l < m; l += 32)
+      A[(size_t)li * m + l] = (T)(i <= l ? H[(int64_t)i * ld + l] : H[(int64_t)l * ld + i]);
   }
   for (int j = 0; j + 2 < m; ++j) {
     cl.sync();  // row j final; every CTA done with the previous step's p
     const int o = j % C;
-    const double* Aj = cl.map_shared_rank(A, o) + (size_t)(j / C) * m;
-    double s = 0.0;
+    const T* Aj = cl.map_shared_rank(A, o) + (size_t)(j / C) * m;
+    T s = 0;
     for (int l = j + 1 + tid; l < m; l += nth) {
-      const double x = Aj[l];
+      const T x = Aj[l];
       v[l] = x;
       s = fma(x, x, s);
     }
-    const double nrm2 = cl_block_sum(s, red, bc);
+    const T nrm2 = cl_block_sum(s, red, bc);
     if (tid == 0) {
-      const double x0 = v[j + 1];
-      const double alpha = nrm2 > 0.0 ? -copysign(sqrt(nrm2), x0) : 0.0;
-      const double beta = nrm2 > 0.0 ? 1.0 / (nrm2 - alpha * x0) : 0.0;
+      const T x0 = v[j + 1];
+      const T alpha = nrm2 > T(0) ? -copysign(sqrt(nrm2), x0) : T(0);
+      const T beta = nrm2 > T(0) ? T(1) / (nrm2 - alpha * x0) : T(0);
       v[j + 1] = x0 - alpha;
       bc[1] = alpha;
       bc[2] = beta;
     }
     __syncthreads();
-    const double beta = bc[2];
+    const T beta = bc[2];
     if (r == o) {
-      for (int l = j + 1 + tid; l < m; l += nth) H[(int64_t)j * ld + l] = v[l];
+      for (int l = j + 1 + tid; l < m; l += nth) H[(int64_t)j * ld + l] = (double)v[l];
       if (tid == 0) {
-        d_out[j] = A[(size_t)(j / C) * m + j];
-        e_out[j] = bc[1];
-        beta_out[j] = beta;
+        d_out[j] = (double)A[(size_t)(j / C) * m + j];
+        e_out[j] = (double)bc[1];
+        beta_out[j] = (double)beta;
       }
     }
-    if (beta == 0.0) continue;  // same decision in every CTA
+    if (beta == T(0)) continue;  // same decision in every CTA
     // p_i = beta (B v)_i for the owned rows i > j, one warp per row
     const int f = j + 1 - r;
     const int li0 = f <= 0 ? 0 : (f + C - 1) / C;
     for (int li = li0 + wid; li < nl; li += nw) {
       if (r + C * li >= m) break;
-      const double* row = A + (size_t)li * m;
-      double a = 0.0;
+      const T* row = A + (size_t)li * m;
+      T a = 0;
       for (int l = j + 1 + lane; l < m; l += 32) a = fma(row[l], v[l], a);
 #pragma unroll
       for (int o2 = 16; o2 > 0; o2 >>= 1) a += __shfl_down_sync(0xffffffffu, a, o2);
       if (lane == 0) pl[li] = beta * a;
     }
     cl.sync();  // all p_i written
-    double t = 0.0;
+    T t = 0;
     for (int i = j + 1 + tid; i < m; i += nth) {
-      const double pi = cl.map_shared_rank(pl, i % C)[i / C];
+      const T pi = cl.map_shared_rank(pl, i % C)[i / C];
       w[i] = pi;
       t = fma(pi, v[i], t);
     }
-    const double K = 0.5 * beta * cl_block_sum(t, red, bc);
+    const T K = T(0.5) * beta * cl_block_sum(t, red, bc);
     for (int i = j + 1 + tid; i < m; i += nth) w[i] -= K * v[i];
     __syncthreads();
     // rank-2 update of the owned rows: B -= v w^T + w v^T
     for (int li = li0 + wid; li < nl; li += nw) {
       const int i = r + C * li;
       if (i >= m) break;
-      double* row = A + (size_t)li * m;
-      const double vi = v[i], wi = w[i];
+      T* row = A + (size_t)li * m;
+      const T vi = v[i], wi = w[i];
       for (int l = j + 1 + lane; l < m; l += 32) row[l] -= vi * w[l] + wi * v[l];
     }
   }
@@ -141,12 +150,12 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cl(double* H, int64_t ld
   if (tid == 0) {
     if (m >= 2) {
       if ((m - 2) % C == r) {
-        d_out[m - 2] = A[(size_t)((m - 2) / C) * m + m - 2];
-        e_out[m - 2] = A[(size_t)((m - 2) / C) * m + m - 1];
+        d_out[m - 2] = (double)A[(size_t)((m - 2) / C) * m + m - 2];
+        e_out[m - 2] = (double)A[(size_t)((m - 2) / C) * m + m - 1];
       }
-      if ((m - 1) % C == r) d_out[m - 1] = A[(size_t)((m - 1) / C) * m + m - 1];
+      if ((m - 1) % C == r) d_out[m - 1] = (double)A[(size_t)((m - 1) / C) * m + m - 1];
     } else if (r == 0) {
-      d_out[0] = A[0];
+      d_out[0] = (double)A[0];
     }
     if (r == 0) e_out[m - 1] = 0.0;
   }
@@ -165,6 +174,7 @@ __device__ __forceinline__ long long pivot_key(double x) { return x >= 0.0 ? __d
 // Output: Rt (in place of G): Rt[t][k] = R_{k,t} for k < t < rank and
 // Rt[k][k] = 1 / R_kk (pivot order); piv[0..c) (kept pivots first, then the
 // dropped indices ascending); info[0..3] = rank, kept_min, dropped_max, 0.
+template <typename T>
 __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, int c, double drop_tol,
                                                          double abs_ref, const double* abs_ref_ptr, int* piv_out,
                                                          double* info) {
@@ -172,26 +182,28 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
   const int C = (int)cl.num_blocks(), r = (int)cl.block_rank();
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   const int nl = (c + C - 1) / C;
-  extern __shared__ double sm[];
-  double* A = sm;                        // nl x c Schur rows (original index space)
-  double* Rk = A + (size_t)nl * c;       // current row of R (original index space)
-  double* rinv = Rk + c;                 // 1 / R_kk
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* A = reinterpret_cast<T*>(sm_raw);  // nl x c Schur rows (original index space)
+  T* Rk = A + (size_t)nl * c;          // current row of R (original index space)
+  T* rinv = Rk + c;                    // 1 / R_kk
   int* piv = reinterpret_cast<int*>(rinv + c);
-  int* done = piv + c;                   // pivoted already
+  int* done = piv + c;                 // pivoted already
   __shared__ long long slot_key[2];
   __shared__ int slot_idx[2];
-  __shared__ double s_ref, s_rinv, s_kept, s_dropped;
+  __shared__ double s_ref, s_thr, s_vlast, s_vdrop;
+  __shared__ T s_rinv;
   __shared__ int s_p, s_stop, s_rank;
   for (int li = wid; li < nl; li += nw) {
     const int i = r + C * li;
     if (i >= c) break;
-    for (int l = lane; l < c; l += 32) A[(size_t)li * c + l] = i <= l ? G[(int64_t)i * ld + l] : G[(int64_t)l * ld + i];
+    for (int l = lane; l < c; l += 32)
+      A[(size_t)li * c + l] = (T)(i <= l ? G[(int64_t)i * ld + l] : G[(int64_t)l * ld + i]);
   }
   for (int l = tid; l < c; l += nth) done[l] = 0;
   if (tid == 0) {
     s_rank = c;
-    s_kept = 0.0;
-    s_dropped = 0.0;
+    s_vlast = 0.0;
+    s_vdrop = 0.0;
   }
   __syncthreads();
   for (int k = 0; k < c; ++k) {
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
       for (int li = lane; li < nl; li += 32) {
         const int i = r + C * li;
         if (i < c && !done[i]) {
-          const long long key = pivot_key(A[(size_t)li * c + i]);
+          const long long key = pivot_key((double)A[(size_t)li * c + i]);
           if (key > bk || (key == bk && i < bi)) { bk = key; bi = i; }
         }
       }
@@ -232,24 +244,24 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
         if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
       }
       if (lane == 0) {
-        const double v = bk >= 0 ? __longlong_as_double(bk) : -1.0;
+        const double v = bk >= 0 ? __longlong_as_double(bk) : -1.0;  // exact value of the pivot
         if (k == 0) {
           const double a = abs_ref_ptr ? fabs(*abs_ref_ptr) : abs_ref;
           s_ref = fmax(v, a * a);
+          s_thr = drop_tol * drop_tol * s_ref;
         }
-        const double ref = s_ref;
-        if (bi >= c || !(v > 0.0) || !(v > drop_tol * drop_tol * ref) || !isfinite(v)) {
+        if (bi >= c || !(v > 0.0) || !(v > s_thr) || !isfinite(v)) {
           s_stop = 1;
           s_rank = k;
-          s_dropped = (ref > 0.0 && v > 0.0) ? sqrt(v / ref) : 0.0;
+          s_vdrop = v > 0.0 ? v : 0.0;
         } else {
           s_stop = 0;
-          const double rkk = sqrt(v);
-          s_rinv = 1.0 / rkk;
-          s_kept = ref > 0.0 ? rkk / sqrt(ref) : 0.0;
+          const T ri = T(1) / sqrt((T)v);
+          s_rinv = ri;
+          s_vlast = v;
           s_p = bi;
           piv[k] = bi;
-          rinv[k] = s_rinv;
+          rinv[k] = ri;
           done[bi] = 1;
         }
       }
@@ -257,17 +269,17 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
     __syncthreads();
     if (s_stop) break;  // same decision in every CTA
     const int p = s_p;
-    const double ri = s_rinv;
-    const double* Ap = cl.map_shared_rank(A, p % C) + (size_t)(p / C) * c;
-    for (int l = tid; l < c; l += nth) Rk[l] = done[l] ? 0.0 : Ap[l] * ri;
+    const T ri = s_rinv;
+    const T* Ap = cl.map_shared_rank(A, p % C) + (size_t)(p / C) * c;
+    for (int l = tid; l < c; l += nth) Rk[l] = done[l] ? T(0) : Ap[l] * ri;
     __syncthreads();
     // Schur update of the owned rows that are not pivoted yet
     for (int li = wid; li < nl; li += nw) {
       const int i = r + C * li;
       if (i >= c) break;
       if (done[i]) continue;
-      const double rki = Rk[i];
-      double* row = A + (size_t)li * c;
+      const T rki = Rk[i];
+      T* row = A + (size_t)li * c;
       for (int l = lane; l < c; l += 32) row[l] = fma(-rki, Rk[l], row[l]);
     }
     __syncthreads();
@@ -285,15 +297,17 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
   for (int k = 0; k < rk; ++k) {
     const int p = piv[k];
     if (p % C != r) continue;
-    const double* Sk = A + (size_t)(p / C) * c;
-    for (int t = k + tid; t < rk; t += nth) G[(int64_t)t * ld + k] = t == k ? rinv[k] : Sk[piv[t]] * rinv[k];
+    const T* Sk = A + (size_t)(p / C) * c;
+    for (int t = k + tid; t < rk; t += nth)
+      G[(int64_t)t * ld + k] = (double)(t == k ? rinv[k] : Sk[piv[t]] * rinv[k]);
   }
   if (r == 0) {
     for (int l = tid; l < c; l += nth) piv_out[l] = piv[l];
     if (tid == 0) {
+      const double ref = s_ref;
       info[0] = rk;
-      info[1] = rk > 0 ? s_kept : 0.0;
-      info[2] = s_dropped;
+      info[1] = (rk > 0 && ref > 0.0) ? sqrt(s_vlast / ref) : 0.0;  // last kept pivot / reference
+      info[2] = (ref > 0.0 && s_vdrop > 0.0) ? sqrt(s_vdrop / ref) : 0.0;
       info[3] = 0.0;
     }
   }
@@ -305,32 +319,33 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
 // Rt holds R transposed with reciprocal diagonal (k_pchol_cl).
 constexpr int kTrinvWarps = 4;
 
+template <typename T>
 __global__ void __launch_bounds__(kTrinvWarps * 32) k_trinv(const double* Rt, int64_t ld, const int* piv,
-                                                            const double* info, int c, double* T, int64_t ldt) {
-  extern __shared__ double xs[];  // kTrinvWarps x c
+                                                            const double* info, int c, double* Tm, int64_t ldt) {
+  extern __shared__ __align__(16) unsigned char xs_raw[];  // kTrinvWarps x c
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int j = blockIdx.x * kTrinvWarps + wid;
   if (j >= c) return;
   const int rk = (int)info[0];
   if (j >= rk) {
-    for (int i = lane; i < c; i += 32) T[(int64_t)i * ldt + j] = 0.0;
+    for (int i = lane; i < c; i += 32) Tm[(int64_t)i * ldt + j] = 0.0;
     return;
   }
-  double* s = xs + (size_t)wid * c;
-  for (int i = lane; i < j; i += 32) s[i] = 0.0;
-  double xt = Rt[(int64_t)j * ld + j];
+  T* s = reinterpret_cast<T*>(xs_raw) + (size_t)wid * c;
+  for (int i = lane; i < j; i += 32) s[i] = 0;
+  T xt = (T)Rt[(int64_t)j * ld + j];
   if (lane == 0) s[j] = xt;
   __syncwarp();
   for (int t = j; t >= 1; --t) {
     const double* col = Rt + (int64_t)t * ld;  // col[i] = R_{i,t}, i < t
-    for (int i = lane; i < t; i += 32) s[i] = fma(col[i], xt, s[i]);
+    for (int i = lane; i < t; i += 32) s[i] = fma((T)col[i], xt, s[i]);
     __syncwarp();
-    xt = -s[t - 1] * Rt[(int64_t)(t - 1) * ld + (t - 1)];
+    xt = -s[t - 1] * (T)Rt[(int64_t)(t - 1) * ld + (t - 1)];
     __syncwarp();
     if (lane == 0) s[t - 1] = xt;
     __syncwarp();
   }
-  for (int i = lane; i < c; i += 32) T[(int64_t)piv[i] * ldt + j] = i <= j ? s[i] : 0.0;
+  for (int i = lane; i < c; i += 32) Tm[(int64_t)piv[i] * ldt + j] = i <= j ? (double)s[i] : 0.0;
 }
 
 // True when `kern` can be launched as one cluster of C CTAs with `smem` bytes
@@ -397,34 +412,46 @@ bool launch_cl(K kern, int C, size_t smem, cudaStream_t s, Args... args) {
 
 int want_cluster(int m) { return m >= 96 ? 16 : 8; }
 
-}  // namespace
-
-bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, cudaStream_t s) {
-  if (m < 1) return true;
+template <typename T>
+bool tridiag_cluster_t(double* H, int64_t ld, int m, double* d, double* e, double* beta, cudaStream_t s) {
   for (int C = want_cluster(m); C >= 2; C >>= 1) {
     const int nl = (m + C - 1) / C;
-    const size_t smem = sizeof(double) * ((size_t)nl * m + 2 * (size_t)m + nl);
-    if (!cluster_ok(k_tridiag_cl, smem, C)) continue;
-    if (launch_cl(k_tridiag_cl, C, smem, s, H, ld, m, d, e, beta)) return true;
+    const size_t smem = sizeof(T) * ((size_t)nl * m + 2 * (size_t)m + nl);
+    if (!cluster_ok(k_tridiag_cl<T>, smem, C)) continue;
+    if (launch_cl(k_tridiag_cl<T>, C, smem, s, H, ld, m, d, e, beta)) return true;
   }
   return false;
 }
 
-bool pchol_cluster(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
-                   double* T, int64_t ldt, int* piv, double* info, cudaStream_t s) {
-  if (c < 1) return false;
-  const size_t tsmem = sizeof(double) * kTrinvWarps * (size_t)c;
-  if (!reserve_dynamic_smem(k_trinv, tsmem)) return false;
+template <typename T>
+bool pchol_cluster_t(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                     double* Tm, int64_t ldt, int* piv, double* info, cudaStream_t s) {
+  const size_t tsmem = sizeof(T) * kTrinvWarps * (size_t)c;
+  if (!reserve_dynamic_smem(k_trinv<T>, tsmem)) return false;
   for (int C = want_cluster(c); C >= 2; C >>= 1) {
     const int nl = (c + C - 1) / C;
-    const size_t smem = sizeof(double) * ((size_t)nl * c + 2 * (size_t)c) + sizeof(int) * 2 * (size_t)c;
-    if (!cluster_ok(k_pchol_cl, smem, C)) continue;
-    if (!launch_cl(k_pchol_cl, C, smem, s, G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, piv, info)) continue;
-    k_trinv<<<(unsigned)((c + kTrinvWarps - 1) / kTrinvWarps), kTrinvWarps * 32, tsmem, s>>>(G, ldg, piv, info, c,
-                                                                                               T, ldt);
+    const size_t smem = sizeof(T) * ((size_t)nl * c + 2 * (size_t)c) + sizeof(int) * 2 * (size_t)c;
+    if (!cluster_ok(k_pchol_cl<T>, smem, C)) continue;
+    if (!launch_cl(k_pchol_cl<T>, C, smem, s, G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, piv, info)) continue;
+    k_trinv<T><<<(unsigned)((c + kTrinvWarps - 1) / kTrinvWarps), kTrinvWarps * 32, tsmem, s>>>(G, ldg, piv, info,
+                                                                                                  c, Tm, ldt);
     return true;
   }
   return false;
+}
+
+}  // namespace
+
+bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, bool f32, cudaStream_t s) {
+  if (m < 1) return true;
+  return f32 ? tridiag_cluster_t<float>(H, ld, m, d, e, beta, s) : tridiag_cluster_t<double>(H, ld, m, d, e, beta, s);
+}
+
+bool pchol_cluster(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                   double* Tm, int64_t ldt, int* piv, double* info, bool f32, cudaStream_t s) {
+  if (c < 1) return false;
+  return f32 ? pchol_cluster_t<float>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, Tm, ldt, piv, info, s)
+             : pchol_cluster_t<double>(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, Tm, ldt, piv, info, s);
 }
 
 }  // namespace grest
