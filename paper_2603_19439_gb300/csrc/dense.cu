@@ -745,8 +745,14 @@ void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t
 bool pchol_cluster(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
                    double* T, int64_t ldt, int* piv, double* info, bool f32, cudaStream_t s);
 
+bool pchol_f32_1cta(const double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
+                    double* Tm, int64_t ldt, int* piv, double* info, cudaStream_t s);
+
 int pchol_inverse(double* G, int64_t ldg, int c, double drop_tol, double abs_ref, const double* abs_ref_ptr,
                   double* T, int64_t ldt, int* piv, double* info, bool f32, cudaStream_t s) {
+  // one SM for small problems (barrier latency dominates), a cluster for large
+  // ones (the Schur updates are bound by shared-memory bandwidth on one SM)
+  if (f32 && c <= 64 && pchol_f32_1cta(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, piv, info, s)) return 1;
   if (pchol_cluster(G, ldg, c, drop_tol, abs_ref, abs_ref_ptr, T, ldt, piv, info, f32, s)) return 2;
   const size_t smem = sizeof(double) * ((size_t)c * (c + 1) / 2) + sizeof(int) * (c + 1) + 16;
   if (reserve_dynamic_smem(k_pchol_smem, smem)) {

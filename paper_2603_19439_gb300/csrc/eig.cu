@@ -26,13 +26,16 @@ constexpr int kMaxM = 512;  // largest projected problem (K + 2 (L + P) <= 576 i
 
 struct EigWork {
   double *d, *e, *ds, *e2, *beta, *ev, *lam, *tnorm, *scr;
-  float *dsf, *e2f;  // FP32 copies of ds, e2 for the FP32 multisection
-  int *ord, *sel;
+  float *dsf, *e2f;          // FP32 copies of ds, e2 for the FP32 multisection
+  float *df, *ef, *betaf;    // FP32 copies of d, e, beta
+  float* vf;                 // FP32 reflectors (row j, ld m) of the FP32 path
+  int *ord, *sel, *cl0;      // cl0[a]: first member of the cluster of sorted selected value a
 };
 
 // d, e, scaled d, scaled e^2, beta, ev: mmax each; ord: mmax ints; lam: kMaxK;
-// sel: kMaxK ints; tnorm[8]; FP32 copies of ds and e2 (mmax doubles); then the
-// inverse-iteration scratch (6 mmax kMaxK).
+// sel: kMaxK ints; tnorm[8]; FP32 copies of ds, e2, d, e, beta; cl0 (kMaxK
+// ints); FP32 reflectors (mmax x mmax floats); then the inverse-iteration
+// scratch (6 mmax kMaxK).
 __device__ __host__ inline EigWork eig_layout(double* w, int mmax) {
   EigWork L;
   L.d = w;
@@ -45,9 +48,15 @@ __device__ __host__ inline EigWork eig_layout(double* w, int mmax) {
   L.lam = w + 7 * mmax;
   L.sel = reinterpret_cast<int*>(w + 7 * mmax + kMaxK);
   L.tnorm = w + 7 * mmax + 2 * kMaxK;
-  L.dsf = reinterpret_cast<float*>(w + 7 * mmax + 2 * kMaxK + 8);
+  double* f0 = w + 7 * mmax + 2 * kMaxK + 8;  // FP32 region: 5 mmax floats (3 mmax doubles)
+  L.dsf = reinterpret_cast<float*>(f0);
   L.e2f = L.dsf + mmax;
-  L.scr = w + 8 * mmax + 2 * kMaxK + 8;
+  L.df = L.e2f + mmax;
+  L.ef = L.df + mmax;
+  L.betaf = L.ef + mmax;
+  L.cl0 = reinterpret_cast<int*>(f0 + 3 * mmax);  // kMaxK ints
+  L.vf = reinterpret_cast<float*>(f0 + 3 * mmax + kMaxK / 2);
+  L.scr = f0 + 3 * mmax + kMaxK / 2 + ((size_t)mmax * mmax + 1) / 2;
   return L;
 }
 
@@ -306,6 +315,9 @@ __global__ void __launch_bounds__(256) k_sturm_prep(int m, double* work, int mma
     L.e2[t] = es * es;
     L.dsf[t] = (float)L.ds[t];
     L.e2f[t] = (float)L.e2[t];
+    L.df[t] = (float)L.d[t];
+    L.ef[t] = (float)L.e[t];
+    L.betaf[t] = (float)L.beta[t];
   }
 }
 
@@ -401,12 +413,16 @@ __global__ void __launch_bounds__(256) k_select(int m, int k, int op, double* wo
     }
     const double sep = 10.0 * eps * fmax(tnorm, DBL_MIN);
     double prev = -DBL_MAX;
+    const double ortol = 1e-3 * tnorm;
+    int c0 = 0;
     for (int a = 0; a < k; ++a) {
       const int t = sel_i[a];
       double v = L.ev[L.ord[t]];
       if (a > 0 && v < prev + sep) v = prev + sep;
+      if (a > 0 && !(v - prev < ortol)) c0 = a;  // a starts a new cluster
       L.lam[t] = v;
       L.sel[a] = t;
+      L.cl0[a] = c0;
       prev = v;
     }
     L.tnorm[0] = tnorm;
@@ -428,29 +444,43 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
 // selected pair and one warp per block: the chains are serial, so the warps
 // are spread over the SM sub-partitions.  The reciprocal of each U pivot is
 // formed once in the LU and reused by the solves.
-template <typename T>
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mmax, double* F, int64_t ldf) {
   EigWork L = eig_layout(work, mmax);
+  extern __shared__ __align__(16) unsigned char iv_raw[];
   const int t = blockIdx.x * 32 + threadIdx.x;
   if (t >= k) return;
-  // per-thread arrays interleaved across threads (coalesced): element i at [i * kMaxK]
+  // per-thread arrays interleaved across threads (coalesced / conflict-free):
+  // element i at [i * stride], in shared memory (stride 32) or global scratch
   struct Strided {
     T* b;
-    __device__ T& operator[](int i) const { return b[(int64_t)i * kMaxK]; }
+    int64_t st;
+    __device__ T& operator[](int i) const { return b[(int64_t)i * st]; }
   };
-  T* scr = reinterpret_cast<T*>(L.scr);
-  const Strided ur{scr + t}, c{scr + (int64_t)mmax * kMaxK + t}, c2{scr + (int64_t)2 * mmax * kMaxK + t},
-      l{scr + (int64_t)3 * mmax * kMaxK + t}, y{scr + (int64_t)4 * mmax * kMaxK + t},
-      flags{scr + (int64_t)5 * mmax * kMaxK + t};
+  T* scr;
+  int64_t st;
+  if (SMEM) {
+    scr = reinterpret_cast<T*>(iv_raw) + threadIdx.x;
+    st = 32;
+  } else {
+    scr = reinterpret_cast<T*>(L.scr) + t;
+    st = kMaxK;
+  }
+  const int64_t pl = (int64_t)mmax * st;
+  const Strided ur{scr, st}, c{scr + pl, st}, c2{scr + 2 * pl, st}, l{scr + 3 * pl, st}, y{scr + 4 * pl, st},
+      flags{scr + 5 * pl, st};
+  constexpr bool F32 = sizeof(T) == 4;
+  auto dd = [&](int i) -> T { return F32 ? (T)L.df[i] : (T)L.d[i]; };
+  auto ee = [&](int i) -> T { return F32 ? (T)L.ef[i] : (T)L.e[i]; };
   const T lm = (T)L.lam[t];
-  const T eps = (sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON) * (T)fmax(L.tnorm[0], DBL_MIN);
+  const T eps = (F32 ? (T)FLT_EPSILON : (T)DBL_EPSILON) * (T)fmax(L.tnorm[0], DBL_MIN);
   // LU of T - lambda I with partial pivoting; ur[i] = 1 / U_ii
-  T ai = (T)L.d[0] - lm;  // running diagonal entry of the active row
-  T ci = m > 1 ? (T)L.e[0] : T(0);
+  T ai = dd(0) - lm;  // running diagonal entry of the active row
+  T ci = m > 1 ? ee(0) : T(0);
   for (int i = 0; i + 1 < m; ++i) {
-    const T b = (T)L.e[i];  // sub-diagonal entry below a_i
-    const T an = (T)L.d[i + 1] - lm;
-    const T cn = i + 2 < m ? (T)L.e[i + 1] : T(0);
+    const T b = ee(i);  // sub-diagonal entry below a_i
+    const T an = dd(i + 1) - lm;
+    const T cn = i + 2 < m ? ee(i + 1) : T(0);
     if (fabs(ai) >= fabs(b)) {
       if (ai == T(0)) ai = eps;
       const T r = T(1) / ai;
@@ -518,11 +548,9 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work
   __shared__ T red[32];
   EigWork L = eig_layout(work, mmax);
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
-  const double ortol = 1e-3 * L.tnorm[0];
   for (int a = 1; a < k; ++a) {
     const int ta = L.sel[a];
-    int b0 = a;
-    while (b0 > 0 && L.lam[L.sel[b0]] - L.lam[L.sel[b0 - 1]] < ortol) --b0;
+    const int b0 = L.cl0[a];
     if (b0 == a) continue;
     for (int pass = 0; pass < 2; ++pass) {
       for (int b = b0 + wid; b < a; b += nw) {
@@ -565,57 +593,92 @@ __global__ void __launch_bounds__(kBtWarps * 32) k_backtransform(const double* H
   T* x = reinterpret_cast<T*>(bt_raw) + wid * m;
   for (int i = lane; i < m; i += 32) x[i] = (T)F[(int64_t)i * ldf + t];
   __syncwarp();
+  constexpr bool F32 = sizeof(T) == 4;
   for (int j = m - 3; j >= 0; --j) {
-    const T b = (T)L.beta[j];
+    const T b = F32 ? (T)L.betaf[j] : (T)L.beta[j];
     if (b == T(0)) continue;
     const double* v = H + (int64_t)j * ld + j + 1;
+    const float* vfj = L.vf + (size_t)j * m + j + 1;
     const int n = m - j - 1;
     T s = 0;
-    for (int i = lane; i < n; i += 32) s = fma((T)v[i], x[j + 1 + i], s);
+    for (int i = lane; i < n; i += 32) s = fma(F32 ? (T)vfj[i] : (T)v[i], x[j + 1 + i], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     s *= b;
-    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * (T)v[i];
+    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * (F32 ? (T)vfj[i] : (T)v[i]);
     __syncwarp();
   }
   for (int i = lane; i < m; i += 32) F[(int64_t)i * ldf + t] = (double)x[i];
 }
 
+// FP32 copies of reflectors stored in H's rows (cluster / fallback reductions)
+__global__ void k_reflectors_f32(const double* H, int64_t ld, int m, double* work, int mmax) {
+  EigWork L = eig_layout(work, mmax);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m), l = (int)(e % m);
+    if (l > j) L.vf[e] = (float)H[(int64_t)j * ld + l];
+  }
+}
+
 }  // namespace
 
-size_t eig_work_doubles(int mmax) { return (size_t)8 * mmax + 2 * kMaxK + 8 + (size_t)kMaxK * 6 * mmax + 64; }
+size_t eig_work_doubles(int mmax) {
+  return (size_t)10 * mmax + 2 * kMaxK + 8 + kMaxK / 2 + ((size_t)mmax * mmax + 1) / 2 + (size_t)kMaxK * 6 * mmax + 64;
+}
 
 bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, bool f32, cudaStream_t s);
+bool tridiag_f32_1cta(const double* H, int64_t ld, int m, double* d, double* e, double* beta, float* df, float* ef,
+                      float* betaf, float* vf, cudaStream_t s);
 
 int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
                    double* info, double* work, bool f32, cudaStream_t s) {
   const int mmax = m;
   EigWork L = eig_layout(work, mmax);
-  if (!tridiag_cluster(H, ld, m, L.d, L.e, L.beta, f32, s)) {
+  int launches = 6;
+  // one SM for small problems, a cluster for large ones (as for the pivoted Cholesky)
+  if (f32 && m <= 64 && tridiag_f32_1cta(H, ld, m, L.d, L.e, L.beta, L.df, L.ef, L.betaf, L.vf, s)) {
+    launches += 1;
+  } else if (tridiag_cluster(H, ld, m, L.d, L.e, L.beta, f32, s)) {
+    launches += 1;
+    if (f32) {
+      k_reflectors_f32<<<64, 256, 0, s>>>(H, ld, m, work, mmax);
+      launches += 1;
+    }
+  } else {
     const size_t smem = sizeof(double) * ((size_t)m * (m + 1) / 2 + 2 * (size_t)m + 2);
     if (reserve_dynamic_smem(k_tridiag_smem, smem)) {
       k_tridiag_smem<<<1, 1024, smem, s>>>(H, ld, m, work, mmax);
     } else {
       k_tridiag<<<1, 1024, sizeof(double) * 2 * (m + 1), s>>>(H, ld, m, work, mmax);
     }
+    launches += 1;
+    if (f32) {
+      k_reflectors_f32<<<64, 256, 0, s>>>(H, ld, m, work, mmax);
+      launches += 1;
+    }
   }
   k_sturm_prep<<<1, 256, 0, s>>>(m, work, mmax);
   const unsigned nbt = (unsigned)((k + kBtWarps - 1) / kBtWarps);
+  const unsigned niv = (unsigned)((k + 31) / 32);
   if (f32) {
     k_multisect<float><<<m, 32, 0, s>>>(m, work, mmax);
     k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, (double)FLT_EPSILON);
-    k_invit<float><<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+    const size_t ism = sizeof(float) * 6 * 32 * (size_t)mmax;
+    if (reserve_dynamic_smem(k_invit<float, true>, ism))
+      k_invit<float, true><<<niv, 32, ism, s>>>(m, k, work, mmax, F, ldf);
+    else
+      k_invit<float, false><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
     k_cluster_orth<float><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
     k_backtransform<float><<<nbt, kBtWarps * 32, sizeof(float) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F, ldf);
   } else {
     k_multisect<double><<<m, 32, 0, s>>>(m, work, mmax);
     k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, DBL_EPSILON);
-    k_invit<double><<<(k + 31) / 32, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+    k_invit<double, false><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
     k_cluster_orth<double><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
     k_backtransform<double><<<nbt, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F,
                                                                                        ldf);
   }
-  return 7;
+  return launches;
 }
 
 }  // namespace grest

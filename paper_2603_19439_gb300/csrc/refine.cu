@@ -201,48 +201,64 @@ __global__ void __launch_bounds__(256) k_spmm_df_long(const int64_t* __restrict_
 // Yl may be null; 32-row tiles of X and Y staged in shared memory.
 constexpr int kDfRows = 32;
 
+// Thread t owns C entries (i, j) with i = t / 8 + 32 u and j = 4 (t mod 8) +
+// 32 v + 0..3 (u, v < k / 32 rounded up): per staged row, one x_i and a float4
+// of y_h (and y_l) serve four products.
+template <int NU>
 __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ X, int64_t ldx, const float* __restrict__ Yh,
                                                  const float* __restrict__ Yl, int64_t ldy, int k, int64_t n,
                                                  int64_t rows_per_block, double* __restrict__ part) {
-  __shared__ float xs[kDfRows][64], yhs[kDfRows][64], yls[kDfRows][64];
+  __shared__ __align__(16) float xs[kDfRows][64], yhs[kDfRows][64], yls[kDfRows][64];
   const int tid = threadIdx.x;
-  const int nent = k * k;
-  const int per = (nent + 255) / 256;  // <= 16
-  float hi[16], lo[16];
+  const int ti = tid >> 3, tj = (tid & 7) * 4;
+  float hi[NU][NU][4], lo[NU][NU][4];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+  for (int u = 0; u < NU; ++u)
+#pragma unroll
+    for (int v = 0; v < NU; ++v)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { hi[u][v][q] = 0.f; lo[u][v][q] = 0.f; }
   const int64_t rb = blockIdx.x * rows_per_block;
   int64_t re = rb + rows_per_block;
   if (re > n) re = n;
   for (int64_t r0 = rb; r0 < re; r0 += kDfRows) {
     const int rows = (int)((re - r0) < kDfRows ? (re - r0) : kDfRows);
     __syncthreads();
-    for (int e = tid; e < kDfRows * k; e += 256) {
-      const int rr = e / k, c = e % k;
-      const bool in = rr < rows;
+    for (int e = tid; e < kDfRows * 64; e += 256) {
+      const int rr = e >> 6, c = e & 63;
+      const bool in = rr < rows && c < k;
       const int64_t r = r0 + rr;
       xs[rr][c] = in ? X[r * ldx + c] : 0.f;
       yhs[rr][c] = in ? Yh[r * ldy + c] : 0.f;
       yls[rr][c] = (in && Yl) ? Yl[r * ldy + c] : 0.f;
     }
     __syncthreads();
+    for (int rr = 0; rr < rows; ++rr) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      if (q < per) {
-        const int e = tid + 256 * q;
-        if (e < nent) {
-          const int i = e / k, j = e % k;
-          for (int rr = 0; rr < rows; ++rr) df_madd2(hi[q], lo[q], xs[rr][i], yhs[rr][j], yls[rr][j]);
+      for (int u = 0; u < NU; ++u) {
+        const float xv = xs[rr][ti + 32 * u];
+#pragma unroll
+        for (int v = 0; v < NU; ++v) {
+          const float4 yh = *(const float4*)&yhs[rr][tj + 32 * v];
+          const float4 yl = *(const float4*)&yls[rr][tj + 32 * v];
+          df_madd2(hi[u][v][0], lo[u][v][0], xv, yh.x, yl.x);
+          df_madd2(hi[u][v][1], lo[u][v][1], xv, yh.y, yl.y);
+          df_madd2(hi[u][v][2], lo[u][v][2], xv, yh.z, yl.z);
+          df_madd2(hi[u][v][3], lo[u][v][3], xv, yh.w, yl.w);
         }
       }
     }
   }
-  double* out = part + (int64_t)blockIdx.x * nent;
+  double* out = part + (int64_t)blockIdx.x * k * k;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int e = tid + 256 * q;
-    if (q < per && e < nent) out[e] = (double)hi[q] + (double)lo[q];
-  }
+  for (int u = 0; u < NU; ++u)
+#pragma unroll
+    for (int v = 0; v < NU; ++v)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ti + 32 * u, j = tj + 32 * v + q;
+        if (i < k && j < k) out[i * k + j] = (double)hi[u][v][q] + (double)lo[u][v][q];
+      }
 }
 
 __global__ void k_gram_df_reduce(const double* __restrict__ part, int64_t nb, int k, double* C, int64_t ldc) {
@@ -256,8 +272,34 @@ __global__ void k_gram_df_reduce(const double* __restrict__ part, int64_t nb, in
 // ---------------------------------------------------------------- U S
 // Out (n x k, FP64) = X (n x k, FP32) S (k x k, FP64): one warp per row,
 // lane = output column (two columns for k > 32).
-__global__ void __launch_bounds__(256) k_lift_df(const float* __restrict__ X, int64_t ldx, const double* __restrict__ S,
-                                                 int k, int64_t n, double* __restrict__ Out, int64_t ldo) {
+// k <= 32: column `lane` of S (split into hi + lo) in registers.
+__global__ void __launch_bounds__(256) k_lift_df32(const float* __restrict__ X, int64_t ldx,
+                                                   const double* __restrict__ S, int k, int64_t n,
+                                                   double* __restrict__ Out, int64_t ldo) {
+  const int lane = threadIdx.x & 31;
+  float sh[32], sl[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    sh[q] = sl[q] = 0.f;
+    if (q < k && lane < k) split(S[q * k + lane], sh[q], sl[q]);
+  }
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
+    const float xv = lane < k ? X[r * ldx + lane] : 0.f;
+    float h = 0.f, l = 0.f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const float xq = __shfl_sync(0xffffffffu, xv, q);
+      if (q < k) df_madd(h, l, sh[q], sl[q], xq);
+    }
+    if (lane < k) Out[r * ldo + lane] = (double)h + (double)l;
+  }
+}
+
+// 32 < k <= 64: S split into shared memory, two output columns per lane.
+__global__ void __launch_bounds__(256) k_lift_df64(const float* __restrict__ X, int64_t ldx,
+                                                   const double* __restrict__ S, int k, int64_t n,
+                                                   double* __restrict__ Out, int64_t ldo) {
   __shared__ float sh[64][64], sl[64][64];
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) split(S[e], sh[e / k][e % k], sl[e / k][e % k]);
   __syncthreads();
@@ -270,10 +312,10 @@ __global__ void __launch_bounds__(256) k_lift_df(const float* __restrict__ X, in
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
     for (int q = 0; q < k; ++q) {
       const float xq = __shfl_sync(0xffffffffu, q < 32 ? xv0 : xv1, q & 31);
-      if (lane < k) df_madd(h0, l0, sh[q][lane], sl[q][lane], xq);
+      df_madd(h0, l0, sh[q][lane], sl[q][lane], xq);
       if (lane + 32 < k) df_madd(h1, l1, sh[q][lane + 32], sl[q][lane + 32], xq);
     }
-    if (lane < k) Out[r * ldo + lane] = (double)h0 + (double)l0;
+    Out[r * ldo + lane] = (double)h0 + (double)l0;
     if (lane + 32 < k) Out[r * ldo + lane + 32] = (double)h1 + (double)l1;
   }
 }
@@ -325,25 +367,35 @@ __global__ void __launch_bounds__(256) k_sign_part(const double* __restrict__ X,
   }
 }
 
+// one warp per column: lanes scan the block partials, then a shuffle reduction
 __global__ void k_sign_final(const double* __restrict__ X, int64_t ldx, int w, int64_t nb,
                              const unsigned long long* __restrict__ pkey, const int64_t* __restrict__ prow,
                              int* __restrict__ flip) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= w) return;
   unsigned long long bk = 0;
   int64_t br = INT64_MAX;
-  for (int64_t b = 0; b < nb; ++b) {
+  for (int64_t b = lane; b < nb; b += 32) {
     const unsigned long long kq = pkey[b * w + c];
     const int64_t rq = prow[b * w + c];
     if (rq == INT64_MAX) continue;
     if (br == INT64_MAX || kq > bk || (kq == bk && rq < br)) { bk = kq; br = rq; }
   }
-  int f = 0;
-  if (br != INT64_MAX) {
-    const long long bits = reinterpret_cast<const long long*>(X + br * ldx)[c];
-    f = (bits < 0 && (bits & 0x7fffffffffffffffll) != 0) ? 1 : 0;  // strictly negative
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+    const int64_t orow = __shfl_down_sync(0xffffffffu, br, o);
+    if (orow != INT64_MAX && (br == INT64_MAX || ok > bk || (ok == bk && orow < br))) { bk = ok; br = orow; }
   }
-  flip[c] = f;
+  if (lane == 0) {
+    int f = 0;
+    if (br != INT64_MAX) {
+      const long long bits = reinterpret_cast<const long long*>(X + br * ldx)[c];
+      f = (bits < 0 && (bits & 0x7fffffffffffffffll) != 0) ? 1 : 0;  // strictly negative
+    }
+    flip[c] = f;
+  }
 }
 
 __global__ void k_sign_apply(double* __restrict__ X, int64_t ldx, int w, int64_t n, const int* __restrict__ flip) {
@@ -395,7 +447,10 @@ int gram_df(const float* X, int64_t ldx, const float* Yh, const float* Yl, int64
   int64_t rpb = (n + nb - 1) / nb;
   rpb = ((rpb + kDfRows - 1) / kDfRows) * kDfRows;
   nb = (n + rpb - 1) / rpb;
-  k_gram_df<<<(unsigned)nb, 256, 0, s>>>(X, ldx, Yh, Yl, ldy, k, n, rpb, part);
+  if (k <= 32)
+    k_gram_df<1><<<(unsigned)nb, 256, 0, s>>>(X, ldx, Yh, Yl, ldy, k, n, rpb, part);
+  else
+    k_gram_df<2><<<(unsigned)nb, 256, 0, s>>>(X, ldx, Yh, Yl, ldy, k, n, rpb, part);
   k_gram_df_reduce<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(part, nb, k, C, ldc);
   return 2;
 }
@@ -404,7 +459,10 @@ int lift_df(const float* X, int64_t ldx, const double* S, int k, int64_t n, doub
   if (n <= 0 || k <= 0 || k > 64) return 0;
   int64_t blocks = (n + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_lift_df<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, S, k, n, Out, ldo);
+  if (k <= 32)
+    k_lift_df32<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, S, k, n, Out, ldo);
+  else
+    k_lift_df64<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, S, k, n, Out, ldo);
   return 1;
 }
 
@@ -416,7 +474,7 @@ int sign_normalize_fast(double* X, int64_t ldx, int w, int64_t n, double* part, 
   unsigned long long* pkey = reinterpret_cast<unsigned long long*>(part);
   int* flip = reinterpret_cast<int*>(part + nb * w);
   k_sign_part<<<(unsigned)nb, 256, 0, s>>>(X, ldx, w, n, rpb, pkey, ipart);
-  k_sign_final<<<1, 64, 0, s>>>(X, ldx, w, nb, pkey, ipart, flip);
+  k_sign_final<<<(unsigned)((w + 7) / 8), 256, 0, s>>>(X, ldx, w, nb, pkey, ipart, flip);
   int64_t blocks = (n + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_sign_apply<<<(unsigned)blocks, 256, 0, s>>>(X, ldx, w, n, flip);
