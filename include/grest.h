@@ -148,6 +148,9 @@ typedef struct {
   double prof_work[5];
   int64_t prof_launches[5];
   int64_t kernel_launches; /* kernels this library enqueued during the step       */
+  /* GREST_FLAG_PROFILE: compulsory HBM bytes per class (each operand block read
+   * once, each output written once; SpMM as in prof_work). */
+  double prof_bytes[5];
 } grest_stats;
 
 /* Fill *cfg with defaults for k tracked pairs: ADJ, AUTO, L = P = 100

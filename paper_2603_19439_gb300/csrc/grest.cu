@@ -97,6 +97,7 @@ struct grest_ctx {
   int prof_n = 0;
   int prof_cls[kProfEvents / 2];
   double prof_work[kProfEvents / 2];
+  double prof_bytes[kProfEvents / 2];
   bool profiling() const { return (cfg.flags & GREST_FLAG_PROFILE) != 0; }
 };
 
@@ -219,17 +220,19 @@ int prof_begin(grest_ctx* c) {
   return i;
 }
 
-void prof_end(grest_ctx* c, int i, int cls, double work) {
+void prof_end(grest_ctx* c, int i, int cls, double work, double bytes = 0.0) {
   if (i < 0) return;
   cudaEventRecord(c->pev[i + 1], c->stream);
   c->prof_cls[i / 2] = cls;
   c->prof_work[i / 2] = work;
+  c->prof_bytes[i / 2] = bytes;
 }
 
 void prof_collect(grest_ctx* c, grest_stats& st) {
   for (int k = 0; k < 5; ++k) {
     st.prof_ms[k] = 0.0;
     st.prof_work[k] = 0.0;
+    st.prof_bytes[k] = 0.0;
     st.prof_launches[k] = 0;
   }
   for (int i = 0; i + 1 < c->prof_n; i += 2) {
@@ -238,6 +241,7 @@ void prof_collect(grest_ctx* c, grest_stats& st) {
     int k = c->prof_cls[i / 2];
     st.prof_ms[k] += ms;
     st.prof_work[k] += c->prof_work[i / 2];
+    st.prof_bytes[k] += c->prof_bytes[i / 2];
     st.prof_launches[k] += 1;
   }
   c->prof_n = 0;
@@ -262,7 +266,8 @@ void prof_spmm(grest_ctx* c, int p, int w, int64_t r0, int64_t r1, int64_t col_l
   if (nnz_proc < 0) nnz_proc = c->nnz;
   if (x_rows < 0) x_rows = r1 - r0;
   const double eb = c->g.val ? 12.0 : 4.0;
-  prof_end(c, p, 0, 12.0 * (r1 - r0) + eb * nnz_proc + w * (ybytes * (r1 - r0) + xbytes * x_rows));
+  const double by = 12.0 * (r1 - r0) + eb * nnz_proc + w * (ybytes * (r1 - r0) + xbytes * x_rows);
+  prof_end(c, p, 0, by, by);
 }
 
 void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
@@ -291,7 +296,7 @@ void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, in
   int p = prof_begin(c);
   gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
-  prof_end(c, p, 1, 2.0 * n * a * b);
+  prof_end(c, p, 1, 2.0 * n * a * b, 8.0 * n * (X == Y && a == b ? a : a + b));
 }
 
 void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
@@ -302,7 +307,7 @@ void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int6
     done = gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) == 0;
   if (!done) gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
-  prof_end(c, p, 1, 2.0 * n * a * b);
+  prof_end(c, p, 1, 2.0 * n * a * b, 4.0 * n * (X == Y && a == b ? a : a + b));
 }
 
 void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X, int64_t ldx, const double* B,
@@ -310,7 +315,7 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X,
   int p = prof_begin(c);
   gemm_nn_f64(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
   if (n > 0 && cc > 0) c->launches += 1;
-  prof_end(c, p, 2, 2.0 * n * a * cc);
+  prof_end(c, p, 2, 2.0 * n * a * cc, 8.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)));
 }
 
 void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, int64_t ldx, const double* B,
@@ -323,7 +328,7 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, 
     gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
     if (n > 0 && cc > 0) c->launches += 1;
   }
-  prof_end(c, p, 2, 2.0 * n * a * cc);
+  prof_end(c, p, 2, 2.0 * n * a * cc, 4.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)));
 }
 
 // f32: the projected problem's entries come from FP32 blocks (mixed path), so
@@ -498,14 +503,17 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   float* MUl = MUh + (size_t)c->g.n_cap * c->ldu;
   int p = prof_begin(c);
   c->launches += gram_df(c->U32, c->ldu, c->U32, nullptr, c->ldu, K, N2, c->G, K, c->part, c->part_cap, s);
-  prof_end(c, p, 1, 2.0 * N2 * K * K);
+  prof_end(c, p, 1, 2.0 * N2 * K * K, 4.0 * N2 * K);
   p = prof_begin(c);
   c->launches += spmm_df(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, c->U32, c->ldu, MUh, MUl, c->ldu,
                          K, N2, s);
-  prof_end(c, p, 0, 12.0 * N2 + (c->g.val ? 12.0 : 4.0) * c->nnz + K * (8.0 * N2 + 4.0 * N2));
+  {
+    const double by = 12.0 * N2 + (c->g.val ? 12.0 : 4.0) * c->nnz + K * (8.0 * N2 + 4.0 * N2);
+    prof_end(c, p, 0, by, by);
+  }
   p = prof_begin(c);
   c->launches += gram_df(c->U32, c->ldu, MUh, MUl, c->ldu, K, N2, c->H, K, c->part, c->part_cap, s);
-  prof_end(c, p, 1, 2.0 * N2 * K * K);
+  prof_end(c, p, 1, 2.0 * N2 * K * K, 12.0 * N2 * K);
   p = prof_begin(c);
   c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
@@ -518,7 +526,7 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   p = prof_begin(c);
   c->launches += lift_df(c->U32, c->ldu, c->Gs, K, N2, c->U, c->ldu, s);
   c->launches += sign_normalize_fast(c->U, c->ldu, K, N2, c->part, c->ipart, s);
-  prof_end(c, p, 2, 2.0 * N2 * K * K);
+  prof_end(c, p, 2, 2.0 * N2 * K * K, 4.0 * N2 * K + 8.0 * N2 * K * 3);
   CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
   return GREST_OK;
 }

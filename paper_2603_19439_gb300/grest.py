@@ -56,7 +56,7 @@ class Stats(C.Structure):
                 ("ms_total", C.c_float), ("ms_graph", C.c_float), ("ms_spmm", C.c_float), ("ms_basis", C.c_float),
                 ("ms_project", C.c_float), ("ms_eig", C.c_float), ("ms_lift", C.c_float), ("ms_refine", C.c_float),
                 ("prof_ms", C.c_double * 5), ("prof_work", C.c_double * 5), ("prof_launches", C.c_int64 * 5),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("prof_bytes", C.c_double * 5)]
 
     def as_dict(self):
         out = {}

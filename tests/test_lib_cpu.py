@@ -45,7 +45,7 @@ def test_struct_sizes_match_header():
     # int32 x 9, pad, uint64, double, int64 x 3
     assert ctypes.sizeof(grest.Config) == 40 + 8 + 8 + 24
     assert ctypes.sizeof(grest.Update) == 8 * 10 + 8
-    assert ctypes.sizeof(grest.Stats) == 24 + 24 + 48 + 32 + 3 * 40 + 8
+    assert ctypes.sizeof(grest.Stats) == 24 + 24 + 48 + 32 + 3 * 40 + 8 + 40
 
 
 def test_init_rejects_bad_arguments_without_gpu(lib):
