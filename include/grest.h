@@ -67,8 +67,17 @@ enum {
 };
 
 enum { GREST_FP64 = 0, GREST_MIXED = 1 };                 /* arithmetic of the step */
-enum { GREST_PROJ_EXACT = 0, GREST_PROJ_LOWRANK = 1 };   /* Eq. (main2) / Eq. (main3) */
-enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };          /* W = P_perp M_new X_bar / P_perp Delta X_bar */
+/* Projected operator: EXACT forms H = Z^T M_new Z (Eq. main2); LOWRANK forms
+ * the paper's surrogate H = (X_bar^T Z)^T Lambda (X_bar^T Z) + Z^T Delta Z
+ * (Eq. main3, Alg. 2 as printed), where Delta = M_new - M_old (M_old padded
+ * with zero rows and columns for new nodes) and Lambda the previous Ritz
+ * values; it needs no product with the whole graph.
+ * W block: RESID uses P_perp (M_new X_bar); DELTA the paper's P_perp (Delta X_bar)
+ * (Sec. 3.3).  LOWRANK and DELTA are available for GREST_OP_ADJ and
+ * GREST_OP_LAP, for batches without node removal (GREST_ERR_UNSUPPORTED
+ * otherwise); LOWRANK runs in the FP64 path only. */
+enum { GREST_PROJ_EXACT = 0, GREST_PROJ_LOWRANK = 1 };
+enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };
 
 /* grest_config.flags */
 #define GREST_FLAG_CHECK 1u   /* after each step compute residual diagnostics into grest_stats */

@@ -107,6 +107,7 @@ struct GraphWork {
   int32_t* erow = nullptr;   // [ent_cap]
   double* ew = nullptr;      // [ent_cap] weight (inserts)
   int32_t* eins = nullptr;   // [ent_cap] inserts before entry (prefix)
+  double* edel = nullptr;    // [ent_cap] old weight of a deleted edge, by sorted position
   int32_t* tmp_col = nullptr;// [tmp_cap]
   double* tmp_val = nullptr; // [tmp_cap]
   int64_t* dn_pref = nullptr;// [max removed nodes + 1]
@@ -120,6 +121,13 @@ constexpr int kLongRow = 512;
 // These launchers return the number of kernels they enqueued.
 int graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, cudaStream_t s);
 int graph_refresh_derived(Csr& g, GraphWork& w, int64_t n_rows, cudaStream_t s);
+// Y = (M_new - M_old) X for the batch just applied (ADJ or LAP; M_old padded
+// with zero rows / columns for new nodes; no node removal): Y over all N2 rows.
+// dmax_old: device copy of d_max before the update.  Returns launches.
+int delta_apply(const Csr& g, const GraphWork& w, int op, const double* X, int64_t ldx, double* Y, int64_t ldy, int wd,
+                int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s);
+int delta_apply(const Csr& g, const GraphWork& w, int op, const float* X, int64_t ldx, float* Y, int64_t ldy, int wd,
+                int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s);
 // total row length over rows [0, n) into *out (device int64)
 int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s);
 

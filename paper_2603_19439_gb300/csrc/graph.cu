@@ -13,6 +13,8 @@
 //
 // Validation finishes before commit; every state-changing kernel returns at
 // once when the error word is set, so a rejected batch changes nothing.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace grest {
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(256) k_merge_rows(const int32_t* touched, cons
                                                      const int32_t* eins, const uint8_t* delflag, const int64_t* row_off,
                                                      const int32_t* row_len, const int32_t* col, const double* val,
                                                      const int64_t* tmp_off, int32_t* tmp_col, double* tmp_val,
-                                                     int32_t* new_len, int32_t* err) {
+                                                     int32_t* new_len, double* edel, int32_t* err) {
   if (*err) return;
   const int64_t nt = *n_touched;
   for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
@@ -288,7 +290,10 @@ __global__ void __launch_bounds__(256) k_merge_rows(const int32_t* touched, cons
     for (int64_t j = threadIdx.x; j < olen; j += blockDim.x) {
       int32_t c = old[j];
       int64_t l = lower_bound_key(K, L, c);
-      if (l < L && key_col(K[l]) == c && key_tag(K[l]) != kTagIns) continue;  // deleted
+      if (l < L && key_col(K[l]) == c && key_tag(K[l]) != kTagIns) {  // deleted: keep its old weight
+        edel[s0 + l] = oldv ? oldv[j] : 1.0;
+        continue;
+      }
       int64_t ins_before = l < L ? P[l] : nins;
       int64_t del_before = l - ins_before;
       int64_t pos = j - del_before + ins_before;
@@ -437,6 +442,59 @@ __global__ void k_sum_len(const int32_t* row_len, int64_t n, unsigned long long*
   if (threadIdx.x == 0) atomicAdd(out, red[0]);
 }
 
+
+// --- Delta X = (M_new - M_old) X for the paper's W block (P_perp Delta X_bar,
+// Sec. 3.3) and the low-rank projection (Eq. main3), ADJ and LAP.  M_old is
+// padded with zero rows and columns for the S new nodes.
+//   diagonal: delta_r = alpha_new - d_r (new rows), alpha_new - alpha_old
+//             (old live rows; the degree change is added per touched row),
+//             zero for ADJ and for tombstoned rows
+//   touched rows: sum over the row's batch entries of (+w insert | -w_old
+//             delete) x_c, and for LAP old rows - (d_new - d_old) x_r
+template <typename T>
+__global__ void k_delta_diag(const T* __restrict__ X, int64_t ldx, T* __restrict__ Y, int64_t ldy, int w, int64_t N,
+                             int64_t N2, int op, const double* __restrict__ deg, const uint8_t* __restrict__ live,
+                             const double* __restrict__ dmax_new, const double* __restrict__ dmax_old) {
+  const double an = 2.0 * (*dmax_new), ao = 2.0 * (*dmax_old);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N2 * w; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / w;
+    const int c = (int)(e % w);
+    double dl = 0.0;
+    if (op == GREST_OP_LAP && live[r]) dl = r >= N ? an - deg[r] : an - ao;
+    Y[r * ldy + c] = (T)(dl * (double)X[r * ldx + c]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_delta_rows(const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                    int64_t ldy, int w, int64_t N, int op,
+                                                    const int32_t* __restrict__ touched,
+                                                    const int64_t* __restrict__ n_touched,
+                                                    const int64_t* __restrict__ seg, const uint64_t* __restrict__ ekey,
+                                                    const double* __restrict__ ew, const double* __restrict__ edel) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nt = *n_touched;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt; t += warps) {
+    const int32_t r = touched[t];
+    const int64_t s0 = seg[r], L = seg[r + 1] - s0;
+    for (int c0 = 0; c0 < w; c0 += 32) {
+      const int c = c0 + lane;
+      double acc = 0.0, dd = 0.0;
+      for (int64_t i = 0; i < L; ++i) {
+        const uint64_t k = ekey[s0 + i];
+        const double v = key_tag(k) == kTagIns ? ew[s0 + key_idx(k)] : -edel[s0 + i];
+        dd += v;
+        if (c < w) acc = fma(v, (double)X[(int64_t)key_col(k) * ldx + c], acc);
+      }
+      if (c < w) {
+        if (op == GREST_OP_LAP && r < N) acc -= dd * (double)X[(int64_t)r * ldx + c];
+        Y[(int64_t)r * ldy + c] += (T)acc;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s) {
@@ -527,7 +585,7 @@ int graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, cud
   ++nk;
   k_merge_rows<<<gsz, 256, 0, s>>>(w.touched, w.scalars + 0, w.seg, w.ekey, w.ew, w.eins, w.delflag, g.row_off,
                                     g.row_len, g.col, g.val, w.tmp_off, w.tmp_col, g.val ? w.tmp_val : nullptr,
-                                    w.new_len, err);
+                                    w.new_len, w.edel, err);
   ++nk;
   // capacity: touched rows that outgrow their slot
   const int64_t max_t = N2;  // upper bound of the touched count
@@ -547,6 +605,28 @@ int graph_apply_batch(Csr& g, GraphWork& w, const BatchDev& b, int32_t* err, cud
     ++nk;
   }
   return nk;
+}
+
+template <typename T>
+int delta_apply_t(const Csr& g, const GraphWork& w, int op, const T* X, int64_t ldx, T* Y, int64_t ldy, int wd,
+                  int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s) {
+  if (N2 <= 0 || wd <= 0) return 0;
+  const int64_t tot = N2 * wd;
+  k_delta_diag<T><<<(unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 32), 256, 0, s>>>(
+      X, ldx, Y, ldy, wd, N, N2, op, g.deg, g.live, g.dmax, dmax_old);
+  k_delta_rows<T><<<152 * 8, 256, 0, s>>>(X, ldx, Y, ldy, wd, N, op, w.touched, w.scalars + 0, w.seg, w.ekey, w.ew,
+                                          w.edel);
+  return 2;
+}
+
+int delta_apply(const Csr& g, const GraphWork& w, int op, const double* X, int64_t ldx, double* Y, int64_t ldy, int wd,
+                int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s) {
+  return delta_apply_t<double>(g, w, op, X, ldx, Y, ldy, wd, N, N2, dmax_old, s);
+}
+
+int delta_apply(const Csr& g, const GraphWork& w, int op, const float* X, int64_t ldx, float* Y, int64_t ldy, int wd,
+                int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s) {
+  return delta_apply_t<float>(g, w, op, X, ldx, Y, ldy, wd, N, N2, dmax_old, s);
 }
 
 }  // namespace grest

@@ -72,6 +72,8 @@ struct grest_ctx {
   int64_t part_cap = 0;
   int64_t* ipart = nullptr;
   int* piv = nullptr;    // pivot order of the pivoted Cholesky (cmax + K ints)
+  double* dmax_old = nullptr;   // d_max before the update (DELTA / LOWRANK modes)
+  double* XZ = nullptr;         // X_bar^T Z (LOWRANK mode), 64 x mmax
   uint8_t* gemm_img = nullptr;  // tensor-core GEMM: B^T operand images
   size_t gemm_img_cap = 0;
   double* eigwork = nullptr;
@@ -141,7 +143,7 @@ void free_ctx(grest_ctx* c) {
                   c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
                   c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
-                  c->ipart, c->piv, c->gemm_img, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+                  c->ipart, c->piv, c->gemm_img, c->dmax_old, c->XZ, c->gw.edel, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_info) cudaFreeHost(c->h_info);
@@ -178,9 +180,9 @@ grest_status ensure_graph_work(grest_ctx* c, int64_t entries) {
   GraphWork& w = c->gw;
   if (entries > w.ent_cap) {
     int64_t cap = std::max<int64_t>(entries, 2 * w.ent_cap);
-    cudaFree(w.ekey); cudaFree(w.ew); cudaFree(w.eins);
-    w.ekey = nullptr; w.ew = nullptr; w.eins = nullptr;
-    CK(dalloc(&w.ekey, cap)); CK(dalloc(&w.ew, cap)); CK(dalloc(&w.eins, cap));
+    cudaFree(w.ekey); cudaFree(w.ew); cudaFree(w.eins); cudaFree(w.edel);
+    w.ekey = nullptr; w.ew = nullptr; w.eins = nullptr; w.edel = nullptr;
+    CK(dalloc(&w.ekey, cap)); CK(dalloc(&w.ew, cap)); CK(dalloc(&w.eins, cap)); CK(dalloc(&w.edel, cap));
     w.ent_cap = cap;
   }
   int64_t tneed = c->g.nnz_cap + w.ent_cap;
@@ -289,6 +291,15 @@ void spmm(grest_ctx* c, const float* X, int64_t ldx, double* Y, int64_t ldy, int
   int p = prof_begin(c);
   spmm_f32_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
   prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 8.0);
+}
+
+// Y = Delta X (Sec. 3.3 block, Eq. main3) for the batch just applied
+template <typename T>
+void delta(grest_ctx* c, const T* X, int64_t ldx, T* Y, int64_t ldy, int w, int64_t N, int64_t N2) {
+  int p = prof_begin(c);
+  c->launches += delta_apply(c->g, c->gw, c->cfg.op, X, ldx, Y, ldy, w, N, N2, c->dmax_old, c->stream);
+  const double by = (double)sizeof(T) * N2 * w * 2.0;
+  prof_end(c, p, 0, by, by);
 }
 
 void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n,
@@ -484,6 +495,16 @@ __global__ void k_small_mm(const double* A, const double* B, int k, double* out)
   }
 }
 
+// Eq. main3: H += (X_bar^T Z)^T Lambda (X_bar^T Z); XZ is ku x m (ld m)
+__global__ void k_lowrank_add(const double* XZ, int m, int ku, const double* lam, double* H, int64_t ldh) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  const int i = (int)(e / m), j = (int)(e % m);
+  double s = 0.0;
+  for (int k = 0; k < ku; ++k) s = fma(XZ[(int64_t)k * m + i] * lam[k], XZ[(int64_t)k * m + j], s);
+  H[(int64_t)i * ldh + j] += s;
+}
+
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, a, b);
@@ -557,13 +578,33 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
     c->Ku = r1;
   }
   const int Ku = c->Ku;
-  // A3: Y1 = M X_bar
-  spmm(c, Z, ldz, MZ, ldz, Ku, 0, N2, 0);
+  const bool lowrank = c->cfg.projection == GREST_PROJ_LOWRANK;
+  const bool delta_w = c->cfg.w_block == GREST_WB_DELTA;
+  // A3: MZ[:, 0:Ku] = M X_bar (EXACT projection) or Delta X_bar (LOWRANK,
+  // Eq. main3); the W block is projected from M X_bar (RESID) or Delta X_bar
+  // (DELTA, Sec. 3.3); when that is the other product it goes to V2
+  const T* src = MZ;
+  int64_t lds = ldz;
+  if (!lowrank) {
+    spmm(c, Z, ldz, MZ, ldz, Ku, 0, N2, 0);
+    if (delta_w) {
+      delta(c, (const T*)Z, ldz, V2, ldv, Ku, N, N2);
+      src = V2;
+      lds = ldv;
+    }
+  } else {
+    delta(c, (const T*)Z, ldz, MZ, ldz, Ku, N, N2);
+    if (!delta_w) {
+      spmm(c, Z, ldz, V2, ldv, Ku, 0, N2, 0);
+      src = V2;
+      lds = ldv;
+    }
+  }
   CK(cudaEventRecord(c->ev[2], s));
-  // A4: C = X_bar^T Y1; W = Y1 - X_bar C, re-projected once
+  // A4: C = X_bar^T src; W = src - X_bar C, re-projected once
   T* W = Z + Ku;
-  gram(c, Z, ldz, Ku, MZ, ldz, Ku, N2, c->Cm, Ku, false);
-  gemm(c, N2, Ku, Ku, -1.0, Z, ldz, c->Cm, Ku, 1.0, MZ, ldz, W, ldz);
+  gram(c, Z, ldz, Ku, src, lds, Ku, N2, c->Cm, Ku, false);
+  gemm(c, N2, Ku, Ku, -1.0, Z, ldz, c->Cm, Ku, 1.0, src, lds, W, ldz);
   project_out(c, W, ldz, Ku, N2);
   // A5: new-node block
   int cb = 0;
@@ -634,11 +675,22 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   }
   const int m = Ku + r;
   if (m < K) return GREST_ERR_NUMERIC;
-  // A7: MQ = M Q
-  if (r > 0) spmm(c, V, ldz, MZ + Ku, ldz, r, 0, N2, 0);
+  // A7: MQ = M Q (EXACT) or Delta Q (LOWRANK)
+  if (r > 0) {
+    if (!lowrank)
+      spmm(c, V, ldz, MZ + Ku, ldz, r, 0, N2, 0);
+    else
+      delta(c, (const T*)V, ldz, MZ + Ku, ldz, r, N, N2);
+  }
   CK(cudaEventRecord(c->ev[4], s));
-  // A8: H = Z^T (M Z) (Eq. main2), symmetrized
+  // A8: H = Z^T (M Z) (Eq. main2), or Z^T (Delta Z) + (X_bar^T Z)^T Lambda
+  // (X_bar^T Z) (Eq. main3); symmetrized
   gram(c, Z, ldz, m, MZ, ldz, m, N2, c->H, m, false);
+  if (lowrank) {
+    gram(c, Z, ldz, Ku, Z, ldz, m, N2, c->XZ, m, false);
+    k_lowrank_add<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, s>>>(c->XZ, m, Ku, c->theta, c->H, m);
+    c->launches += 1;
+  }
   symmetrize(c->H, m, m, s);
   c->launches += 1;
   CK(cudaEventRecord(c->ev[5], s));
@@ -738,9 +790,16 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   if (cfg->k < 1 || cfg->k > 64 || cfg->op < 0 || cfg->op > 2 || cfg->L < 1 || cfg->P < 0 || cfg->L + cfg->P > 256 ||
       cfg->subspace < 0 || cfg->subspace > 3 || !(cfg->drop_tol > 0.0) || cfg->k > n)
     return GREST_ERR_INVALID_ARG;
-  if ((cfg->precision != GREST_FP64 && cfg->precision != GREST_MIXED) || cfg->projection != GREST_PROJ_EXACT ||
-      cfg->w_block != GREST_WB_RESID)
+  if ((cfg->precision != GREST_FP64 && cfg->precision != GREST_MIXED) ||
+      (cfg->projection != GREST_PROJ_EXACT && cfg->projection != GREST_PROJ_LOWRANK) ||
+      (cfg->w_block != GREST_WB_RESID && cfg->w_block != GREST_WB_DELTA))
+    return GREST_ERR_INVALID_ARG;
+  // the explicit Delta of the paper's block and of Eq. main3 is formed for the
+  // adjacency and the shifted Laplacian; the low-rank surrogate has no FP64
+  // refinement in the mixed path
+  if ((cfg->projection == GREST_PROJ_LOWRANK || cfg->w_block == GREST_WB_DELTA) && cfg->op == GREST_OP_NLAP)
     return GREST_ERR_UNSUPPORTED;
+  if (cfg->projection == GREST_PROJ_LOWRANK && cfg->precision == GREST_MIXED) return GREST_ERR_UNSUPPORTED;
   if (!U0 || !theta0) return GREST_ERR_UNSUPPORTED;
   const int64_t nnz = rowptr[n];
   for (int64_t i = 0; i < n; ++i)
@@ -843,6 +902,8 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));
   IK(dalloc(&c->eigwork, eig_work_doubles(std::max(mm, c->q))));
   IK(dalloc(&c->piv, std::max(mm, c->q) + 8));
+  IK(dalloc(&c->dmax_old, 1));
+  IK(dalloc(&c->XZ, (int64_t)64 * mm));
   c->gemm_img_cap = gemm_tc_img_bytes(512, 256);
   IK(dalloc(&c->gemm_img, c->gemm_img_cap));
   IK(dalloc(&c->err, 1));
@@ -894,6 +955,8 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
       (u->n_del_nodes > 0 && !u->del_nodes))
     return GREST_ERR_INVALID_ARG;
   if (u->ins_w && !c->g.val) return GREST_ERR_INVALID_ARG;
+  const bool delta_modes = c->cfg.projection == GREST_PROJ_LOWRANK || c->cfg.w_block == GREST_WB_DELTA;
+  if (delta_modes && u->n_del_nodes > 0) return GREST_ERR_UNSUPPORTED;  // Delta of a removed row is not kept
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
   cudaStream_t s = c->stream;
   const int64_t N = c->g.n, S = u->n_new_nodes;
@@ -939,6 +1002,7 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   bd.dn = c->b_dn;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
   c->batch_new_edges = u->n_ins;
+  if (delta_modes) CK(cudaMemcpyAsync(c->dmax_old, c->g.dmax, sizeof(double), cudaMemcpyDeviceToDevice, s));
   {
     int p = prof_begin(c);
     c->launches += graph_apply_batch(c->g, c->gw, bd, c->err, s);

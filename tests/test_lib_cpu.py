@@ -59,3 +59,24 @@ def test_init_rejects_bad_arguments_without_gpu(lib):
     assert L.grest_init(ctypes.byref(cfg), 1, rp.ctypes.data, None, None, None, None, None, ctypes.byref(h)) == 1
     cfg = grest.default_config(2, L=200, P=100)
     assert L.grest_init(ctypes.byref(cfg), 1, rp.ctypes.data, None, None, None, None, None, ctypes.byref(h)) == 1
+
+
+def test_init_rejects_unsupported_modes_without_gpu(lib):
+    """The explicit Delta of DELTA / LOWRANK exists for ADJ and LAP; LOWRANK has
+    no mixed-precision refinement.  These are refused before any device call."""
+    import numpy as np
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    h = ctypes.c_void_p()
+    rp = np.array([0, 0, 0], np.int64)
+    u0 = np.eye(2)
+    t0 = np.ones(2)
+    for kw in (dict(op=grest.OP_NLAP, projection=grest.PROJ_LOWRANK), dict(op=grest.OP_NLAP, w_block=grest.WB_DELTA),
+               dict(precision=grest.MIXED, projection=grest.PROJ_LOWRANK)):
+        cfg = grest.default_config(1, **kw)
+        st = L.grest_init(ctypes.byref(cfg), 2, rp.ctypes.data, None, None, u0.ctypes.data, t0.ctypes.data, None,
+                          ctypes.byref(h))
+        assert st == 8, (kw, st)
+    cfg = grest.default_config(1, projection=7)
+    assert L.grest_init(ctypes.byref(cfg), 2, rp.ctypes.data, None, None, u0.ctypes.data, t0.ctypes.data, None,
+                        ctypes.byref(h)) == 1
