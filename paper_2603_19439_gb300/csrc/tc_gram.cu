@@ -14,13 +14,17 @@
 // the operands (K-major: each operand row is one column of X or Y with its
 // rows contiguous) are transposes of the row-major blocks; kind::tf32 takes
 // K-major operands only (a transposed-operand descriptor produced no result
-// on this part), so the transpose is done in shared memory, pipelined:
+// on this part), so the transpose is done by the CTA's threads, pipelined:
 //   warp 0     TMA producer: raw 32-row tiles of X and Y into a ring
 //   warp 1     tensor-memory owner and MMA issuer (one thread)
-//   warps 2-9  transpose + hi / lo split of each raw tile into a ring of
-//              128B-swizzled operand tiles; every 256 rows, drain the
-//              previous span's accumulator (double-buffered in tensor
-//              memory) into the double-float registers
+//   warps 2-5  transpose + hi / lo split of X into the A operand, written
+//              straight into tensor memory (lane = operand row)
+//   warps 6-9  the same for Y into the B operand (shared memory, 128B
+//              swizzle); every 256 rows all eight warps drain the previous
+//              span's accumulator (double-buffered in tensor memory) into
+//              double-float registers
+// Tensor memory: two 128-column accumulators and four 64-column A stages
+// (hi, lo); shared memory: the raw ring and four B stages.
 // Every mbarrier wait is bounded; on a timeout the kernel records an error,
 // waits (bounded) for its own copies and MMAs in flight, frees its tensor
 // memory and returns.
@@ -37,7 +41,8 @@ constexpr int kSpan = 8;           // chunks per FP32 accumulation span (256 row
 constexpr int kTileG = 128;        // C tile edge
 constexpr int kGramThreads = 320;  // 10 warps
 constexpr int kOpBytes = 128 * 128;  // one 128-row K-major operand tile (32 TF32 per row), swizzled
-constexpr int kMaxRaw = 4, kMaxOp = 2;
+constexpr int kMaxRaw = 4, kMaxOp = 4;
+constexpr uint32_t kAcol = 256;  // first tensor-memory column of the A stages (64 columns each)
 constexpr int kSmemBudget = 225 * 1024;
 
 struct GramArgs {
@@ -87,11 +92,11 @@ __device__ __forceinline__ bool drain_span(int sp, uint32_t tmem, int N, int qua
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (colhalf * 64 < N) {
     uint32_t v[32];
-    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * N + colhalf * 64), v);
+    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + colhalf * 64), v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) two_sum_acc(hi[j], lo[j], __uint_as_float(v[j]));
     if (colhalf * 64 + 32 < N) {
-      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * N + colhalf * 64 + 32), v);
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + colhalf * 64 + 32), v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) two_sum_acc(hi[32 + j], lo[32 + j], __uint_as_float(v[j]));
     }
@@ -100,6 +105,26 @@ __device__ __forceinline__ bool drain_span(int sp, uint32_t tmem, int N, int qua
   __syncwarp();
   if (lane == 0) mbar_arrive(&acce[b]);
   return true;
+}
+
+// Transpose + split of one raw tile column r (operand row r, K = raw rows)
+// into tensor memory: hi at columns [acol, acol + 32), lo at [acol + 32,
+// acol + 64) of this warp's lanes; rows beyond the tile width are zero.
+__device__ __forceinline__ void convert_a_tmem(const float* __restrict__ raw, int w, int r, uint32_t taddr) {
+#pragma unroll
+  for (int q = 0; q < kRows / 8; ++q) {
+    uint32_t h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float v = r < w ? raw[(8 * q + i) * w + r] : 0.f;
+      const float hv = tf32_rna(v);
+      h[i] = __float_as_uint(hv);
+      l[i] = __float_as_uint(tf32_rna(v - hv));
+    }
+    tmem_st8(taddr + 8 * q, h);
+    tmem_st8(taddr + 32 + 8 * q, l);
+  }
+  tmem_wait_st();
 }
 
 __global__ void __launch_bounds__(kGramThreads, 1)
@@ -135,7 +160,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   const int raw_bytes = kRows * (p.bxw + p.byw) * 4;
   const int raw_stride = ((raw_bytes + 1023) / 1024) * 1024;
   const int op_b_bytes = N * 128;
-  const int op_stride = 2 * kOpBytes + 2 * op_b_bytes;
+  const int op_stride = 2 * op_b_bytes;  // B hi, B lo (A lives in tensor memory)
   uint8_t* raw0 = sm;
   uint8_t* op0 = sm + (size_t)R * raw_stride;
   if (tid == 0) {
@@ -155,7 +180,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
-  const uint32_t ncols = N <= 64 ? 128u : 256u;
+  const uint32_t ncols = 512u;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tmem_base)),
                  "r"(ncols));
@@ -196,14 +221,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         if (!mbar_wait(&op_full[st], (uint32_t)((q / S) & 1)) || abort_flag) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         uint8_t* op = op0 + (size_t)st * op_stride;
-        const uint32_t ah = smem_u32(op), al = ah + kOpBytes;
-        const uint32_t bh = diag ? ah : al + kOpBytes, bl = diag ? al : bh + op_b_bytes;
-        const uint32_t d = tmem + (uint32_t)(b * N);
+        const uint32_t bh = smem_u32(op), bl = bh + op_b_bytes;
+        const uint32_t ah = tmem + kAcol + 64u * st, al = ah + 32u;
+        const uint32_t d = tmem + (uint32_t)(b * 128);
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
-          mma_tf32(d, sdesc(ah + 32 * k4), sdesc(bh + 32 * k4), idesc, (q % kSpan != 0 || k4 > 0) ? 1u : 0u);
-          mma_tf32(d, sdesc(ah + 32 * k4), sdesc(bl + 32 * k4), idesc, 1u);
-          mma_tf32(d, sdesc(al + 32 * k4), sdesc(bh + 32 * k4), idesc, 1u);
+          mma_tf32_ts(d, ah + 8 * k4, sdesc(bh + 32 * k4), idesc, (q % kSpan != 0 || k4 > 0) ? 1u : 0u);
+          mma_tf32_ts(d, ah + 8 * k4, sdesc(bl + 32 * k4), idesc, 1u);
+          mma_tf32_ts(d, al + 8 * k4, sdesc(bh + 32 * k4), idesc, 1u);
         }
         mma_commit(&op_empty[st]);
         if (q % kSpan == kSpan - 1 || q == nloc - 1) mma_commit(&accf[b]);
@@ -214,10 +239,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
   } else {
     // ---------------- transpose / split, then drain spans into double-float registers
-    const int ct = tid - 64;                 // 0..255
-    const int half = ct >> 7, r = ct & 127;  // half 0: X -> A, half 1: Y -> B
-    const int quarter = warp & 3, colhalf = (warp - 2) >> 2;
-    const int row = quarter * 32 + lane;     // C row within the tile (TMEM lane)
+    const int quarter = warp & 3, colhalf = (warp - 2) >> 2;  // colhalf 0: A from X, 1: B from Y
+    const int row = quarter * 32 + lane;     // operand row / C row within the tile (TMEM lane)
+    const int r = row;
     float hi[64], lo[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
@@ -229,18 +253,20 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       if (abort_flag) { ok = false; break; }
       const float* raw = (const float*)(raw0 + (size_t)rs * raw_stride);
       uint8_t* op = op0 + (size_t)os * op_stride;
-      if (diag) {
-        // one operand serves as A and B: both halves convert X, each half of the K range
-        if (half == 0)
-          convert_tile<0, kRows / 8>(raw, p.bxw, r, op, op + kOpBytes);
-        else
-          convert_tile<kRows / 8, kRows / 4>(raw, p.bxw, r, op, op + kOpBytes);
-      } else if (half == 0) {
-        convert_tile<0, kRows / 4>(raw, p.bxw, r, op, op + kOpBytes);
-      } else if (r < N) {
-        convert_tile<0, kRows / 4>(raw + kRows * p.bxw, p.byw, r, op + 2 * kOpBytes, op + 2 * kOpBytes + op_b_bytes);
+      if (colhalf == 0) {
+        // A (from X) into tensor memory, this warp's lane quarter
+        convert_a_tmem(raw, p.bxw, r, tmem + ((uint32_t)(quarter * 32) << 16) + kAcol + 64u * os);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      } else {
+        // B (from Y, or from X on a diagonal tile) into shared memory
+        if (r < N) {
+          if (diag)
+            convert_tile<0, kRows / 4>(raw, p.bxw, r, op, op + op_b_bytes);
+          else
+            convert_tile<0, kRows / 4>(raw + kRows * p.bxw, p.byw, r, op, op + op_b_bytes);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
         mbar_arrive(&raw_empty[rs]);
@@ -306,7 +332,7 @@ int gram_f32_tc(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy,
   p.byw = b >= kTileG ? kTileG : ((b + 3) / 4) * 4;
   p.N = b >= kTileG ? kTileG : ((b + 15) / 16) * 16;
   const int raw_stride = ((kRows * (p.bxw + p.byw) * 4 + 1023) / 1024) * 1024;
-  const int op_stride = 2 * kOpBytes + 2 * p.N * 128;
+  const int op_stride = 2 * p.N * 128;
   p.op_stages = kMaxOp;
   int R = (kSmemBudget - 1024 - kMaxOp * op_stride) / raw_stride;
   if (R > kMaxRaw) R = kMaxRaw;
