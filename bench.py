@@ -232,7 +232,7 @@ def source_hash(files):
 
 
 def initial_pairs(tr, n, k, torch):
-    """Leading K pairs of A^(0) (Alg. 2, line 3: any direct eigensolver):
+    """Leading K pairs of A^(0) (the initial pairs of Alg. 2, from a direct eigensolver):
     ARPACK Lanczos whose products A x run in the library's SpMM."""
     import scipy.sparse.linalg as ssl
     x_d = torch.empty((n, 1), dtype=torch.float64, device="cuda")

@@ -21,6 +21,8 @@ order and notation, in float64 with NumPy/SciPy library primitives
   Sec. 4 (orthogonalization)  only P_perp [Delta X_bar, R] is orthonormalized
   Eq. (main2) / Eq. (main3)   H = Z^T M_new Z (exact) or its rank-K surrogate
   Alg. 1                      leading eigenpairs of H -> Ritz pairs (theta, Z f)
+  Sec. 5 (downstream task)    subgraph centrality X_K exp(Lambda_K) X_K^T 1, top-J
+                              sets and their overlap
 
 Readings where the paper is silent (each is restated in the design doc):
   R1  EXACT projection (Eq. main2) is the default; LOWRANK (Eq. main3) is a mode.
@@ -407,10 +409,36 @@ def grest_step(state: State, b, cfg: Config, weighted=False, keep=False):
     return State(A=Anew, live=live, X=Xnew, lam=theta[sel].copy(), step=state.step + 1), info
 
 
+# ------------------------------------------------------------ Sec. 5 downstream task
+
+def subgraph_centrality(X, lam, live):
+    """Sec. 5: exp(A) 1 approximated from the K tracked pairs as
+    X_K exp(Lambda_K) X_K^T 1, multiplied by exp(-max(lam)) (a positive common
+    factor, so the ranking is unchanged and nothing overflows).  Removed nodes
+    (live false) take no part in X^T 1 and get the value 0."""
+    X = np.where(live[:, None], X, 0.0)
+    s = X.T @ np.ones(X.shape[0])
+    c = X @ (np.exp(lam - lam.max()) * s)
+    return np.where(live, c, 0.0)
+
+
+def top_central(c, live, J):
+    """Sec. 5: the J most central live nodes, by value descending; equal values
+    go to the lower node id, so the set and its order are unique."""
+    ids = np.flatnonzero(live)
+    order = np.lexsort((ids, -c[ids]))
+    return ids[order[:J]]
+
+
+def central_overlap(found, ref):
+    """Sec. 5 accuracy measure: |I_hat intersect I| / J for two top-J id sets."""
+    return len(np.intersect1d(found, ref)) / max(len(ref), 1)
+
+
 # ------------------------------------------------------------ helpers for tests
 
 def init_state(n, rowptr, col, val, K, op, X0=None, lam0=None, dense_limit=4000):
-    """Initial pairs by a direct eigendecomposition (Alg. 2 line 3): dense eigh
+    """Initial pairs of Alg. 2 by a direct eigendecomposition: dense eigh
     for small graphs, scipy eigsh otherwise; the same X0 is given to both sides."""
     A = csr_from_arrays(n, rowptr, col, val)
     live = np.ones(n, bool)

@@ -494,3 +494,55 @@ def test_rsvd_steps_give_top_left_singular_vectors():
     assert sv[4] - sv[5] > 1e-3 * sv[0]
     assert sin_angle(Usv[:, :5], R) < 1e-10
     assert np.abs(R.T @ R - np.eye(5)).max() < 1e-13
+
+
+# ------------------------------------------------------------------ Sec. 5 subgraph centrality
+
+def test_centrality_with_all_pairs_equals_matrix_exponential():
+    """K = N: X exp(Lambda) X^T 1 is exp(A) 1 exactly (scipy's expm, Pade)."""
+    import scipy.linalg as sla
+    g = wl.chung_lu_graph(40, 2.3, 4, 5)
+    rp, col, val = g.csr()
+    A = O.csr_from_arrays(g.n, rp, col, val).toarray()
+    lam, V = np.linalg.eigh(A)
+    live = np.ones(g.n, bool)
+    c = O.subgraph_centrality(V, lam, live)
+    ref = sla.expm(A) @ np.ones(g.n) * np.exp(-lam.max())
+    assert np.abs(c - ref).max() <= 1e-12 * np.abs(ref).max()
+    # a removed node: the principal submatrix on the live nodes, 0 for the removed one
+    live[7] = False
+    Al = A[np.ix_(live, live)]
+    lam2, V2 = np.linalg.eigh(Al)
+    X = np.zeros((g.n, g.n - 1))
+    X[live] = V2
+    c2 = O.subgraph_centrality(X, lam2, live)
+    ref2 = sla.expm(Al) @ np.ones(g.n - 1) * np.exp(-lam2.max())
+    assert c2[7] == 0.0
+    assert np.abs(c2[live] - ref2).max() <= 1e-12 * np.abs(ref2).max()
+
+
+def test_centrality_closed_forms():
+    """Complete graph K_n: 1 is the eigenvector of n - 1, so exp(A) 1 = e^(n-1) 1
+    from the top pair alone.  Star with m leaves: 1 lies in the span of the
+    +-sqrt(m) pairs, and exp(A) 1 = cosh(r) 1 + sinh(r) / r * A 1, r = sqrt(m):
+    hub cosh r + r sinh r, leaves cosh r + sinh(r) / r."""
+    n = 9
+    X = np.full((n, 1), 1 / np.sqrt(n))
+    c = O.subgraph_centrality(X, np.array([n - 1.0]), np.ones(n, bool))
+    assert np.allclose(c, 1.0, rtol=0, atol=1e-14)
+    m = 16
+    r = np.sqrt(m)
+    st, _ = state_from_edges(m + 1, [(0, j) for j in range(1, m + 1)], 2, O.OP_ADJ)
+    assert np.allclose(np.sort(st.lam), [-r, r], atol=1e-12)
+    c = O.subgraph_centrality(st.X, st.lam, np.ones(m + 1, bool)) * np.exp(r)
+    assert abs(c[0] - (np.cosh(r) + r * np.sinh(r))) <= 1e-12 * c[0]
+    assert np.abs(c[1:] - (np.cosh(r) + np.sinh(r) / r)).max() <= 1e-12 * c[0]
+
+
+def test_top_central_order_ties_and_removed_nodes():
+    c = np.array([3.0, 5.0, 5.0, 1.0, 5.0, 0.0, 7.0, -2.0])
+    live = np.array([1, 1, 1, 1, 0, 1, 1, 1], bool)
+    assert O.top_central(c, live, 3).tolist() == [6, 1, 2]
+    assert O.top_central(c, live, 4).tolist() == [6, 1, 2, 0]
+    assert O.top_central(c, live, 7).tolist() == [6, 1, 2, 0, 3, 5, 7]
+    assert O.central_overlap(np.array([6, 1, 2]), np.array([2, 6, 0])) == pytest.approx(2 / 3)
