@@ -8,7 +8,7 @@
  * eigenpairs {(lambda_j, x_j)} of an N x N matrix and an (N+S) x (N+S)
  * perturbation Delta (Eq. adj_update, Sec. 2), estimate the K leading
  * eigenpairs of the updated matrix.  Alg. 2 applies that update once per
- * received Delta: grest_init is Alg. 2's input and initial pairs (line 3),
+ * received Delta: grest_init takes Alg. 2's input and initial pairs,
  * grest_apply_update is one pass of the loop (receive Delta, pad X, build an
  * orthonormal basis Z, solve the projected eigenproblem, lift X = Z F_K), and
  * grest_get_embedding returns (X_K, Lambda_K).
@@ -171,8 +171,14 @@ grest_status grest_config_default(grest_config *cfg, int32_t k);
  * the host: rowptr[n+1] (int64), col[rowptr[n]] (int32, no self loops, each
  * undirected edge present in both rows), val (nullable; positive weights,
  * symmetric).  U0 (n x k row-major, orthonormal columns) and theta0 (k) are
- * the initial leading pairs computed by any direct eigensolver (Alg. 2,
- * line 3); both are required in this build (NULL -> GREST_ERR_UNSUPPORTED).
+ * Alg. 2's initial leading pairs from any eigensolver.  When both are NULL
+ * the library computes them on the device: FP64 block Krylov (blocks of
+ * k + max(8, k/2) columns, full reorthogonalization, Rayleigh-Ritz and
+ * explicit restarts) until every tracked residual ||M x - theta x|| is at
+ * most 1e-11 |theta_1| (GREST_ERR_NUMERIC if 100 restarts do not get there);
+ * graphs of at most 288 nodes are solved densely.  Device memory for this
+ * is taken and released inside grest_init (about n * 600 doubles).  One NULL
+ * and one not -> GREST_ERR_INVALID_ARG.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream).
  */
 grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowptr,
@@ -218,6 +224,25 @@ grest_status grest_get_ritz_values(grest_ctx *ctx, double *ritz, int32_t *m_out)
 
 /* Diagnostics of the last completed step. */
 grest_status grest_get_stats(grest_ctx *ctx, grest_stats *stats);
+
+/*
+ * Sec. 5 downstream task: subgraph centrality approximated from the tracked
+ * pairs, exp(M) 1 ~= X_K exp(Lambda_K) X_K^T 1, returned scaled by
+ * exp(-theta_max) (theta_max the largest tracked value) so that it cannot
+ * overflow; the scaling leaves the ranking unchanged.  For the adjacency
+ * operator this is the paper's measure; for LAP / NLAP it is the same formula
+ * on the tracked (shifted) operator.
+ *   cent:     n_nodes values (NULL: not returned); removed nodes get 0.
+ *   top_ids:  the J most central live node ids (NULL: not returned), ordered by
+ *             value descending, equal values by id ascending (a unique order).
+ *   top_vals: their values (NULL: not returned).
+ * 0 <= J <= min(4096, live nodes), K <= 64, else GREST_ERR_INVALID_ARG.
+ * on_device: 1 = the output pointers are device memory, 0 = host memory.
+ * GREST_ERR_NUMERIC if a value is NaN.  Synchronous; the caller owns every
+ * buffer; the tracked state is not modified.
+ */
+grest_status grest_centrality(grest_ctx *ctx, int32_t J, double *cent, int32_t *top_ids,
+                              double *top_vals, int32_t on_device);
 
 /*
  * Y = M X for the context's current operator M (Sec. 4.3 kinds, principal

@@ -215,6 +215,17 @@ int gram_df(const float* X, int64_t ldx, const float* Yh, const float* Yl, int64
 int lift_df(const float* X, int64_t ldx, const double* S, int k, int64_t n, double* Out, int64_t ldo, cudaStream_t s);
 int sign_normalize_fast(double* X, int64_t ldx, int w, int64_t n, double* part, int64_t* ipart, cudaStream_t s);
 
+// central.cu (Sec. 5 downstream task): c = exp(-theta_max) X_K exp(Lambda_K) X_K^T 1
+// over the live rows (0 for removed nodes) into cent[n]; the live count goes
+// to *n_live_host (pinned) once the stream reaches it.  central_top then
+// writes the J most central ids / values (c descending, id ascending) from
+// the keys central_values left in `work`.  Each returns its launch count.
+int central_max_j();
+size_t central_work_bytes(int64_t n);
+int central_values(const double* X, int64_t ldx, int K, const double* theta, const uint8_t* live, int64_t n,
+                   double* cent, void* work, int64_t* n_live_host, int32_t* err, cudaStream_t s);
+int central_top(int64_t n, int J, int32_t* top_ids, double* top_vals, void* work, cudaStream_t s);
+
 // eig.cu
 // Symmetric eigensolver for H (m x m row-major, ld; overwritten).  Writes the
 // k leading pairs in tracking order: theta[k], F (m x k row-major, ldf), all m

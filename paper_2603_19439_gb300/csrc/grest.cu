@@ -78,6 +78,12 @@ struct grest_ctx {
   size_t gemm_img_cap = 0;
   double* eigwork = nullptr;
   int32_t* err = nullptr;
+  // grest_centrality scratch (allocated on first use)
+  void* cent_work = nullptr;
+  size_t cent_work_cap = 0;
+  double* cent_buf = nullptr;   // n_cap
+  int32_t* top_id_buf = nullptr;
+  double* top_val_buf = nullptr;
   // batch staging
   int32_t *b_iu = nullptr, *b_iv = nullptr, *b_du = nullptr, *b_dv = nullptr, *b_dn = nullptr;
   double* b_w = nullptr;
@@ -143,7 +149,7 @@ void free_ctx(grest_ctx* c) {
                   c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
                   c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
-                  c->ipart, c->piv, c->gemm_img, c->dmax_old, c->XZ, c->gw.edel, c->eigwork, c->err, c->resn, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+                  c->ipart, c->piv, c->gemm_img, c->dmax_old, c->XZ, c->gw.edel, c->eigwork, c->err, c->resn, c->cent_work, c->cent_buf, c->top_id_buf, c->top_val_buf, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_info) cudaFreeHost(c->h_info);
@@ -722,6 +728,298 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   return GREST_OK;
 }
 
+// Ynew = a MY + b Y + g Yold over n x w (shared ld; Yold may be Ynew): one
+// step of the scaled Chebyshev recurrence
+__global__ void k_cheb_step(const double* __restrict__ MY, const double* __restrict__ Y, const double* Yold,
+                            double* Ynew, int64_t ld, int w, int64_t n, double a, double b, double g) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = (e / w) * ld + (e % w);
+    Ynew[o] = fma(a, MY[o], fma(b, Y[o], Yold ? g * Yold[o] : 0.0));
+  }
+}
+
+// H[r0 + i][c0 + j] = A[i][j] (+ B[i][j]) for an a x w block (ld w)
+__global__ void k_put_block(double* __restrict__ H, int64_t ldh, int64_t c0, const double* __restrict__ A,
+                            const double* __restrict__ B, int a, int w) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)a * w) return;
+  const int64_t i = e / w, j = e % w;
+  H[i * ldh + c0 + j] = B ? A[e] + B[e] : A[e];
+}
+
+// H (m x m): the strict lower triangle from the upper one
+__global__ void k_mirror_upper(double* __restrict__ H, int64_t ld, int m) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * m) return;
+  const int64_t r = e / m, cc = e % m;
+  if (r > cc) H[r * ld + cc] = H[cc * ld + r];
+}
+
+// Alg. 2's initial pairs on the device: the K leading pairs of M^(0) (FP64).
+// Two kinds of round, each ending in Rayleigh-Ritz for b = K + max(8, K/2)
+// vectors X and the residuals of the K tracked ones:
+//  * block Krylov: the basis V = [V_0 .. V_s] (n x m, m = (s+1) b <= 512,
+//    V_0 = X) grows by V_{j+1} = orth(M V_j), two classical Gram-Schmidt
+//    passes against all of V and CholQR2; H = V^T M V is assembled from the
+//    Gram-Schmidt coefficients (block column j of H is V^T M V_j).  A block
+//    Gram-Schmidt leaves rank deficient (converged pairs, an invariant
+//    subspace) has the missing columns replaced by Gaussian ones.
+//  * Chebyshev-filtered subspace iteration (Zhou and Saad, J. Comput. Phys.
+//    2007, scaled three-term recurrence): once the block is within 1e-3 of
+//    converging, the leading pairs that already meet the tolerance are
+//    locked, and the other columns are multiplied by a Chebyshev polynomial
+//    that damps [lower bound, cut] (ADJ: a polynomial in M^2 on
+//    [0, theta_b^2], as both ends of the spectrum are wanted; LAP / NLAP: in
+//    M on [0, theta_b]) with the locked vectors projected out after every
+//    product, then re-orthonormalized.  Its cost is mostly SpMMs, which on
+//    this hardware are far cheaper than the FP64 Gram-Schmidt of a Krylov
+//    round; a round that does not halve the residual goes back to Krylov.
+// Stops when every tracked residual ||M x - theta x|| is at most
+// tol |theta_1|.  Graphs of at most 288 nodes take the dense route: H = M.
+grest_status initial_pairs_device(grest_ctx* c, int max_rounds, double tol) {
+  cudaStream_t s = c->stream;
+  const int K = c->K, op = c->cfg.op;
+  const int64_t n = c->g.n;
+  if (n < K) return GREST_ERR_INVALID_ARG;
+  const bool dense = n <= 288;
+  int b = std::min<int64_t>(K + std::max(8, K / 2), std::min<int64_t>(c->cmax, n));
+  int sdeg = dense ? 0 : (int)std::min<int64_t>(16, std::min<int64_t>(512 / b - 1, n / b - 1));
+  if (!dense && sdeg < 1) return GREST_ERR_INVALID_ARG;
+  const int m = dense ? (int)n : (sdeg + 1) * b;
+  double *V = nullptr, *W = nullptr, *MX = nullptr, *Hc = nullptr, *C1 = nullptr, *C2 = nullptr, *F = nullptr,
+         *rz = nullptr, *th = nullptr, *ew = nullptr;
+  CK(dalloc(&V, n * (int64_t)m)); CK(dalloc(&W, n * (int64_t)b)); CK(dalloc(&MX, n * (int64_t)b));
+  CK(dalloc(&Hc, (int64_t)m * m)); CK(dalloc(&C1, (int64_t)m * b)); CK(dalloc(&C2, (int64_t)m * b));
+  CK(dalloc(&F, (int64_t)m * b)); CK(dalloc(&rz, m)); CK(dalloc(&th, b)); CK(dalloc(&ew, eig_work_doubles(m)));
+  struct Free {
+    double** p[10];
+    ~Free() { for (auto q : p) { cudaFree(*q); *q = nullptr; } }
+  } fr{{&V, &W, &MX, &Hc, &C1, &C2, &F, &rz, &th, &ew}};
+  auto sym_eig = [&](int mm, int k) {
+    int p = prof_begin(c);
+    c->launches += sym_eig_select(Hc, mm, mm, k, op, th, F, k, rz, c->info + 56, ew, false, s);
+    prof_end(c, p, 3, 4.0 * mm * mm * mm / 3.0 + 2.0 * mm * mm * k);
+  };
+  auto finish = [&](const double* X, int64_t ldx) -> grest_status {
+    CK(cudaMemcpy2DAsync(c->U, sizeof(double) * c->ldu, X, sizeof(double) * ldx, sizeof(double) * K, n,
+                         cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->theta, th, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+    c->launches += sign_normalize_fast(c->U, c->ldu, K, n, c->part, c->ipart, s);
+    CK(cudaGetLastError());
+    {
+      const grest_status rb = read_back(c, 0);
+      if (rb != GREST_OK) return rb;
+    }
+    return *c->h_err ? map_dev_err(*c->h_err) : GREST_OK;
+  };
+  if (dense) {
+    // H = M I, all n pairs of the dense operator; the K leading ones are X
+    k_fill_identity<double><<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(V, n, (int)n);
+    spmm(c, (const double*)V, n, Hc, n, (int)n, 0, n, 0);
+    symmetrize(Hc, n, (int)n, s);
+    c->launches += 2;
+    b = std::min<int>(b, (int)n);
+    sym_eig((int)n, K);
+    return finish(F, K);
+  }
+  // |M| <= ub: Gershgorin (ADJ: d_max; LAP: alpha = 2 d_max; NLAP: 2), the
+  // reference for the rank test of a new block
+  CK(cudaMemcpyAsync(c->h_info, c->g.dmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double dmax = c->h_info[0];
+  const double ub = std::max(op == GREST_OP_NLAP ? 2.0 : (op == GREST_OP_LAP ? 2.0 * dmax : dmax), 1e-300);
+  uint64_t draws = 0;  // Philox stream index of the Gaussian blocks
+  // columns [col0, col0 + w) of V: orthonormal Gaussian columns orthogonal to V's columns before col0
+  auto random_cols = [&](int col0, int w) -> grest_status {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      gaussian_omega(W, b, n, w, c->cfg.seed ^ 0x494e495449414cull, draws++, s);
+      c->launches += 1;
+      for (int pass = 0; pass < 2 && col0 > 0; ++pass) {
+        gram(c, (const double*)V, m, col0, (const double*)W, b, w, n, C1, w, false);
+        gemm(c, n, col0, w, -1.0, (const double*)V, m, C1, w, 1.0, (const double*)W, b, W, b);
+      }
+      int r = 0;
+      grest_status st = cholqr_pass(c, (const double*)W, b, w, n, 1e-10, 0.0, nullptr, V + col0, m, 0, true, &r);
+      if (st != GREST_OK) return st;
+#ifdef GREST_TRACE_INIT
+      fprintf(stderr, "init random columns %d + %d attempt %d rank %d\n", col0, w, attempt, r);
+#endif
+      if (r < w) continue;
+      st = cholqr_pass(c, (const double*)(V + col0), m, w, n, 1e-14, 0.0, nullptr, W, b, 4, false, &r);
+      if (st != GREST_OK) return st;
+      copy_cols_f64(W, b, V + col0, m, n, w, s);
+      c->launches += 1;
+      return GREST_OK;
+    }
+    return GREST_ERR_NUMERIC;
+  };
+  grest_status st = random_cols(0, b);
+  if (st != GREST_OK) return st;
+  bool have_mx = false;  // MX = M V_0 from the previous round's residual check
+  bool krylov = true;
+  double prev = HUGE_VAL;
+  int nc = 0;            // locked leading pairs (Chebyshev rounds)
+  std::vector<double> hres(K), hth(b);
+  // Chebyshev rounds work in V_0 with V_1 .. V_4 as scratch (needs s >= 4)
+  const bool cheb_ok = sdeg >= 4;
+  const unsigned gbk = (unsigned)std::min<int64_t>((n * b + 255) / 256, 152 * 32);
+  auto deflate = [&](double* Y, int w) {  // Y -= X_L (X_L^T Y), X_L = V_0[:, :nc]
+    if (nc == 0) return;
+    gram(c, (const double*)V, m, nc, (const double*)Y, m, w, n, C1, w, false);
+    gemm(c, n, nc, w, -1.0, (const double*)V, m, C1, w, 1.0, (const double*)Y, m, Y, m);
+  };
+  for (int round = 0; round < max_rounds; ++round) {
+    if (krylov) {
+      for (int j = 0; j <= sdeg; ++j) {
+        double* Vj = V + (int64_t)j * b;
+        const int a = (j + 1) * b;  // columns of V so far
+        if (j == 0 && have_mx) {
+          copy_cols_f64(MX, b, W, b, n, b, s);
+          c->launches += 1;
+        } else {
+          spmm(c, (const double*)Vj, m, W, b, b, 0, n, 0);
+        }
+        // block column j of H = V^T M V_j: first Gram-Schmidt pass
+        gram(c, (const double*)V, m, a, (const double*)W, b, b, n, C1, b, false);
+        if (j == sdeg) {
+          k_put_block<<<(unsigned)((a * b + 255) / 256), 256, 0, s>>>(Hc, m, (int64_t)j * b, C1, nullptr, a, b);
+          c->launches += 1;
+          break;
+        }
+        gemm(c, n, a, b, -1.0, (const double*)V, m, C1, b, 1.0, (const double*)W, b, W, b);
+        gram(c, (const double*)V, m, a, (const double*)W, b, b, n, C2, b, false);
+        gemm(c, n, a, b, -1.0, (const double*)V, m, C2, b, 1.0, (const double*)W, b, W, b);
+        k_put_block<<<(unsigned)((a * b + 255) / 256), 256, 0, s>>>(Hc, m, (int64_t)j * b, C1, C2, a, b);
+        c->launches += 1;
+        // V_{j+1} = CholQR2(W).  Directions left at the rounding level of |M|
+        // (pairs that have converged, or an invariant subspace reached) are
+        // replaced by Gaussian columns orthogonal to everything before them.
+        int r = 0;
+        double* Vn = Vj + b;
+        st = cholqr_pass(c, (const double*)W, b, b, n, 1e-13, ub, nullptr, Vn, m, 0, true, &r);
+        if (st != GREST_OK) return st;
+        if (r > 0) {
+          st = cholqr_pass(c, (const double*)Vn, m, r, n, 1e-14, 0.0, nullptr, W, b, 4, false, &r);
+          if (st != GREST_OK) return st;
+          copy_cols_f64(W, b, Vn, m, n, r, s);
+          c->launches += 1;
+        }
+        if (r < b) {
+          st = random_cols((j + 1) * b + r, b - r);
+          if (st != GREST_OK) return st;
+        }
+      }
+      // Rayleigh-Ritz in span(V): the b leading pairs, X = V F
+      k_mirror_upper<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, s>>>(Hc, m, m);
+      c->launches += 1;
+      sym_eig(m, b);
+      gemm(c, n, m, b, 1.0, (const double*)V, m, F, b, 0.0, (const double*)nullptr, 0, W, b);
+    } else {
+      // filter the active columns V_0[:, nc:] in place (t = M^2 for ADJ, M otherwise)
+      const int a = b - nc;
+      double* Xa = V + nc;
+      const double cut = op == GREST_OP_ADJ ? std::fabs(hth[b - 1]) : hth[b - 1];
+      const double a0 = 0.0;  // M^2 >= 0; T = alpha I - L >= 0; T_n >= 0
+      const double tb = op == GREST_OP_ADJ ? ub * ub : ub;
+      double a1 = op == GREST_OP_ADJ ? cut * cut : cut;
+      // a cut at the spectral bound (a multiple top eigenvalue) leaves no room above it
+      if (!(tb - a1 > 1e-3 * (tb - a0))) a1 = a0 + 0.5 * (tb - a0);
+      if (!(a1 > a0) || !(tb > a1)) return GREST_ERR_NUMERIC;
+      const double c0 = 0.5 * (a0 + a1), e0 = 0.5 * (a1 - a0);
+      const double sigma1 = e0 / (tb - c0);
+      // degree: the largest active pair gains at most 1e6 over the cut, so the
+      // filtered block keeps a condition number CholQR2 orthonormalizes to O(u)
+      const double t1 = op == GREST_OP_ADJ ? hth[nc] * hth[nc] : hth[nc];
+      const double z1 = std::max((t1 - c0) / e0, 1.0);
+      int degree = 1;
+      for (double tm = 1.0, tk = z1; degree < 32;) {
+        const double tn = 2.0 * z1 * tk - tm;
+        if (!(tn <= 1e6)) break;
+        tm = tk;
+        tk = tn;
+        ++degree;
+      }
+      double* P0 = V + 1 * (int64_t)b;  // Y_{k-1}
+      double* P1 = V + 2 * (int64_t)b;  // Y_k
+      double* Tb = V + 3 * (int64_t)b;  // T Y_k
+      double* T2 = V + 4 * (int64_t)b;  // M Y_k (ADJ)
+      auto apply_t = [&](const double* in, double* out) {
+        if (op == GREST_OP_ADJ) {
+          spmm(c, in, m, T2, m, a, 0, n, 0);
+          deflate(T2, a);
+          spmm(c, (const double*)T2, m, out, m, a, 0, n, 0);
+        } else {
+          spmm(c, in, m, out, m, a, 0, n, 0);
+        }
+        deflate(out, a);
+      };
+      copy_cols_f64(Xa, m, P0, m, n, a, s);
+      apply_t(P0, Tb);
+      k_cheb_step<<<gbk, 256, 0, s>>>(Tb, P0, nullptr, P1, m, a, n, sigma1 / e0, -c0 * sigma1 / e0, 0.0);
+      c->launches += 2;
+      double sigma = sigma1;
+      for (int k = 2; k <= degree; ++k) {
+        const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+        apply_t(P1, Tb);
+        k_cheb_step<<<gbk, 256, 0, s>>>(Tb, P1, P0, P0, m, a, n, 2.0 * sigma_new / e0, -2.0 * sigma_new * c0 / e0,
+                                        -sigma * sigma_new);
+        c->launches += 1;
+        std::swap(P0, P1);
+        sigma = sigma_new;
+      }
+      // P1 = filtered block: project out X_L twice, CholQR2 into V_0[:, nc:]
+      deflate(P1, a);
+      deflate(P1, a);
+      int r = 0;
+      st = cholqr_pass(c, (const double*)P1, m, a, n, 1e-14, 0.0, nullptr, Xa, m, 0, true, &r);
+      if (st != GREST_OK) return st;
+      if (r < a) {  // the filter collapsed some columns: Gaussian ones take their place
+        st = random_cols(nc + r, a - r);
+        if (st != GREST_OK) return st;
+      }
+      st = cholqr_pass(c, (const double*)Xa, m, a, n, 1e-14, 0.0, nullptr, P0, m, 4, false, &r);
+      if (st != GREST_OK) return st;
+      copy_cols_f64(P0, m, Xa, m, n, a, s);
+      // Rayleigh-Ritz in span(V_0)
+      spmm(c, (const double*)V, m, MX, b, b, 0, n, 0);
+      gram(c, (const double*)V, m, b, (const double*)MX, b, b, n, Hc, b, false);
+      symmetrize(Hc, b, b, s);
+      c->launches += 2;
+      sym_eig(b, b);
+      gemm(c, n, b, b, 1.0, (const double*)V, m, F, b, 0.0, (const double*)nullptr, 0, W, b);
+    }
+    spmm(c, (const double*)W, b, MX, b, b, 0, n, 0);
+    residual_norms(MX, W, b, K, th, n, c->part, c->resn, s);
+    c->launches += 1;
+    CK(cudaMemcpyAsync(hres.data(), c->resn, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hth.data(), th, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    {
+      const grest_status rb = read_back(c, 0);
+      if (rb != GREST_OK) return rb;
+    }
+    if (*c->h_err) return map_dev_err(*c->h_err);
+    const double scale = std::max(std::fabs(hth[0]), 1e-300);
+    double rmax = 0.0;
+    for (int j = 0; j < K; ++j) rmax = std::max(rmax, hres[j]);
+#ifdef GREST_TRACE_INIT
+    fprintf(stderr, "init round %d %s m %d nc %d rmax %.3e theta %.6f .. %.6f\n", round,
+            krylov ? "krylov" : "chebyshev", m, nc, rmax / scale, hth[0], hth[K - 1]);
+#endif
+    if (!(rmax == rmax)) return GREST_ERR_NUMERIC;
+    if (rmax <= tol * scale) return finish(W, b);
+    // next round starts from V_0 = X (orthonormal: V and F are), M V_0 = MX
+    copy_cols_f64(W, b, V, m, n, b, s);
+    c->launches += 1;
+    have_mx = true;
+    krylov = !cheb_ok || rmax > 1e-3 * scale || rmax > 0.5 * prev;
+    prev = rmax;
+    nc = 0;
+    if (!krylov)
+      while (nc < K && hres[nc] <= tol * scale) ++nc;
+  }
+  return GREST_ERR_NUMERIC;
+}
+
 grest_status run_checks(grest_ctx* c, int64_t n) {
   // M U, residual norms, orthonormality and Galerkin residual, in FP64
   cudaStream_t s = c->stream;
@@ -800,7 +1098,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   if ((cfg->projection == GREST_PROJ_LOWRANK || cfg->w_block == GREST_WB_DELTA) && cfg->op == GREST_OP_NLAP)
     return GREST_ERR_UNSUPPORTED;
   if (cfg->projection == GREST_PROJ_LOWRANK && cfg->precision == GREST_MIXED) return GREST_ERR_UNSUPPORTED;
-  if (!U0 || !theta0) return GREST_ERR_UNSUPPORTED;
+  if ((U0 == nullptr) != (theta0 == nullptr)) return GREST_ERR_INVALID_ARG;
   const int64_t nnz = rowptr[n];
   for (int64_t i = 0; i < n; ++i)
     if (rowptr[i + 1] < rowptr[i]) return GREST_ERR_INVALID_ARG;
@@ -924,8 +1222,8 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(cudaMemsetAsync(g.live, 1, n, s));
   IK(cudaMemcpyAsync(g.arena_top, &total, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   IK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
-  // initial pairs
-  {
+  // initial pairs given by the caller (else computed on the device below)
+  if (U0) {
     std::vector<double> hu((size_t)n * c->ldu, 0.0);
     for (int64_t i = 0; i < n; ++i)
       for (int j = 0; j < c->K; ++j) hu[(size_t)i * c->ldu + j] = U0[(size_t)i * c->K + j];
@@ -944,6 +1242,13 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   c->stats.n_nodes = n;
   c->stats.nnz = nnz;
   c->nnz = nnz;
+  if (!U0) {
+    const grest_status ist = initial_pairs_device(c, 100, 1e-11);
+    if (ist != GREST_OK) {
+      free_ctx(c);
+      return ist;
+    }
+  }
   *out = c;
   return GREST_OK;
 }
@@ -1122,6 +1427,45 @@ grest_status grest_apply_operator(grest_ctx* c, const double* X, int64_t ldx, do
   spmm(c, X, ldx, Y, ldy, w, 0, c->g.n, 0);
   CK(cudaGetLastError());
   return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+grest_status grest_centrality(grest_ctx* c, int32_t J, double* cent, int32_t* top_ids, double* top_vals,
+                              int32_t on_device) {
+  if (!c || J < 0 || J > central_max_j() || c->K > 64) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  cudaStream_t s = c->stream;
+  const int64_t n = c->g.n;
+  const size_t need = central_work_bytes(c->g.n_cap);
+  if (need > c->cent_work_cap) {
+    cudaFree(c->cent_work);
+    c->cent_work = nullptr;
+    c->cent_work_cap = 0;
+    CK(cudaMalloc(&c->cent_work, need));
+    c->cent_work_cap = need;
+  }
+  if (!c->cent_buf) CK(dalloc(&c->cent_buf, c->g.n_cap));
+  if (!c->top_id_buf) CK(dalloc(&c->top_id_buf, central_max_j()));
+  if (!c->top_val_buf) CK(dalloc(&c->top_val_buf, central_max_j()));
+  double* cdev = (on_device && cent) ? cent : c->cent_buf;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
+  central_values(c->U, c->ldu, c->K, c->theta, c->g.live, n, cdev, c->cent_work, c->h_scal, c->err, s);
+  CK(cudaMemcpyAsync(c->h_err, c->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  if (*c->h_err) return map_dev_err(*c->h_err);
+  if ((int64_t)J > c->h_scal[0]) return GREST_ERR_INVALID_ARG;
+  if (cent && !on_device) CK(cudaMemcpyAsync(cent, cdev, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (J > 0 && (top_ids || top_vals)) {
+    int32_t* ids = on_device && top_ids ? top_ids : c->top_id_buf;
+    double* vals = on_device && top_vals ? top_vals : c->top_val_buf;
+    central_top(n, J, ids, vals, c->cent_work, s);
+    CK(cudaGetLastError());
+    if (!on_device) {
+      if (top_ids) CK(cudaMemcpyAsync(top_ids, ids, sizeof(int32_t) * J, cudaMemcpyDeviceToHost, s));
+      if (top_vals) CK(cudaMemcpyAsync(top_vals, vals, sizeof(double) * J, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  return from_cuda(cudaStreamSynchronize(s));
 }
 
 grest_status grest_gram(grest_ctx* c, const double* X, int64_t ldx, int32_t a, const double* Y, int64_t ldy,

@@ -70,7 +70,8 @@ class Stats(C.Structure):
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
            "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
-           "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_destroy", "grest_status_str"]
+           "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_destroy",
+           "grest_status_str"]
 
 _lib = None
 
@@ -97,6 +98,7 @@ def load_library(path=None):
     lib.grest_gram.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
     lib.grest_gram_f32.argtypes = [vp, vp, i64, i32, vp, i64, i32, i64, vp, i64]
     lib.grest_gemm_f32.argtypes = [vp, i64, i32, i32, C.c_double, vp, i64, vp, i64, C.c_double, vp, i64, vp, i64]
+    lib.grest_centrality.argtypes = [vp, i32, vp, vp, vp, i32]
     lib.grest_gram_noalloc.argtypes = [vp, i64, i32, vp, i64, i32, i64, vp, i64, vp]
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
@@ -252,6 +254,28 @@ class Tracker:
                                      B.data_ptr(), B.stride(0), beta, cin, ldc, Out.data_ptr(), Out.stride(0))
         if st != 0:
             raise GrestError(st, "grest_gemm_f32")
+
+    def centrality(self, J=0, values=True):
+        """Sec. 5 subgraph centrality exp(-theta_max) X_K exp(Lambda_K) X_K^T 1
+        (host arrays): returns (c or None, top-J ids, top-J values)."""
+        cn = C.c_int64()
+        st = self.lib.grest_get_embedding(self.h, None, None, None, C.byref(cn), 0)
+        if st != 0:
+            raise GrestError(st, "grest_get_embedding")
+        c = np.empty(cn.value) if values else None
+        ids = np.empty(max(int(J), 0), np.int32)
+        vals = np.empty(max(int(J), 0))
+        st = self.lib.grest_centrality(self.h, int(J), _ptr(c), _ptr(ids) if J > 0 else None,
+                                       _ptr(vals) if J > 0 else None, 0)
+        if st != 0:
+            raise GrestError(st, "grest_centrality")
+        return c, ids, vals
+
+    def centrality_device(self, J, cent=None, ids=None, vals=None):
+        """The same into torch CUDA tensors (cent float64 n, ids int32 J, vals float64 J; each may be None)."""
+        st = self.lib.grest_centrality(self.h, int(J), _ptr(cent), _ptr(ids), _ptr(vals), 1)
+        if st != 0:
+            raise GrestError(st, "grest_centrality")
 
     def sync(self):
         st = self.lib.grest_sync(self.h)
