@@ -51,7 +51,7 @@ typedef enum {
   GREST_ERR_UNSUPPORTED = 8      /* option not implemented in this build */
 } grest_status;
 
-/* Operator whose leading eigenpairs are tracked (Sec. 2 and Sec. 4.3). */
+/* Operator whose leading eigenpairs are tracked (Sec. 2 and Sec. 4.2). */
 enum {
   GREST_OP_ADJ = 0,  /* adjacency A; pairs ordered by |lambda| descending (Sec. 2) */
   GREST_OP_LAP = 1,  /* T = alpha I - (D - A), alpha = 2 d_max of the current graph */
@@ -245,7 +245,7 @@ grest_status grest_centrality(grest_ctx *ctx, int32_t J, double *cent, int32_t *
                               double *top_vals, int32_t on_device);
 
 /*
- * Y = M X for the context's current operator M (Sec. 4.3 kinds, principal
+ * Y = M X for the context's current operator M (Sec. 4.2 kinds, principal
  * submatrix on live nodes).  X and Y are device arrays of n_nodes rows,
  * row-major with leading dimensions ldx, ldy (>= w), w <= 288 columns.  This
  * is the library's CSR SpMM, exposed for residual checks and measurement.

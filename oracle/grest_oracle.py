@@ -12,7 +12,7 @@ order and notation, in float64 with NumPy/SciPy library primitives
 (sparse products, LAPACK QR and symmetric eigensolver):
 
   Sec. 2, Eq. (adj_update)    A_hat = pad(A) + Delta, Delta = [[K, G], [G^T, C]]
-  Sec. 4.3                    operator M: adjacency A, shifted Laplacian
+  Sec. 4.2                    operator M: adjacency A, shifted Laplacian
                               T = alpha I - (D - A) with alpha = 2 d_max, or
                               shifted normalized Laplacian T_n = I + D^-1/2 A D^-1/2
   Alg. 2 (pad)                X_bar = [X; 0]

@@ -1,5 +1,6 @@
-// Downstream task of Sec. 5: approximate subgraph centrality from the tracked
-// pairs, exp(M) 1 ~= X_K exp(Lambda_K) X_K^T 1, and the J most central nodes.
+// Downstream task of Sec. 5, with the matrix-function tracking of Sec. 4.1:
+// approximate subgraph centrality from the tracked pairs,
+// exp(M) 1 ~= X_K exp(Lambda_K) X_K^T 1, and the J most central nodes.
 //
 //   s = X_K^T 1                      column sums over live rows (fixed-order reduction)
 //   w_j = exp(theta_j - theta_max) s_j

@@ -68,7 +68,7 @@ struct Csr {
   double* dmax = nullptr;        // device scalar, max degree over live nodes
 };
 
-// Operator description for the SpMM epilogue (Sec. 4.3).
+// Operator description for the SpMM epilogue (Sec. 4.2).
 struct OpParams {
   int op;                  // GREST_OP_*
   const double* deg;       // degree (LAP)

@@ -56,7 +56,7 @@ __device__ __forceinline__ void split(double v, float& h, float& l) {
 }
 
 // ---------------------------------------------------------------- M U
-// Y (hi, lo) = M X for FP32 X (n x w, w <= 64), the operator of Sec. 4.3:
+// Y (hi, lo) = M X for FP32 X (n x w, w <= 64), the operator of Sec. 4.2:
 //   ADJ   y_r = sum_j a_rj x_j
 //   LAP   y_r = (alpha - d_r) x_r + sum_j a_rj x_j
 //   NLAP  y_r = x_r + s_r sum_j a_rj s_j x_j,  s = d^-1/2

@@ -1,5 +1,5 @@
 // CSR SpMM Y = M X over tall-skinny row-major blocks, with the operator of
-// Sec. 4.3 applied in the epilogue:
+// Sec. 4.2 applied in the epilogue:
 //   ADJ   y_r = sum_j a_rj x_j
 //   LAP   y_r = (alpha - d_r) x_r + sum_j a_rj x_j,   alpha = 2 d_max
 //   NLAP  y_r = x_r + s_r sum_j a_rj s_j x_j,          s = d^-1/2
@@ -79,7 +79,7 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo,
   return lo;
 }
 
-// diagonal coefficient of row r (Sec. 4.3); the sum term is scaled by `scale`
+// diagonal coefficient of row r (Sec. 4.2); the sum term is scaled by `scale`
 __device__ __forceinline__ void diag_terms(const OpParams& op, int64_t r, double& dcoef, double& scale) {
   dcoef = 0.0;
   scale = 1.0;

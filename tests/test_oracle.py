@@ -161,14 +161,14 @@ def test_closed_form_adjacency_spectra():
 
 def test_closed_form_shifted_laplacians():
     n = 8
-    # T = alpha I - L, alpha = 2 d_max (Sec. 4.3); L(K_n) = {0, n x (n-1)}
+    # T = alpha I - L, alpha = 2 d_max (Sec. 4.2); L(K_n) = {0, n x (n-1)}
     al = 2 * (n - 1)
     assert np.allclose(spectrum(n, complete(n), O.OP_LAP), np.sort([al] + [al - n] * (n - 1)))
     # cycle: L eigenvalues 2 - 2cos(2 pi j/n), d_max = 2, alpha = 4
     assert np.allclose(spectrum(n, cycle(n), O.OP_LAP), np.sort(4 - (2 - 2 * np.cos(2 * np.pi * np.arange(n) / n))))
     # T_n = 2I - L_n with L_n(K_n) = {0, n/(n-1) x (n-1)}
     assert np.allclose(spectrum(n, complete(n), O.OP_NLAP), np.sort([2.0] + [2 - n / (n - 1)] * (n - 1)))
-    # Gershgorin bounds of Sec. 4.3: T in [0, 2 d_max], T_n in [0, 2]
+    # Gershgorin bounds of Sec. 4.2: T in [0, 2 d_max], T_n in [0, 2]
     g, _ = wl.sbm_graph(60, 3, 0.3, 0.05, 5)
     rp, col, _ = g.csr()
     A = O.csr_from_arrays(60, rp, col)
