@@ -434,6 +434,55 @@ def run_grest(args):
     return 0
 
 
+def run_kernels(args):
+    """--kernels: CUDA-event times of the mixed path's tensor-core Gram and GEMM
+    entry points (grest_gram_f32, grest_gemm_f32) on n x w FP32 blocks of the
+    widths one 1M-node update uses; one JSON line (not the bench contract's)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_19439_gb300 import grest as G
+    from paper_2603_19439_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    g, _ = wl.sbm_graph(200, 2, 0.1, 0.02, 71)
+    rp, col, _ = g.csr()
+    X0 = np.linalg.qr(np.random.default_rng(0).standard_normal((200, 4)))[0]
+    tr = G.Tracker(g.n, rp, col, None, X0, np.ones(4), 4)
+    n, reps, out = args.nodes, 10, {"gram": [], "gemm": []}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for a, b, sym in [(32, 32, False), (32, 232, False), (200, 200, True), (232, 232, True), (164, 164, False)]:
+        X = torch.randn((n, a), dtype=torch.float32, device="cuda")
+        Y = X if sym else torch.randn((n, b), dtype=torch.float32, device="cuda")
+        C = torch.empty((a, b), dtype=torch.float64, device="cuda")
+        ms = timed(lambda: tr.gram_f32(X, Y, C))
+        by = n * (a + (0 if sym else b)) * 4
+        out["gram"].append({"a": a, "b": b, "X_is_Y": sym, "ms": ms, "GB/s": by / ms / 1e6})
+        del X, Y
+    for a, c, beta in [(32, 232, 1.0), (232, 232, 0.0), (200, 200, 0.0), (232, 132, 0.0), (164, 32, 0.0)]:
+        X = torch.randn((n, a), dtype=torch.float32, device="cuda")
+        B = torch.randn((a, c), dtype=torch.float64, device="cuda")
+        O = torch.randn((n, c), dtype=torch.float32, device="cuda")
+        ms = timed(lambda: tr.gemm_f32(X, B, O, 1.0, beta, O if beta else None))
+        by = n * (a + c * (2 if beta else 1)) * 4
+        out["gemm"].append({"a": a, "c": c, "beta": beta, "ms": ms, "GB/s": by / ms / 1e6})
+        del X, B, O
+    tr.close()
+    print(json.dumps({"kernels": out, "n": n, "reps": reps, "unit": "ms per call (CUDA events, warm)"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,6 +492,8 @@ def main():
     ap.add_argument("--init", choices=["device", "arpack"], default="device",
                     help="initial pairs: the library's device solver, or host ARPACK over the library SpMM")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels", action="store_true",
+                    help="time the tensor-core Gram / GEMM entry points at the step's widths instead")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")
     ap.add_argument("--mixed-only", action="store_true", help="skip the FP64 path")
     ap.add_argument("--nodes", type=int, default=WL["n"],
@@ -453,6 +504,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernels:
+        return run_kernels(args)
     return run_grest(args)
 
 
