@@ -211,3 +211,37 @@ def test_centrality_small_graph_all_nodes():
     with pytest.raises(G.GrestError):
         tr.centrality(g.n + 1)
     tr.close()
+
+
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP, O.OP_NLAP])
+def test_device_initial_pairs_dense_route_small_graph(op):
+    """n <= 288: the device solver takes H = M densely (no Krylov rounds)."""
+    g = wl.chung_lu_graph(250, 2.3, 6, 40 + op)
+    M, ev, V = full_spectrum(g, op)
+    k = 12
+    rp, col, val = g.csr()
+    tr = G.Tracker(g.n, rp, col, val, None, None, k, op=op)
+    check_initial_pairs(tr, M, ev, V, op, k)
+    tr.close()
+
+
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_NLAP])
+def test_tracking_from_device_initial_pairs(op):
+    """Device start, then update steps: the oracle starts from its own dense
+    eigendecomposition of the same graph (the two starts agree to ~1e-12), and
+    the tracked pairs stay within the FP64 tolerances step by step."""
+    g = wl.chung_lu_graph(3000, 2.3, 8, 51 + op)
+    k = 16
+    rp, col, val = g.csr()
+    tr = G.Tracker(g.n, rp, col, val, None, None, k, op=op)
+    st = O.init_state(g.n, rp, col, val, k, op)
+    cfg = O.Config(k=k, op=op, subspace=G.SUB_AUTO, L=100, P=100, seed=0, drop_tol=1e-7)
+    rng = np.random.default_rng(5)
+    gb = g.copy()
+    for t in range(3):
+        b = wl.random_churn_batch(gb, 15, 50, 30, rng)
+        gb.apply(b)
+        tr.update(b)
+        st, info = O.grest_step(st, b, cfg)
+        U.compare(tr, st, info, op, k, f"step {t}")
+    tr.close()
