@@ -328,6 +328,28 @@ grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const d
 /* Release every device buffer of the context. NULL is ignored. */
 void grest_destroy(grest_ctx *ctx);
 
+/*
+ * Batches: many independent graphs, one update each per call.  A batch
+ * refers to existing contexts (it owns none of them; destroy them after the
+ * batch); each context should have its own non-blocking CUDA stream so that
+ * their work overlaps on the device.  grest_batch_apply_updates applies
+ * updates[i] to context i as grest_apply_update would, with n_threads host
+ * threads taking contexts in turn; each context's result is the same as when
+ * it is updated alone (its kernels and their order are unchanged).
+ *   n_graphs >= 1, n_threads >= 1, no context twice -> else GREST_ERR_INVALID_ARG.
+ *   status (nullable): n_graphs per-context results; stats (nullable):
+ *   n_graphs step diagnostics.  Returns GREST_OK, or the first (lowest index)
+ *   failing context's status; a failed context keeps its previous state as
+ *   with grest_apply_update, the others are updated.
+ * The caller must not use the batch's contexts from other threads while a
+ * call is running.
+ */
+typedef struct grest_batch grest_batch;
+grest_status grest_batch_create(int32_t n_graphs, grest_ctx *const *ctxs, int32_t n_threads, grest_batch **out);
+grest_status grest_batch_apply_updates(grest_batch *batch, const grest_update *updates, grest_status *status,
+                                       grest_stats *stats);
+void grest_batch_destroy(grest_batch *batch);
+
 /* Static string naming a status code. */
 const char *grest_status_str(grest_status s);
 

@@ -20,7 +20,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -1522,5 +1524,51 @@ void grest_destroy(grest_ctx* c) {
   cudaStreamSynchronize(c->stream);
   free_ctx(c);
 }
+
+// ---------------------------------------------------------------- batches of contexts
+struct grest_batch {
+  std::vector<grest_ctx*> ctx;
+  int threads = 1;
+};
+
+grest_status grest_batch_create(int32_t n_graphs, grest_ctx* const* ctxs, int32_t n_threads, grest_batch** out) {
+  if (!out || !ctxs || n_graphs < 1 || n_threads < 1) return GREST_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<grest_ctx*> v(ctxs, ctxs + n_graphs);
+  for (grest_ctx* c : v)
+    if (!c) return GREST_ERR_INVALID_ARG;
+  std::vector<grest_ctx*> sorted = v;
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return GREST_ERR_INVALID_ARG;
+  grest_batch* b = new grest_batch;
+  b->ctx = std::move(v);
+  b->threads = std::min<int>(n_threads, n_graphs);
+  *out = b;
+  return GREST_OK;
+}
+
+grest_status grest_batch_apply_updates(grest_batch* b, const grest_update* updates, grest_status* status,
+                                       grest_stats* stats) {
+  if (!b || !updates) return GREST_ERR_INVALID_ARG;
+  const int n = (int)b->ctx.size();
+  std::vector<grest_status> st(n, GREST_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1))
+      st[i] = grest_apply_update(b->ctx[i], &updates[i], stats ? &stats[i] : nullptr);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < b->threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  grest_status first = GREST_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = st[i];
+    if (first == GREST_OK && st[i] != GREST_OK) first = st[i];
+  }
+  return first;
+}
+
+void grest_batch_destroy(grest_batch* b) { delete b; }
 
 }  // extern "C"

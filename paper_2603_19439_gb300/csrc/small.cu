@@ -30,6 +30,8 @@
 #include <cooperative_groups.h>
 #include <float.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -360,6 +362,8 @@ bool cluster_ok(K kern, size_t smem, int C) {
   };
   static Entry cache[128];
   static int n_cache = 0;
+  static std::mutex mu;  // contexts may step concurrently (grest_batch_apply_updates)
+  std::lock_guard<std::mutex> lock(mu);
   for (int i = 0; i < n_cache; ++i)
     if (cache[i].k == (const void*)kern && cache[i].smem == smem && cache[i].C == C) return cache[i].ok;
   bool ok = false;

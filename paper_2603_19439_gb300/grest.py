@@ -70,8 +70,8 @@ class Stats(C.Structure):
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
            "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
-           "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_destroy",
-           "grest_status_str"]
+           "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_batch_create",
+           "grest_batch_apply_updates", "grest_batch_destroy", "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -100,12 +100,16 @@ def load_library(path=None):
     lib.grest_gemm_f32.argtypes = [vp, i64, i32, i32, C.c_double, vp, i64, vp, i64, C.c_double, vp, i64, vp, i64]
     lib.grest_centrality.argtypes = [vp, i32, vp, vp, vp, i32]
     lib.grest_gram_noalloc.argtypes = [vp, i64, i32, vp, i64, i32, i64, vp, i64, vp]
+    lib.grest_batch_create.argtypes = [i32, C.POINTER(vp), i32, C.POINTER(vp)]
+    lib.grest_batch_apply_updates.argtypes = [vp, C.POINTER(Update), C.POINTER(i32), C.POINTER(Stats)]
+    lib.grest_batch_destroy.argtypes = [vp]
+    lib.grest_batch_destroy.restype = None
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
     lib.grest_status_str.argtypes = [i32]
     lib.grest_status_str.restype = C.c_char_p
     for f in EXPORTS[:-2]:
-        if f != "grest_destroy":
+        if f not in ("grest_destroy", "grest_batch_destroy"):
             getattr(lib, f).restype = i32
     if path is None:
         _lib = lib
@@ -146,6 +150,64 @@ def gram_noalloc(X, Y, C, stream=None):
         raise GrestError(st, "grest_gram_noalloc")
 
 
+def _batch_arrays(batch, on_device):
+    if on_device:
+        return [batch.ins_u, batch.ins_v, batch.ins_w, batch.del_u, batch.del_v, batch.del_nodes]
+    return [_host(batch.ins_u, np.int32), _host(batch.ins_v, np.int32), _host(batch.ins_w, np.float64),
+            _host(batch.del_u, np.int32), _host(batch.del_v, np.int32), _host(batch.del_nodes, np.int32)]
+
+
+def _update_struct(batch, arrs, on_device):
+    iu, iv, iw, du, dv, dn = arrs
+    return Update(n_new_nodes=int(batch.n_new), n_ins=int(len(iu)), ins_u=_ptr(iu), ins_v=_ptr(iv), ins_w=_ptr(iw),
+                  n_del=int(len(du)), del_u=_ptr(du), del_v=_ptr(dv),
+                  n_del_nodes=int(len(dn)) if dn is not None else 0, del_nodes=_ptr(dn),
+                  on_device=1 if on_device else 0)
+
+
+class Batch:
+    """Many Trackers updated together (grest_batch_apply_updates): one update
+    each per call, n_threads native host threads, each tracker on its own
+    stream.  The batch owns none of the trackers."""
+
+    def __init__(self, trackers, n_threads=8):
+        self.lib = load_library()
+        self.trackers = list(trackers)
+        arr = (C.c_void_p * len(self.trackers))(*[t.h.value for t in self.trackers])
+        h = C.c_void_p()
+        st = self.lib.grest_batch_create(len(self.trackers), arr, int(n_threads), C.byref(h))
+        if st != 0:
+            raise GrestError(st, "grest_batch_create")
+        self.h = h
+
+    def update(self, batches, on_device=False):
+        """Apply batches[i] to tracker i.  Returns the per-tracker status codes
+        (0 = ok) and step diagnostics; raises when any tracker failed."""
+        n = len(self.trackers)
+        if len(batches) != n:
+            raise ValueError("one update per tracker")
+        keep = [_batch_arrays(b, on_device) for b in batches]
+        ups = (Update * n)(*[_update_struct(b, a, on_device) for b, a in zip(batches, keep)])
+        status = (C.c_int32 * n)()
+        stats = (Stats * n)()
+        st = self.lib.grest_batch_apply_updates(self.h, ups, status, stats)
+        codes = [int(x) for x in status]
+        if st != 0:
+            raise GrestError(st, "grest_batch_apply_updates")
+        return codes, [s.as_dict() for s in stats]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grest_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Tracker:
     """One evolving graph and its K tracked eigenpairs on the GPU."""
 
@@ -172,11 +234,7 @@ class Tracker:
         else:
             arrs = [_host(batch.ins_u, np.int32), _host(batch.ins_v, np.int32), _host(batch.ins_w, np.float64),
                     _host(batch.del_u, np.int32), _host(batch.del_v, np.int32), _host(batch.del_nodes, np.int32)]
-        iu, iv, iw, du, dv, dn = arrs
-        u = Update(n_new_nodes=int(batch.n_new), n_ins=int(len(iu)), ins_u=_ptr(iu), ins_v=_ptr(iv), ins_w=_ptr(iw),
-                   n_del=int(len(du)), del_u=_ptr(du), del_v=_ptr(dv),
-                   n_del_nodes=int(len(dn)) if dn is not None else 0, del_nodes=_ptr(dn),
-                   on_device=1 if on_device else 0)
+        u = _update_struct(batch, arrs, on_device)
         s = Stats()
         st = self.lib.grest_apply_update(self.h, C.byref(u), C.byref(s))
         if st != 0:

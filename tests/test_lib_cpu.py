@@ -80,3 +80,22 @@ def test_init_rejects_unsupported_modes_without_gpu(lib):
     cfg = grest.default_config(1, projection=7)
     assert L.grest_init(ctypes.byref(cfg), 2, rp.ctypes.data, None, None, u0.ctypes.data, t0.ctypes.data, None,
                         ctypes.byref(h)) == 1
+
+
+def test_batch_create_checks_arguments_without_gpu(lib):
+    """grest_batch_create only records the context handles: argument checks
+    (empty, NULL entry, the same context twice) run on the host.  Status 1 is
+    GREST_ERR_INVALID_ARG."""
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    vp = ctypes.c_void_p
+    h = vp()
+    fake = (vp * 3)(0x1000, 0x2000, 0x1000)
+    assert L.grest_batch_create(0, fake, 1, ctypes.byref(h)) == 1
+    assert L.grest_batch_create(3, fake, 2, ctypes.byref(h)) == 1  # duplicate
+    nul = (vp * 2)(0x1000, None)
+    assert L.grest_batch_create(2, nul, 2, ctypes.byref(h)) == 1
+    assert L.grest_batch_create(2, fake, 0, ctypes.byref(h)) == 1
+    assert L.grest_batch_create(2, fake, 4, ctypes.byref(h)) == 0 and h.value
+    assert L.grest_batch_apply_updates(None, None, None, None) == 1
+    L.grest_batch_destroy(h)
