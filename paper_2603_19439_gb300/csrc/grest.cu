@@ -843,9 +843,6 @@ grest_status initial_pairs_device(grest_ctx* c, int max_rounds, double tol) {
       int r = 0;
       grest_status st = cholqr_pass(c, (const double*)W, b, w, n, 1e-10, 0.0, nullptr, V + col0, m, 0, true, &r);
       if (st != GREST_OK) return st;
-#ifdef GREST_TRACE_INIT
-      fprintf(stderr, "init random columns %d + %d attempt %d rank %d\n", col0, w, attempt, r);
-#endif
       if (r < w) continue;
       st = cholqr_pass(c, (const double*)(V + col0), m, w, n, 1e-14, 0.0, nullptr, W, b, 4, false, &r);
       if (st != GREST_OK) return st;
@@ -1003,10 +1000,6 @@ grest_status initial_pairs_device(grest_ctx* c, int max_rounds, double tol) {
     const double scale = std::max(std::fabs(hth[0]), 1e-300);
     double rmax = 0.0;
     for (int j = 0; j < K; ++j) rmax = std::max(rmax, hres[j]);
-#ifdef GREST_TRACE_INIT
-    fprintf(stderr, "init round %d %s m %d nc %d rmax %.3e theta %.6f .. %.6f\n", round,
-            krylov ? "krylov" : "chebyshev", m, nc, rmax / scale, hth[0], hth[K - 1]);
-#endif
     if (!(rmax == rmax)) return GREST_ERR_NUMERIC;
     if (rmax <= tol * scale) return finish(W, b);
     // next round starts from V_0 = X (orthonormal: V and F are), M V_0 = MX
