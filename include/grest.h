@@ -350,6 +350,55 @@ grest_status grest_batch_apply_updates(grest_batch *batch, const grest_update *u
                                        grest_stats *stats);
 void grest_batch_destroy(grest_batch *batch);
 
+/* Device bytes the library allocated for the context (buffers grown by later
+ * batches included); used for admission by a memory budget. */
+grest_status grest_get_device_bytes(grest_ctx *ctx, int64_t *bytes);
+
+/*
+ * Serving many resident graphs.  A server owns n_workers host threads and a
+ * device-memory budget.  Graphs are registered with their host CSR (and
+ * optional initial pairs; NULL = computed on the device as in grest_init);
+ * the server copies them.  A graph becomes resident (its context and its own
+ * non-blocking stream are created) when it first has a request and its
+ * context fits in the budget beside the resident graphs, or when nothing else
+ * is resident; otherwise its requests wait until removals free memory.
+ * Requests (one update each, host arrays, copied at submission) of one graph
+ * run in submission order; different graphs run concurrently, and a request
+ * starts as soon as a worker is free (continuous batching).  Each result is
+ * the same as the update applied alone.
+ *   grest_server_submit returns a ticket; grest_server_wait blocks until the
+ *   ticket's update ran and returns its status, step diagnostics, the time it
+ *   waited after submission and the time it ran (ms; any output may be NULL).
+ *   grest_server_poll sets *done to 1 once the ticket has run (0 before).
+ *   grest_server_remove_graph releases the graph's device memory once its
+ *   pending requests have run; no further submissions are accepted for it.
+ *   grest_server_get_embedding waits until the graph is idle and copies its
+ *   (X_K, Lambda_K, live) to host memory (GREST_ERR_INVALID_ARG when the
+ *   graph is not resident).
+ *   grest_server_resident reports the resident bytes and graph count.
+ * The budget is checked at admission against the context's size then; a
+ * resident graph whose buffers grow for a larger batch keeps its place (its
+ * new size counts toward later admissions).  There is no eviction: a graph
+ * that does not fit waits until removals free memory.
+ * grest_server_destroy stops the workers after their current requests and
+ * releases every context; no other call may be in progress or follow.
+ */
+typedef struct grest_server grest_server;
+grest_status grest_server_create(int32_t n_workers, int64_t hbm_budget_bytes, grest_server **out);
+grest_status grest_server_add_graph(grest_server *server, const grest_config *cfg, int64_t n, const int64_t *rowptr,
+                                    const int32_t *col, const double *val, const double *U0, const double *theta0,
+                                    int32_t *graph_id);
+grest_status grest_server_submit(grest_server *server, int32_t graph_id, const grest_update *update,
+                                 int64_t *ticket);
+grest_status grest_server_wait(grest_server *server, int64_t ticket, grest_status *result, grest_stats *stats,
+                               double *wait_ms, double *run_ms);
+grest_status grest_server_poll(grest_server *server, int64_t ticket, int32_t *done);
+grest_status grest_server_remove_graph(grest_server *server, int32_t graph_id);
+grest_status grest_server_get_embedding(grest_server *server, int32_t graph_id, double *U, double *theta,
+                                        uint8_t *live, int64_t *n_out);
+grest_status grest_server_resident(grest_server *server, int64_t *bytes, int32_t *n_resident);
+void grest_server_destroy(grest_server *server);
+
 /* Static string naming a status code. */
 const char *grest_status_str(grest_status s);
 

@@ -100,6 +100,7 @@ struct grest_ctx {
   int64_t nnz = 0;        // directed nonzeros (exact, read back after each graph update)
   int64_t batch_new_edges = 0;  // inserted edges of the current batch (upper bound for the new-node block)
   int64_t launches = 0;         // kernels enqueued during the current step
+  size_t dev_bytes = 0;         // device bytes allocated for this context (cumulative)
   cudaEvent_t ev[10];
   // GREST_FLAG_PROFILE: event pairs around every launch group of the step
   static constexpr int kProfEvents = 512;
@@ -125,11 +126,20 @@ grest_status from_cuda(cudaError_t e) {
     if (e_ != cudaSuccess) return from_cuda(e_); \
   } while (0)
 
+// device bytes allocated by this host thread (context sizes for admission)
+thread_local size_t t_dev_bytes = 0;
+
+cudaError_t dmalloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) t_dev_bytes += bytes;
+  return e;
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void**)p, sizeof(T) * count);
+  return dmalloc((void**)p, sizeof(T) * count);
 }
 
 grest_status map_dev_err(int32_t e) {
@@ -209,8 +219,8 @@ grest_status ensure_S(grest_ctx* c, int64_t S) {
   int64_t cap = std::max<int64_t>(S, 2 * c->S_cap);
   cudaFree(c->Omv); cudaFree(c->EtMv);
   c->Omv = c->EtMv = nullptr;
-  CK(cudaMalloc(&c->Omv, c->esz * cap * c->ldq));
-  CK(cudaMalloc(&c->EtMv, c->esz * cap * c->ldq));
+  CK(dmalloc((void**)&c->Omv, c->esz * cap * c->ldq));
+  CK(dmalloc((void**)&c->EtMv, c->esz * cap * c->ldq));
   c->S_cap = cap;
   return GREST_OK;
 }
@@ -1079,6 +1089,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
                         const double* val, const double* U0, const double* theta0, void* cuda_stream,
                         grest_ctx** out) {
   if (!cfg || !out || n < 1 || !rowptr || (!col && rowptr[n] > 0)) return GREST_ERR_INVALID_ARG;
+  const size_t bytes0 = t_dev_bytes;
   *out = nullptr;
   if (cfg->k < 1 || cfg->k > 64 || cfg->op < 0 || cfg->op > 2 || cfg->L < 1 || cfg->P < 0 || cfg->L + cfg->P > 256 ||
       cfg->subspace < 0 || cfg->subspace > 3 || !(cfg->drop_tol > 0.0) || cfg->k > n)
@@ -1171,7 +1182,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&w.rowflag, nc + 1)); IK(dalloc(&w.touched, nc)); IK(dalloc(&w.tmp_off, nc + 1));
   IK(dalloc(&w.need, nc + 1)); IK(dalloc(&w.new_len, nc)); IK(dalloc(&w.long_rows, nc));
   IK(dalloc(&w.scalars, 8));
-  IK(cudaMalloc(&w.scan_tmp, scan_temp_bytes(nc + 1)));
+  IK(dmalloc((void**)&w.scan_tmp, scan_temp_bytes(nc + 1)));
   {
     int64_t mb = cfg->max_batch_edges > 0 ? cfg->max_batch_edges : (1 << 20);
     if (ensure_graph_work(c, 2 * mb) != GREST_OK) { free_ctx(c); return GREST_ERR_OOM; }
@@ -1179,10 +1190,10 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   }
   IK(dalloc(&c->U, nc * c->ldu)); IK(dalloc(&c->Un, nc * c->ldu)); IK(dalloc(&c->theta, 64));
   c->esz = cfg->precision == GREST_MIXED ? sizeof(float) : sizeof(double);
-  IK(cudaMalloc(&c->Zv, c->esz * nc * c->ldz)); IK(cudaMalloc(&c->MZv, c->esz * nc * c->ldz));
-  IK(cudaMalloc(&c->V2v, c->esz * nc * c->ldv));
-  IK(cudaMalloc(&c->Yrv, c->esz * nc * c->ldq)); IK(cudaMalloc(&c->Yr2v, c->esz * nc * c->ldq));
-  IK(cudaMalloc(&c->Idv, c->esz * (int64_t)c->q * c->ldq));
+  IK(dmalloc((void**)&c->Zv, c->esz * nc * c->ldz)); IK(dmalloc((void**)&c->MZv, c->esz * nc * c->ldz));
+  IK(dmalloc((void**)&c->V2v, c->esz * nc * c->ldv));
+  IK(dmalloc((void**)&c->Yrv, c->esz * nc * c->ldq)); IK(dmalloc((void**)&c->Yr2v, c->esz * nc * c->ldq));
+  IK(dmalloc((void**)&c->Idv, c->esz * (int64_t)c->q * c->ldq));
   if (cfg->precision == GREST_MIXED) IK(dalloc(&c->U32, nc * c->ldu));
   if (cfg->flags & GREST_FLAG_CHECK) IK(dalloc(&c->Rres, nc * c->ldu));
   const int cm = c->cmax, mm = c->mmax;
@@ -1237,6 +1248,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   c->stats.n_nodes = n;
   c->stats.nnz = nnz;
   c->nnz = nnz;
+  c->dev_bytes = t_dev_bytes - bytes0;  // the solver's temporaries below are released before returning
   if (!U0) {
     const grest_status ist = initial_pairs_device(c, 100, 1e-11);
     if (ist != GREST_OK) {
@@ -1248,7 +1260,13 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   return GREST_OK;
 }
 
-grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats* stats) {
+grest_status grest_get_device_bytes(grest_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return GREST_ERR_INVALID_ARG;
+  *bytes = (int64_t)c->dev_bytes;
+  return GREST_OK;
+}
+
+static grest_status apply_update_impl(grest_ctx* c, const grest_update* u, grest_stats* stats) {
   if (!c || !u) return GREST_ERR_INVALID_ARG;
   if (u->n_new_nodes < 0 || u->n_ins < 0 || u->n_del < 0 || u->n_del_nodes < 0) return GREST_ERR_INVALID_ARG;
   if ((u->n_ins > 0 && (!u->ins_u || !u->ins_v)) || (u->n_del > 0 && (!u->del_u || !u->del_v)) ||
@@ -1369,6 +1387,13 @@ grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats
   return GREST_OK;
 }
 
+grest_status grest_apply_update(grest_ctx* c, const grest_update* u, grest_stats* stats) {
+  const size_t b0 = t_dev_bytes;
+  const grest_status st = apply_update_impl(c, u, stats);
+  if (c) c->dev_bytes += t_dev_bytes - b0;  // buffers grown for this batch
+  return st;
+}
+
 grest_status grest_sync(grest_ctx* c) {
   if (!c) return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
@@ -1435,7 +1460,7 @@ grest_status grest_centrality(grest_ctx* c, int32_t J, double* cent, int32_t* to
     cudaFree(c->cent_work);
     c->cent_work = nullptr;
     c->cent_work_cap = 0;
-    CK(cudaMalloc(&c->cent_work, need));
+    CK(dmalloc((void**)&c->cent_work, need));
     c->cent_work_cap = need;
   }
   if (!c->cent_buf) CK(dalloc(&c->cent_buf, c->g.n_cap));

@@ -71,7 +71,10 @@ class Stats(C.Structure):
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
            "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
            "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_batch_create",
-           "grest_batch_apply_updates", "grest_batch_destroy", "grest_destroy", "grest_status_str"]
+           "grest_batch_apply_updates", "grest_batch_destroy", "grest_get_device_bytes", "grest_server_create",
+           "grest_server_add_graph", "grest_server_submit", "grest_server_wait", "grest_server_poll", "grest_server_remove_graph",
+           "grest_server_get_embedding", "grest_server_resident", "grest_server_destroy", "grest_destroy",
+           "grest_status_str"]
 
 _lib = None
 
@@ -104,12 +107,24 @@ def load_library(path=None):
     lib.grest_batch_apply_updates.argtypes = [vp, C.POINTER(Update), C.POINTER(i32), C.POINTER(Stats)]
     lib.grest_batch_destroy.argtypes = [vp]
     lib.grest_batch_destroy.restype = None
+    lib.grest_get_device_bytes.argtypes = [vp, C.POINTER(i64)]
+    lib.grest_server_create.argtypes = [i32, i64, C.POINTER(vp)]
+    lib.grest_server_add_graph.argtypes = [vp, C.POINTER(Config), i64, vp, vp, vp, vp, vp, C.POINTER(i32)]
+    lib.grest_server_submit.argtypes = [vp, i32, C.POINTER(Update), C.POINTER(i64)]
+    lib.grest_server_wait.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(Stats), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]
+    lib.grest_server_poll.argtypes = [vp, i64, C.POINTER(i32)]
+    lib.grest_server_remove_graph.argtypes = [vp, i32]
+    lib.grest_server_get_embedding.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i64)]
+    lib.grest_server_resident.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
+    lib.grest_server_destroy.argtypes = [vp]
+    lib.grest_server_destroy.restype = None
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
     lib.grest_status_str.argtypes = [i32]
     lib.grest_status_str.restype = C.c_char_p
     for f in EXPORTS[:-2]:
-        if f not in ("grest_destroy", "grest_batch_destroy"):
+        if f not in ("grest_destroy", "grest_batch_destroy", "grest_server_destroy"):
             getattr(lib, f).restype = i32
     if path is None:
         _lib = lib
@@ -199,6 +214,90 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.grest_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over many resident graphs (grest_server_*): native worker
+    threads, one context and stream per admitted graph, admission by a device
+    memory budget, requests of a graph in submission order."""
+
+    def __init__(self, n_workers=8, hbm_budget=1 << 50):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.grest_server_create(int(n_workers), int(hbm_budget), C.byref(h))
+        if st != 0:
+            raise GrestError(st, "grest_server_create")
+        self.h = h
+        self.k = {}
+
+    def add_graph(self, n, rowptr, col, val, k, U0=None, theta0=None, **cfg_fields):
+        cfg = default_config(k, **cfg_fields)
+        keep = [_host(rowptr, np.int64), _host(col, np.int32), _host(val, np.float64), _host(U0, np.float64),
+                _host(theta0, np.float64)]
+        gid = C.c_int32()
+        st = self.lib.grest_server_add_graph(self.h, C.byref(cfg), int(n), *[_ptr(a) for a in keep], C.byref(gid))
+        if st != 0:
+            raise GrestError(st, "grest_server_add_graph")
+        self.k[gid.value] = int(k)
+        return gid.value
+
+    def submit(self, gid, batch):
+        """Queue one update (host arrays, copied); returns a ticket."""
+        arrs = _batch_arrays(batch, False)
+        u = _update_struct(batch, arrs, False)
+        t = C.c_int64()
+        st = self.lib.grest_server_submit(self.h, int(gid), C.byref(u), C.byref(t))
+        if st != 0:
+            raise GrestError(st, "grest_server_submit")
+        return t.value
+
+    def wait(self, ticket):
+        """(status code, step diagnostics, ms waited, ms run) of a ticket."""
+        res, s, w, r = C.c_int32(), Stats(), C.c_double(), C.c_double()
+        st = self.lib.grest_server_wait(self.h, int(ticket), C.byref(res), C.byref(s), C.byref(w), C.byref(r))
+        if st != 0:
+            raise GrestError(st, "grest_server_wait")
+        return res.value, s.as_dict(), w.value, r.value
+
+    def done(self, ticket):
+        d = C.c_int32()
+        st = self.lib.grest_server_poll(self.h, int(ticket), C.byref(d))
+        if st != 0:
+            raise GrestError(st, "grest_server_poll")
+        return bool(d.value)
+
+    def remove_graph(self, gid):
+        st = self.lib.grest_server_remove_graph(self.h, int(gid))
+        if st != 0:
+            raise GrestError(st, "grest_server_remove_graph")
+
+    def embedding(self, gid):
+        n = C.c_int64()
+        st = self.lib.grest_server_get_embedding(self.h, int(gid), None, None, None, C.byref(n))
+        if st != 0:
+            raise GrestError(st, "grest_server_get_embedding")
+        k = self.k[gid]
+        U, th, live = np.empty((n.value, k)), np.empty(k), np.empty(n.value, np.uint8)
+        st = self.lib.grest_server_get_embedding(self.h, int(gid), _ptr(U), _ptr(th), _ptr(live), C.byref(n))
+        if st != 0:
+            raise GrestError(st, "grest_server_get_embedding")
+        return U, th, live.astype(bool)
+
+    def resident(self):
+        b, n = C.c_int64(), C.c_int32()
+        self.lib.grest_server_resident(self.h, C.byref(b), C.byref(n))
+        return b.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grest_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -334,6 +433,13 @@ class Tracker:
         st = self.lib.grest_centrality(self.h, int(J), _ptr(cent), _ptr(ids), _ptr(vals), 1)
         if st != 0:
             raise GrestError(st, "grest_centrality")
+
+    def device_bytes(self):
+        b = C.c_int64()
+        st = self.lib.grest_get_device_bytes(self.h, C.byref(b))
+        if st != 0:
+            raise GrestError(st, "grest_get_device_bytes")
+        return b.value
 
     def sync(self):
         st = self.lib.grest_sync(self.h)
