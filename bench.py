@@ -533,8 +533,9 @@ def run_batched(args):
                 return
             g = graphs[i]
             rp, col, val = g.csr()
+            extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
             trackers[i] = G.Tracker(g.n, rp, col, val, None, None, K, stream=streams[i].cuda_stream, L=20, P=20,
-                                    node_capacity=int(g.n * 1.1) + 1024)
+                                    node_capacity=int(g.n * 1.1) + 1024, **extra)
 
     pool = [threading.Thread(target=make) for _ in range(args.threads)]
     for t in pool:
@@ -563,7 +564,8 @@ def run_batched(args):
     nodes = sum(g.n for g in graphs)
     line = {"metric": f"G-REST batched updates/s, {ng} SBM graphs (n 1k-50k log-uniform), K=8, one update each",
             "value": upd, "unit": "updates/s", "n_gpus": 1, "rounds": rounds, "warmup_rounds": warm,
-            "ms_per_round": 1e3 * sum(times) / rounds, "higher_is_better": True, "dtype": "f64",
+            "ms_per_round": 1e3 * sum(times) / rounds, "higher_is_better": True,
+            "dtype": "f64" if args.batched_precision == "fp64" else "f32+f64",
             "data": "synthetic", "threads": args.threads,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "config": {"workload": "batched SBM", "graphs": ng, "total_nodes": nodes, "K": K, "L": 20, "P": 20,
@@ -680,6 +682,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true", help="many small SBM graphs through grest_batch_apply_updates")
     ap.add_argument("--graphs", type=int, default=512, help="--batched: number of graphs")
+    ap.add_argument("--batched-precision", choices=["fp64", "mixed"], default="fp64", help="--batched: step precision")
     ap.add_argument("--threads", type=int, default=16, help="--batched: host threads")
     ap.add_argument("--serve", action="store_true", help="the serving loop under Poisson update requests")
     ap.add_argument("--requests", type=int, default=256, help="--serve: measured requests")

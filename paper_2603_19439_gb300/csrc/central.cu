@@ -298,7 +298,7 @@ int central_top(int64_t n, int J, int32_t* top_ids, double* top_vals, void* work
   int P = 1;
   while (P < J) P <<= 1;
   const size_t smem = (size_t)P * (sizeof(unsigned long long) + sizeof(int32_t));
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_top_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  reserve_dynamic_smem(k_top_sort, smem);
   k_top_sort<<<1, 1024, smem, s>>>(L.sel_key, L.sel_id, J, P, top_ids, top_vals);
   return launches + 2;
 }

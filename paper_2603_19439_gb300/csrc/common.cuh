@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/grest.h"
 
 namespace grest {
@@ -32,16 +34,22 @@ __device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(
 // current device (opt-in limit minus the kernel's static shared memory), and
 // raise the kernel's limit to `bytes` when that fits.  Returns false (and
 // changes nothing) when it does not fit.
+// The kernel attribute is process-wide and contexts may launch from several
+// host threads at once, so it only ever grows (under one lock): a launch with
+// fewer bytes stays valid whatever another thread reserves meanwhile.
+std::mutex& smem_attr_mutex();
+
 template <typename K>
 inline bool reserve_dynamic_smem(K kernel, size_t bytes) {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(smem_attr_mutex());
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
   if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
-  if (bytes > 48 * 1024 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-                               cudaSuccess) {
+  if (bytes > (size_t)fa.maxDynamicSharedSizeBytes &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }

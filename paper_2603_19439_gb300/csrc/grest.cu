@@ -40,6 +40,13 @@ struct DevBuf {
 
 }  // namespace
 
+namespace grest {
+std::mutex& smem_attr_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+}  // namespace grest
+
 struct grest_ctx {
   grest_config cfg{};
   int dev = 0;

@@ -372,7 +372,7 @@ bool cluster_ok(K kern, size_t smem, int C) {
   if (cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
       cudaFuncGetAttributes(&fa, kern) == cudaSuccess && smem + fa.sharedSizeBytes <= (size_t)optin &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+      reserve_dynamic_smem(kern, smem) &&
       (C <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);

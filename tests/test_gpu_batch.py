@@ -118,3 +118,39 @@ def test_batch_failing_member_leaves_others_updated(cuda):
     batch.close()
     for tr in trs + ref:
         tr.close()
+
+
+def test_batch_mixed_precision_equals_alone(cuda):
+    """Mixed-precision contexts of different sizes stepped concurrently (their
+    tensor-core kernels reserve different amounts of shared memory from
+    several host threads at once): each result equals the update alone."""
+    torch = cuda
+    k = 8
+    graphs = small_graphs(12, 700)
+    states = [O.init_state(g.n, *g.csr(), k, O.OP_ADJ) for g in graphs]
+    kw = dict(precision=G.MIXED, drop_tol=1e-3, L=20, P=20)
+    alone, mixed = [], []
+    for g, st in zip(graphs, states):
+        rp, col, val = g.csr()
+        alone.append(G.Tracker(g.n, rp, col, val, st.X, st.lam, k, stream=torch.cuda.Stream().cuda_stream, **kw))
+        mixed.append(G.Tracker(g.n, rp, col, val, st.X, st.lam, k, stream=torch.cuda.Stream().cuda_stream, **kw))
+    batch = G.Batch(mixed, n_threads=12)
+    rng = np.random.default_rng(13)
+    gbs = [g.copy() for g in graphs]
+    for t in range(2):
+        ups = []
+        for gb in gbs:
+            b = wl.random_churn_batch(gb, max(1, gb.n // 50), 60, 40, rng)
+            gb.apply(b)
+            ups.append(b)
+        for tr, b in zip(alone, ups):
+            tr.update(b)
+        codes, _ = batch.update(ups)
+        assert codes == [0] * len(graphs)
+        for i, (ta, tb) in enumerate(zip(alone, mixed)):
+            Ua, tha, _ = ta.embedding()
+            Ub, thb, _ = tb.embedding()
+            assert np.array_equal(Ua, Ub) and np.array_equal(tha, thb), (t, i)
+    batch.close()
+    for tr in alone + mixed:
+        tr.close()
