@@ -618,7 +618,8 @@ def run_serve(args):
     t_gen = time.time() - t0
     sv = G.Server(n_workers=args.threads)
     t0 = time.time()
-    gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=int(g.n * 1.2) + 4096)
+    extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
+    gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=int(g.n * 1.2) + 4096, **extra)
             for g, k in zip(graphs, ks)]
     # calibration: one request per graph at once (admission and device initial pairs happen here)
     tc = time.perf_counter()
@@ -656,7 +657,8 @@ def run_serve(args):
     used, nres = sv.resident()
     line = {"metric": f"G-REST serving: {ng} resident Chung-Lu graphs, Poisson update requests",
             "value": len(stream) / wall, "unit": "updates/s", "n_gpus": 1, "requests": len(stream),
-            "higher_is_better": True, "dtype": "f64", "data": "synthetic", "workers": args.threads,
+            "higher_is_better": True, "dtype": "f64" if args.batched_precision == "fp64" else "f32+f64",
+            "data": "synthetic", "workers": args.threads,
             "arrival_rate_per_s": rate, "sustained_rate_per_s": cap,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(np.max(lat))},
@@ -682,7 +684,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true", help="many small SBM graphs through grest_batch_apply_updates")
     ap.add_argument("--graphs", type=int, default=512, help="--batched: number of graphs")
-    ap.add_argument("--batched-precision", choices=["fp64", "mixed"], default="fp64", help="--batched: step precision")
+    ap.add_argument("--batched-precision", choices=["fp64", "mixed"], default="fp64", help="--batched / --serve: step precision")
     ap.add_argument("--threads", type=int, default=16, help="--batched: host threads")
     ap.add_argument("--serve", action="store_true", help="the serving loop under Poisson update requests")
     ap.add_argument("--requests", type=int, default=256, help="--serve: measured requests")
