@@ -675,6 +675,34 @@ void launch_gram_part(dim3 grid, int tm, int tn, const T* X, int64_t ldx, int a,
   }
 }
 
+// CTAs of one launch of the variant that fit on the device at once
+template <typename T>
+int gram_wave(int tm, int tn) {
+  const int nthr = (tm / 4) * (tn / 4);
+  int occ = 0, dev = 0, nsm = 152;
+  cudaError_t e;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if (tm == 32 && tn == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part<32, 32>, nthr, 0);
+    else if (tm == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part<32, 64>, nthr, 0);
+    else if (tn == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part<64, 32>, nthr, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part<64, 64>, nthr, 0);
+  } else {
+    if (tm == 32 && tn == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part_f32<32, 32>, nthr, 0);
+    else if (tm == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part_f32<32, 64>, nthr, 0);
+    else if (tn == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part_f32<64, 32>, nthr, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram_part_f32<64, 64>, nthr, 0);
+  }
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 4;
+  }
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm * occ;
+}
+
+// partial-sum buffer of the callers that pass no capacity (a context's part buffer)
+constexpr int64_t kDefaultPartCap = 8'000'000;
+
 template <typename T>
 void gram_t(const T* X, int64_t ldx, int a, const T* Y, int64_t ldy, int b, int64_t n, double* C, int64_t ldc,
             double* part, bool symmetric, int64_t part_cap, cudaStream_t s) {
@@ -688,8 +716,12 @@ void gram_t(const T* X, int64_t ldx, int a, const T* Y, int64_t ldy, int b, int6
   if (symmetric) tm = tn = tile_of(a);
   const int nta = (int)cdiv(a, tm), ntb = (int)cdiv(b, tn);
   const int nt = symmetric ? nta * (nta + 1) / 2 : nta * ntb;
-  int64_t chunks = gram_chunks(n, nta * ntb);
-  if (part_cap > 0 && chunks > part_cap / ((int64_t)a * b)) chunks = part_cap / ((int64_t)a * b);
+  // one full wave of CTAs: row chunks x computed tiles ~ the CTAs that fit at once
+  int64_t chunks = gram_wave<T>(tm, tn) / nt;
+  if (chunks > cdiv(n, 256)) chunks = cdiv(n, 256);
+  const int64_t cap = (part_cap > 0 ? part_cap : kDefaultPartCap) / ((int64_t)a * b);
+  if (chunks > cap) chunks = cap;
+  if (chunks < 1) chunks = 1;
   int64_t rpc = cdiv(n, chunks);
   chunks = cdiv(n, rpc);
   dim3 grid((unsigned)nt, (unsigned)chunks);
