@@ -218,6 +218,43 @@ grest_status grest_get_embedding(grest_ctx *ctx, double *U, double *theta, uint8
  */
 grest_status grest_set_embedding(grest_ctx *ctx, const double *U, const double *theta, int32_t on_device);
 
+/*
+ * Checkpoint and restore of a context (the tracked state of Alg. 2 between
+ * two updates: the graph G^(t), (X_K, Lambda_K) and the step counter).
+ *
+ * grest_checkpoint writes the context's state into the caller's host buffer
+ * buf of *bytes bytes.  buf == NULL: *bytes receives the size needed and
+ * nothing is written.  A buffer smaller than that size: GREST_ERR_CAPACITY
+ * with the size needed in *bytes.  On success *bytes is the size written.
+ * The call waits for the context's stream; the context is not modified.
+ * The buffer holds: a header (format tag, version, the grest_config, node
+ * and nonzero counts, the step counter), the graph as a compact CSR (int64
+ * row pointers, int32 columns sorted within each row, FP64 weights when the
+ * graph is weighted), the FP64 weighted degrees, U (n x k row-major), theta
+ * (k) and the live mask (n bytes).  It is a plain byte array (host byte
+ * order) that the caller may store and reload.
+ *
+ * grest_restore builds a new context from such a buffer (read only; the
+ * caller keeps ownership), with its work on cuda_stream.  Its next updates
+ * give bit-identical results to those of the checkpointed context: the
+ * neighbour order of every row, the degrees, the pairs and the step counter
+ * (which seeds the RSVD test matrix of Sec. 3.5) are restored.  Slack
+ * capacities are laid out afresh (node_capacity / nnz_capacity of the saved
+ * configuration are kept when the restored graph fits them, else the
+ * defaults are used).  A buffer that is not a checkpoint of this format
+ * (tag, version, sizes, row pointers): GREST_ERR_INVALID_ARG before any
+ * device work; grest_init's errors otherwise.
+ *
+ * grest_checkpoint_embedding reads (X_K, Lambda_K) and the live mask out of a
+ * checkpoint buffer on the host (no device needed), with the conventions of
+ * grest_get_embedding: n_out (required) receives n, k_out (nullable) k;
+ * U (n x k), theta (k) and live (n) are nullable host outputs.
+ */
+grest_status grest_checkpoint(grest_ctx *ctx, void *buf, int64_t *bytes);
+grest_status grest_restore(const void *buf, int64_t bytes, void *cuda_stream, grest_ctx **out);
+grest_status grest_checkpoint_embedding(const void *buf, int64_t bytes, double *U, double *theta,
+                                        uint8_t *live, int64_t *n_out, int32_t *k_out);
+
 /* All m Ritz values of the last step in tracking order (Alg. 1); *m_out receives m.
  * ritz may be NULL to query m; it must hold at least m values otherwise. */
 grest_status grest_get_ritz_values(grest_ctx *ctx, double *ritz, int32_t *m_out);
@@ -374,12 +411,23 @@ grest_status grest_get_device_bytes(grest_ctx *ctx, int64_t *bytes);
  *   pending requests have run; no further submissions are accepted for it.
  *   grest_server_get_embedding waits until the graph is idle and copies its
  *   (X_K, Lambda_K, live) to host memory (GREST_ERR_INVALID_ARG when the
- *   graph is not resident).
+ *   graph was never admitted or was removed).
  *   grest_server_resident reports the resident bytes and graph count.
  * The budget is checked at admission against the context's size then; a
  * resident graph whose buffers grow for a larger batch keeps its place (its
- * new size counts toward later admissions).  There is no eviction: a graph
- * that does not fit waits until removals free memory.
+ * new size counts toward later admissions).
+ *   grest_server_set_eviction(on = 1): when the oldest waiting request
+ *   belongs to a graph that does not fit, the least recently used idle
+ *   resident graph (no request queued or running) is checkpointed to host
+ *   memory (grest_checkpoint) and its context freed, one graph at a time
+ *   until the waiting graph fits; an evicted graph is restored from its
+ *   checkpoint (grest_restore) at its next admission, so its results are
+ *   unchanged by the eviction.  grest_server_get_embedding of an evicted
+ *   graph reads the checkpoint.  Off (0, the default): a graph that does
+ *   not fit waits until removals free memory.  Other values:
+ *   GREST_ERR_INVALID_ARG.
+ *   grest_server_counters reports admissions (restores included),
+ *   evictions and restores so far (each output nullable).
  * grest_server_destroy stops the workers after their current requests and
  * releases every context; no other call may be in progress or follow.
  */
@@ -397,6 +445,9 @@ grest_status grest_server_remove_graph(grest_server *server, int32_t graph_id);
 grest_status grest_server_get_embedding(grest_server *server, int32_t graph_id, double *U, double *theta,
                                         uint8_t *live, int64_t *n_out);
 grest_status grest_server_resident(grest_server *server, int64_t *bytes, int32_t *n_resident);
+grest_status grest_server_set_eviction(grest_server *server, int32_t on);
+grest_status grest_server_counters(grest_server *server, int64_t *admissions, int64_t *evictions,
+                                   int64_t *restores);
 void grest_server_destroy(grest_server *server);
 
 /* Static string naming a status code. */

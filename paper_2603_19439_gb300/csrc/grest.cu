@@ -1435,6 +1435,192 @@ grest_status grest_set_embedding(grest_ctx* c, const double* U, const double* th
   return from_cuda(cudaStreamSynchronize(s));
 }
 
+// ------------------------------------------------------------------ checkpoints
+// A checkpoint is one host byte array: a header, then the graph as a compact
+// CSR (rows sorted, as the context keeps them), the weighted degrees as
+// maintained by the updates, the tracked pairs and the live mask.  Restoring
+// it gives a context whose next steps are bit-identical to the original's:
+// the per-row neighbour order, the degrees, (X_K, Lambda_K) and the step
+// counter (which seeds the RSVD test matrix) are all carried over.
+namespace {
+
+constexpr char kCkptMagic[8] = {'G', 'R', 'E', 'S', 'T', 'C', 'K', '1'};
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, K;
+  int64_t n, nnz, step, has_val;
+  grest_config cfg;
+};
+
+struct CkptLayout {
+  size_t rowptr, col, val, deg, U, theta, live, total;
+};
+
+inline size_t up8(size_t x) { return (x + 7) & ~(size_t)7; }
+
+CkptLayout ckpt_layout(int64_t n, int64_t nnz, int K, bool has_val) {
+  CkptLayout L;
+  size_t o = up8(sizeof(CkptHeader));
+  L.rowptr = o;
+  o += sizeof(int64_t) * (size_t)(n + 1);
+  L.col = o;
+  o = up8(o + sizeof(int32_t) * (size_t)nnz);
+  L.val = o;
+  if (has_val) o += sizeof(double) * (size_t)nnz;
+  L.deg = o;
+  o += sizeof(double) * (size_t)n;
+  L.U = o;
+  o += sizeof(double) * (size_t)n * K;
+  L.theta = o;
+  o += sizeof(double) * (size_t)K;
+  L.live = o;
+  L.total = up8(o + (size_t)n);
+  return L;
+}
+
+// Header and size checks of a checkpoint (host only); rowptr is checked too.
+bool ckpt_parse(const void* buf, int64_t bytes, CkptHeader* h, CkptLayout* L) {
+  if (!buf || bytes < (int64_t)sizeof(CkptHeader)) return false;
+  memcpy(h, buf, sizeof(CkptHeader));
+  if (memcmp(h->magic, kCkptMagic, 8) != 0 || h->version != 1) return false;
+  if (h->n < 1 || h->n > INT32_MAX || h->nnz < 0 || h->nnz > ((int64_t)1 << 40) || h->K < 1 || h->K > 64 ||
+      h->K > h->n || h->cfg.k != h->K || (h->has_val != 0 && h->has_val != 1) || h->step < 0)
+    return false;
+  *L = ckpt_layout(h->n, h->nnz, h->K, h->has_val != 0);
+  if ((int64_t)L->total != bytes) return false;
+  const int64_t* rp = reinterpret_cast<const int64_t*>(static_cast<const uint8_t*>(buf) + L->rowptr);
+  if (rp[0] != 0 || rp[h->n] != h->nnz) return false;
+  for (int64_t i = 0; i < h->n; ++i)
+    if (rp[i + 1] < rp[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+grest_status grest_checkpoint(grest_ctx* c, void* buf, int64_t* bytes) {
+  if (!c || !bytes) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  cudaStream_t s = c->stream;
+  CK(cudaStreamSynchronize(s));
+  const Csr& g = c->g;
+  const int64_t n = g.n, nnz = c->nnz;
+  const int K = c->K;
+  const bool has_val = g.val != nullptr;
+  const CkptLayout L = ckpt_layout(n, nnz, K, has_val);
+  if (!buf) {
+    *bytes = (int64_t)L.total;
+    return GREST_OK;
+  }
+  if (*bytes < (int64_t)L.total) {
+    *bytes = (int64_t)L.total;
+    return GREST_ERR_CAPACITY;
+  }
+  int64_t top = 0;
+  CK(cudaMemcpy(&top, g.arena_top, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  std::vector<int64_t> off(n);
+  std::vector<int32_t> len(n), arena(top);
+  std::vector<double> varena(has_val ? top : 0);
+  CK(cudaMemcpyAsync(off.data(), g.row_off, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(len.data(), g.row_len, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  if (top > 0) CK(cudaMemcpyAsync(arena.data(), g.col, sizeof(int32_t) * top, cudaMemcpyDeviceToHost, s));
+  if (has_val && top > 0) CK(cudaMemcpyAsync(varena.data(), g.val, sizeof(double) * top, cudaMemcpyDeviceToHost, s));
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  CK(cudaMemcpyAsync(b + L.deg, g.deg, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpy2DAsync(b + L.U, sizeof(double) * K, c->U, sizeof(double) * c->ldu, sizeof(double) * K, n,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b + L.theta, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(b + L.live, g.live, n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int64_t* rp = reinterpret_cast<int64_t*>(b + L.rowptr);
+  int32_t* col = reinterpret_cast<int32_t*>(b + L.col);
+  double* val = reinterpret_cast<double*>(b + L.val);
+  rp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (len[i] < 0 || off[i] < 0 || off[i] + len[i] > top || rp[i] + len[i] > nnz) return GREST_ERR_CUDA;
+    memcpy(col + rp[i], arena.data() + off[i], sizeof(int32_t) * len[i]);
+    if (has_val) memcpy(val + rp[i], varena.data() + off[i], sizeof(double) * len[i]);
+    rp[i + 1] = rp[i] + len[i];
+  }
+  if (rp[n] != nnz) return GREST_ERR_CUDA;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.K = K;
+  h.n = n;
+  h.nnz = nnz;
+  h.step = c->step;
+  h.has_val = has_val ? 1 : 0;
+  h.cfg = c->cfg;
+  memcpy(b, &h, sizeof(h));
+  memset(b + L.live + n, 0, L.total - (L.live + n));
+  *bytes = (int64_t)L.total;
+  return GREST_OK;
+}
+
+grest_status grest_checkpoint_embedding(const void* buf, int64_t bytes, double* U, double* theta, uint8_t* live,
+                                        int64_t* n_out, int32_t* k_out) {
+  CkptHeader h;
+  CkptLayout L;
+  if (!n_out || !ckpt_parse(buf, bytes, &h, &L)) return GREST_ERR_INVALID_ARG;
+  const uint8_t* b = static_cast<const uint8_t*>(buf);
+  *n_out = h.n;
+  if (k_out) *k_out = h.K;
+  if (U) memcpy(U, b + L.U, sizeof(double) * (size_t)h.n * h.K);
+  if (theta) memcpy(theta, b + L.theta, sizeof(double) * h.K);
+  if (live) memcpy(live, b + L.live, (size_t)h.n);
+  return GREST_OK;
+}
+
+grest_status grest_restore(const void* buf, int64_t bytes, void* cuda_stream, grest_ctx** out) {
+  if (!out) return GREST_ERR_INVALID_ARG;
+  *out = nullptr;
+  CkptHeader h;
+  CkptLayout L;
+  if (!ckpt_parse(buf, bytes, &h, &L)) return GREST_ERR_INVALID_ARG;
+  const uint8_t* b = static_cast<const uint8_t*>(buf);
+  const int64_t* rp = reinterpret_cast<const int64_t*>(b + L.rowptr);
+  const int32_t* col = reinterpret_cast<const int32_t*>(b + L.col);
+  const double* val = h.has_val ? reinterpret_cast<const double*>(b + L.val) : nullptr;
+  const uint8_t* live = b + L.live;
+  // the slack layout of grest_init must fit the saved capacities
+  grest_config cfg = h.cfg;
+  if (cfg.node_capacity > 0 && cfg.node_capacity < h.n) cfg.node_capacity = 0;
+  if (cfg.nnz_capacity > 0) {
+    int64_t need = 0;
+    for (int64_t i = 0; i < h.n; ++i) {
+      const int64_t l = rp[i + 1] - rp[i];
+      need += l + l / 4 + 4;
+    }
+    if (cfg.nnz_capacity < need) cfg.nnz_capacity = 0;
+  }
+  grest_ctx* c = nullptr;
+  grest_status st = grest_init(&cfg, h.n, rp, col, val, reinterpret_cast<const double*>(b + L.U),
+                               reinterpret_cast<const double*>(b + L.theta), cuda_stream, &c);
+  if (st != GREST_OK) return st;
+  c->cfg = h.cfg;
+  c->cfg.node_capacity = cfg.node_capacity;
+  c->cfg.nnz_capacity = cfg.nnz_capacity;
+  cudaStream_t s = c->stream;
+  Csr& g = c->g;
+  bool ok = cudaMemcpyAsync(g.deg, b + L.deg, sizeof(double) * h.n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(g.live, live, h.n, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (ok) {
+    graph_refresh_derived(g, c->gw, h.n, s);
+    zero_dead_rows(c->U, c->ldu, c->K, g.live, h.n, s);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  }
+  if (!ok) {
+    grest_destroy(c);
+    return GREST_ERR_CUDA;
+  }
+  c->step = h.step;
+  c->stats.step = h.step;
+  *out = c;
+  return GREST_OK;
+}
+
 grest_status grest_get_ritz_values(grest_ctx* c, double* ritz, int32_t* m_out) {
   if (!c || !m_out) return GREST_ERR_INVALID_ARG;
   *m_out = c->last_m;

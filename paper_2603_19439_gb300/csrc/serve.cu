@@ -5,8 +5,12 @@
 // stream, and admits graphs by a device-memory budget: a graph becomes
 // resident when its context fits beside the resident ones (or when nothing
 // else is resident), and memory returns to the budget when a graph is
-// removed.  Requests of one graph run in submission order, one at a time;
-// different graphs run concurrently.  Built only on the public C ABI.
+// removed or, with eviction on, when an idle resident graph is checkpointed
+// to host memory (least recently used first) to make room for a graph whose
+// requests are the oldest waiting; an evicted graph is restored from its
+// checkpoint at its next admission.  Requests of one graph run in
+// submission order, one at a time; different graphs run concurrently.  Built
+// only on the public C ABI.
 #include <condition_variable>
 #include <chrono>
 #include <deque>
@@ -46,6 +50,9 @@ struct Graph {
   int64_t bytes = 0;      // device bytes of its context (0 until measured)
   bool resident = false, busy = false, removed = false;
   std::deque<int64_t> queue;  // pending tickets, in submission order
+  std::vector<uint8_t> ckpt;  // grest_checkpoint of an evicted graph (empty otherwise)
+  Clock::time_point last_used{};
+  bool evict_failed = false;  // a checkpoint failed: not evicted again until its next request ran
 };
 
 }  // namespace
@@ -54,6 +61,8 @@ struct grest_server {
   int dev = 0;
   int64_t budget = 0, used = 0;
   int n_resident = 0;
+  bool evict = false;  // checkpoint idle resident graphs to host memory to admit waiting ones
+  int64_t n_admissions = 0, n_evictions = 0, n_restores = 0;
   std::vector<std::unique_ptr<Graph>> graphs;
   std::vector<std::unique_ptr<Ticket>> tickets;
   std::mutex mu;
@@ -86,26 +95,53 @@ void fail_queue(grest_server* sv, Graph& g, grest_status st) {  // mu held
   g.queue.clear();
 }
 
-// The next request a worker can take (mu held): the oldest pending ticket of
-// a graph that is not busy and is resident or can be admitted.  Returns the
-// graph index, or -1; *admit says the graph must be admitted first.
-int pick(grest_server* sv, bool* admit) {
-  int best = -1;
-  Clock::time_point tb{};
+enum Action { kRun, kAdmit, kEvict };
+
+// What a worker does next (mu held).  Among graphs that are not busy and
+// have requests: the oldest pending ticket of a graph that is resident (run
+// it) or fits the budget (admit it first).  With eviction on, when the oldest
+// pending ticket of all belongs to a graph that does not fit, the least
+// recently used idle resident graph is evicted instead.  Returns the graph
+// index, or -1 when there is nothing to do.
+int pick(grest_server* sv, Action* act) {
+  int best = -1, starved = -1;
+  Clock::time_point tb{}, ts{};
   for (int i = 0; i < (int)sv->graphs.size(); ++i) {
     Graph& g = *sv->graphs[i];
     if (g.busy || g.queue.empty()) continue;
+    const Clock::time_point t = sv->tickets[g.queue.front()]->t_submit;
     if (!g.resident) {
       const bool fits = sv->n_resident == 0 || (g.bytes > 0 ? sv->used + g.bytes <= sv->budget : sv->used < sv->budget);
-      if (!fits) continue;
+      if (!fits) {
+        if (starved < 0 || t < ts) {
+          starved = i;
+          ts = t;
+        }
+        continue;
+      }
     }
-    const Clock::time_point t = sv->tickets[g.queue.front()]->t_submit;
     if (best < 0 || t < tb) {
       best = i;
       tb = t;
     }
   }
-  if (best >= 0) *admit = !sv->graphs[best]->resident;
+  if (sv->evict && starved >= 0 && (best < 0 || ts < tb)) {
+    int v = -1;
+    Clock::time_point tv{};
+    for (int j = 0; j < (int)sv->graphs.size(); ++j) {
+      Graph& g = *sv->graphs[j];
+      if (!g.resident || g.busy || !g.queue.empty() || g.removed || g.evict_failed) continue;
+      if (v < 0 || g.last_used < tv) {
+        v = j;
+        tv = g.last_used;
+      }
+    }
+    if (v >= 0) {
+      *act = kEvict;
+      return v;
+    }
+  }
+  if (best >= 0) *act = sv->graphs[best]->resident ? kRun : kAdmit;
   return best;
 }
 
@@ -113,19 +149,54 @@ void worker(grest_server* sv) {
   cudaSetDevice(sv->dev);
   std::unique_lock<std::mutex> lk(sv->mu);
   for (;;) {
-    bool admit = false;
+    Action act = kRun;
     int gi = -1;
-    sv->cv.wait(lk, [&] { return sv->stop || (gi = pick(sv, &admit)) >= 0; });
+    sv->cv.wait(lk, [&] { return sv->stop || (gi = pick(sv, &act)) >= 0; });
     if (sv->stop) return;
     Graph& g = *sv->graphs[gi];
     g.busy = true;
-    if (admit) {
+    if (act == kEvict) {
+      // checkpoint to host memory, then free the context; on failure the
+      // graph stays resident and is not chosen again until a request of it
+      // has run
+      lk.unlock();
+      std::vector<uint8_t> blob;
+      int64_t nb = 0;
+      grest_status s0 = grest_checkpoint(g.ctx, nullptr, &nb);
+      if (s0 == GREST_OK) {
+        blob.resize((size_t)nb);
+        s0 = grest_checkpoint(g.ctx, blob.data(), &nb);
+      }
+      if (s0 == GREST_OK) {
+        grest_destroy(g.ctx);
+        cudaStreamDestroy(g.stream);
+      }
+      lk.lock();
+      if (s0 == GREST_OK) {
+        g.ckpt.swap(blob);
+        g.ctx = nullptr;
+        g.stream = nullptr;
+        g.resident = false;
+        sv->used -= g.bytes;
+        sv->n_resident -= 1;
+        sv->n_evictions += 1;
+      } else {
+        g.evict_failed = true;
+      }
+      g.busy = false;
+      sv->cv.notify_all();
+      continue;
+    }
+    if (act == kAdmit) {
       lk.unlock();
       cudaStream_t st = nullptr;
       grest_ctx* ctx = nullptr;
       grest_status s0 = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? GREST_OK
                                                                                                 : GREST_ERR_CUDA;
-      if (s0 == GREST_OK)
+      const bool from_ckpt = !g.ckpt.empty();
+      if (s0 == GREST_OK && from_ckpt)
+        s0 = grest_restore(g.ckpt.data(), (int64_t)g.ckpt.size(), st, &ctx);
+      else if (s0 == GREST_OK)
         s0 = grest_init(&g.cfg, g.n, g.rowptr.data(), g.col.data(), g.has_val ? g.val.data() : nullptr,
                         g.has_pairs ? g.U0.data() : nullptr, g.has_pairs ? g.theta0.data() : nullptr, st, &ctx);
       int64_t bytes = 0;
@@ -148,8 +219,14 @@ void worker(grest_server* sv) {
         g.stream = st;
         g.bytes = bytes;
         g.resident = true;
+        g.last_used = Clock::now();
         sv->used += bytes;
         sv->n_resident += 1;
+        sv->n_admissions += 1;
+        if (from_ckpt) {
+          sv->n_restores += 1;
+          std::vector<uint8_t>().swap(g.ckpt);
+        }
       }
       g.busy = false;
       sv->cv.notify_all();
@@ -182,6 +259,8 @@ void worker(grest_server* sv) {
     tk.status = st;
     tk.done = true;
     g.busy = false;
+    g.last_used = tk.t_end;
+    g.evict_failed = false;
     if (g.removed && g.queue.empty()) release(sv, g);
     sv->cv.notify_all();
   }
@@ -291,6 +370,7 @@ grest_status grest_server_remove_graph(grest_server* sv, int32_t graph_id) {
     return GREST_ERR_INVALID_ARG;
   Graph& g = *sv->graphs[graph_id];
   g.removed = true;
+  std::vector<uint8_t>().swap(g.ckpt);
   if (!g.busy && g.queue.empty()) release(sv, g);
   sv->cv.notify_all();
   return GREST_OK;
@@ -303,6 +383,8 @@ grest_status grest_server_get_embedding(grest_server* sv, int32_t graph_id, doub
   if (graph_id < 0 || graph_id >= (int32_t)sv->graphs.size()) return GREST_ERR_INVALID_ARG;
   Graph& g = *sv->graphs[graph_id];
   sv->cv.wait(lk, [&] { return !g.busy && g.queue.empty(); });
+  if (!g.resident && !g.ckpt.empty())  // evicted: read the checkpoint
+    return grest_checkpoint_embedding(g.ckpt.data(), (int64_t)g.ckpt.size(), U, theta, live, n_out, nullptr);
   if (!g.resident) return GREST_ERR_INVALID_ARG;  // never admitted, or removed
   g.busy = true;  // no worker takes it while the copy runs
   lk.unlock();
@@ -318,6 +400,23 @@ grest_status grest_server_resident(grest_server* sv, int64_t* bytes, int32_t* n_
   std::lock_guard<std::mutex> lk(sv->mu);
   if (bytes) *bytes = sv->used;
   if (n_resident) *n_resident = sv->n_resident;
+  return GREST_OK;
+}
+
+grest_status grest_server_set_eviction(grest_server* sv, int32_t on) {
+  if (!sv || (on != 0 && on != 1)) return GREST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->evict = on != 0;
+  sv->cv.notify_all();
+  return GREST_OK;
+}
+
+grest_status grest_server_counters(grest_server* sv, int64_t* admissions, int64_t* evictions, int64_t* restores) {
+  if (!sv) return GREST_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (admissions) *admissions = sv->n_admissions;
+  if (evictions) *evictions = sv->n_evictions;
+  if (restores) *restores = sv->n_restores;
   return GREST_OK;
 }
 

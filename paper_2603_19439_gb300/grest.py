@@ -73,8 +73,9 @@ EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sy
            "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_batch_create",
            "grest_batch_apply_updates", "grest_batch_destroy", "grest_get_device_bytes", "grest_server_create",
            "grest_server_add_graph", "grest_server_submit", "grest_server_wait", "grest_server_poll", "grest_server_remove_graph",
-           "grest_server_get_embedding", "grest_server_resident", "grest_server_destroy", "grest_destroy",
-           "grest_status_str"]
+           "grest_server_get_embedding", "grest_server_resident", "grest_server_destroy", "grest_checkpoint",
+           "grest_restore", "grest_checkpoint_embedding", "grest_server_set_eviction", "grest_server_counters",
+           "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -119,6 +120,11 @@ def load_library(path=None):
     lib.grest_server_resident.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     lib.grest_server_destroy.argtypes = [vp]
     lib.grest_server_destroy.restype = None
+    lib.grest_checkpoint.argtypes = [vp, vp, C.POINTER(i64)]
+    lib.grest_restore.argtypes = [vp, i64, vp, C.POINTER(vp)]
+    lib.grest_checkpoint_embedding.argtypes = [vp, i64, vp, vp, vp, C.POINTER(i64), C.POINTER(i32)]
+    lib.grest_server_set_eviction.argtypes = [vp, i32]
+    lib.grest_server_counters.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
     lib.grest_status_str.argtypes = [i32]
@@ -163,6 +169,21 @@ def gram_noalloc(X, Y, C, stream=None):
                                 X.shape[0], C.data_ptr(), C.stride(0), stream)
     if st != 0:
         raise GrestError(st, "grest_gram_noalloc")
+
+
+def checkpoint_embedding(blob):
+    """(U, theta, live) read out of grest_checkpoint bytes on the host."""
+    lib = load_library()
+    buf = np.frombuffer(blob, np.uint8)
+    n, k = C.c_int64(), C.c_int32()
+    st = lib.grest_checkpoint_embedding(_ptr(buf), buf.size, None, None, None, C.byref(n), C.byref(k))
+    if st != 0:
+        raise GrestError(st, "grest_checkpoint_embedding")
+    U, th, live = np.empty((n.value, k.value)), np.empty(k.value), np.empty(n.value, np.uint8)
+    st = lib.grest_checkpoint_embedding(_ptr(buf), buf.size, _ptr(U), _ptr(th), _ptr(live), C.byref(n), None)
+    if st != 0:
+        raise GrestError(st, "grest_checkpoint_embedding")
+    return U, th, live.astype(bool)
 
 
 def _batch_arrays(batch, on_device):
@@ -294,6 +315,21 @@ class Server:
         b, n = C.c_int64(), C.c_int32()
         self.lib.grest_server_resident(self.h, C.byref(b), C.byref(n))
         return b.value, n.value
+
+    def set_eviction(self, on=True):
+        """Checkpoint idle resident graphs to host memory when a waiting graph
+        does not fit the budget (restored at their next admission)."""
+        st = self.lib.grest_server_set_eviction(self.h, 1 if on else 0)
+        if st != 0:
+            raise GrestError(st, "grest_server_set_eviction")
+
+    def counters(self):
+        """(admissions, evictions, restores) so far."""
+        a, e, r = C.c_int64(), C.c_int64(), C.c_int64()
+        st = self.lib.grest_server_counters(self.h, C.byref(a), C.byref(e), C.byref(r))
+        if st != 0:
+            raise GrestError(st, "grest_server_counters")
+        return a.value, e.value, r.value
 
     def close(self):
         if getattr(self, "h", None):
@@ -433,6 +469,35 @@ class Tracker:
         st = self.lib.grest_centrality(self.h, int(J), _ptr(cent), _ptr(ids), _ptr(vals), 1)
         if st != 0:
             raise GrestError(st, "grest_centrality")
+
+    def checkpoint(self):
+        """The context's state as bytes (grest_checkpoint)."""
+        nb = C.c_int64()
+        st = self.lib.grest_checkpoint(self.h, None, C.byref(nb))
+        if st != 0:
+            raise GrestError(st, "grest_checkpoint")
+        buf = np.empty(nb.value, np.uint8)
+        st = self.lib.grest_checkpoint(self.h, _ptr(buf), C.byref(nb))
+        if st != 0:
+            raise GrestError(st, "grest_checkpoint")
+        return buf[:nb.value].tobytes()
+
+    @classmethod
+    def restore(cls, blob, stream=None):
+        """A new Tracker from grest_checkpoint bytes (grest_restore)."""
+        lib = load_library()
+        buf = np.frombuffer(blob, np.uint8)
+        n, k = C.c_int64(), C.c_int32()
+        st = lib.grest_checkpoint_embedding(_ptr(buf), buf.size, None, None, None, C.byref(n), C.byref(k))
+        if st != 0:
+            raise GrestError(st, "grest_checkpoint_embedding")
+        h = C.c_void_p()
+        st = lib.grest_restore(_ptr(buf), buf.size, stream, C.byref(h))
+        if st != 0:
+            raise GrestError(st, "grest_restore")
+        self = cls.__new__(cls)
+        self.lib, self.k, self.cfg, self.h, self._keep = lib, k.value, None, h, None
+        return self
 
     def device_bytes(self):
         b = C.c_int64()

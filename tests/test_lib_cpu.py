@@ -99,3 +99,25 @@ def test_batch_create_checks_arguments_without_gpu(lib):
     assert L.grest_batch_create(2, fake, 4, ctypes.byref(h)) == 0 and h.value
     assert L.grest_batch_apply_updates(None, None, None, None) == 1
     L.grest_batch_destroy(h)
+
+
+def test_checkpoint_calls_check_arguments_without_gpu(lib):
+    """A byte array that is not a checkpoint (wrong tag, too short) is
+    rejected on the host before any device work, by grest_restore and by the
+    host reader grest_checkpoint_embedding; NULL handles are rejected too.
+    Status 1 is GREST_ERR_INVALID_ARG."""
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    junk = (ctypes.c_uint8 * 4096)(*([7] * 4096))
+    h, n, k, nb = vp(), i64(), i32(), i64()
+    assert L.grest_restore(junk, 4096, None, ctypes.byref(h)) == 1 and not h.value
+    assert L.grest_restore(junk, 3, None, ctypes.byref(h)) == 1
+    assert L.grest_restore(None, 0, None, ctypes.byref(h)) == 1
+    assert L.grest_checkpoint_embedding(junk, 4096, None, None, None, ctypes.byref(n), ctypes.byref(k)) == 1
+    assert L.grest_checkpoint_embedding(junk, 4096, None, None, None, None, None) == 1
+    assert L.grest_checkpoint(None, None, ctypes.byref(nb)) == 1
+    assert L.grest_server_set_eviction(None, 1) == 1
+    assert L.grest_server_counters(None, None, None, None) == 1
+    with pytest.raises(grest.GrestError):
+        grest.checkpoint_embedding(bytes(junk))
