@@ -616,7 +616,10 @@ def run_serve(args):
         gb.apply(b)
         reqs.append((gi, b))
     t_gen = time.time() - t0
-    sv = G.Server(n_workers=args.threads)
+    budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else 1 << 50
+    sv = G.Server(n_workers=args.threads, hbm_budget=budget)
+    if args.evict:
+        sv.set_eviction(True)
     t0 = time.time()
     extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
     gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=int(g.n * 1.2) + 4096, **extra)
@@ -655,6 +658,7 @@ def run_serve(args):
         lat.append(wait_ms + run_ms)
     wall = time.perf_counter() - start
     used, nres = sv.resident()
+    adm, evc, rst = sv.counters()
     line = {"metric": f"G-REST serving: {ng} resident Chung-Lu graphs, Poisson update requests",
             "value": len(stream) / wall, "unit": "updates/s", "n_gpus": 1, "requests": len(stream),
             "higher_is_better": True, "dtype": "f64" if args.batched_precision == "fp64" else "f32+f64",
@@ -663,6 +667,8 @@ def run_serve(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(np.max(lat))},
             "failed": int(sum(c != 0 for c in codes)), "resident_graphs": nres, "resident_bytes": used,
+            "hbm_budget_bytes": budget if args.hbm_budget_gb > 0 else None, "eviction": bool(args.evict),
+            "admissions": adm, "evictions": evc, "restores": rst,
             "config": {"workload": "serving Chung-Lu", "graphs": ng, "nodes_total": int(sum(g.n for g in graphs)),
                        "K": "16..32", "edges_per_request": "100..10,000 log-uniform (<= 5% of the graph)"},
             "setup_s": {"generate": t_gen, "first_round_with_admission": t_cal, "add": time.time() - t0},
@@ -688,6 +694,10 @@ def main():
     ap.add_argument("--threads", type=int, default=16, help="--batched: host threads")
     ap.add_argument("--serve", action="store_true", help="the serving loop under Poisson update requests")
     ap.add_argument("--requests", type=int, default=256, help="--serve: measured requests")
+    ap.add_argument("--hbm-budget-gb", type=float, default=0.0,
+                    help="--serve: device-memory budget of the resident graphs (0 = unlimited)")
+    ap.add_argument("--evict", action="store_true",
+                    help="--serve: checkpoint idle graphs to host memory when a waiting graph does not fit")
     ap.add_argument("--kernels", action="store_true",
                     help="time the tensor-core Gram / GEMM entry points at the step's widths instead")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")

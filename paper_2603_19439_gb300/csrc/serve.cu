@@ -62,6 +62,7 @@ struct grest_server {
   int64_t budget = 0, used = 0;
   int n_resident = 0;
   bool evict = false;  // checkpoint idle resident graphs to host memory to admit waiting ones
+  int64_t freeing = 0;  // bytes of evictions in progress
   int64_t n_admissions = 0, n_evictions = 0, n_restores = 0;
   std::vector<std::unique_ptr<Graph>> graphs;
   std::vector<std::unique_ptr<Ticket>> tickets;
@@ -125,7 +126,14 @@ int pick(grest_server* sv, Action* act) {
       tb = t;
     }
   }
-  if (sv->evict && starved >= 0 && (best < 0 || ts < tb)) {
+  // evict only when the evictions already under way would not make room
+  bool room_soon = false;
+  if (starved >= 0 && sv->freeing > 0) {
+    const Graph& w = *sv->graphs[starved];
+    const int64_t after = sv->used - sv->freeing;
+    room_soon = w.bytes > 0 ? after + w.bytes <= sv->budget : after < sv->budget;
+  }
+  if (sv->evict && starved >= 0 && !room_soon && (best < 0 || ts < tb)) {
     int v = -1;
     Clock::time_point tv{};
     for (int j = 0; j < (int)sv->graphs.size(); ++j) {
@@ -159,6 +167,7 @@ void worker(grest_server* sv) {
       // checkpoint to host memory, then free the context; on failure the
       // graph stays resident and is not chosen again until a request of it
       // has run
+      sv->freeing += g.bytes;
       lk.unlock();
       std::vector<uint8_t> blob;
       int64_t nb = 0;
@@ -172,6 +181,7 @@ void worker(grest_server* sv) {
         cudaStreamDestroy(g.stream);
       }
       lk.lock();
+      sv->freeing -= g.bytes;
       if (s0 == GREST_OK) {
         g.ckpt.swap(blob);
         g.ctx = nullptr;
