@@ -193,6 +193,11 @@ void gram_reduce_launch(const double* part, int64_t chunks, int a, int b, double
 
 // tc_gram.cu: tensor-core (tcgen05, 3xTF32) Gram C = X^T Y of FP32 blocks, FP64 output.
 bool gram_tc_supported(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b);
+// CUDA-core FP32 Gram for a narrow side (min(a, b) <= 64, max(a, b) <= 256,
+// 16-byte aligned blocks); returns -1 when the shape or alignment is not taken
+bool gram_narrow_supported(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b);
+int gram_f32_narrow(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+                    int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s);
 // returns 0 when launched, -1 when the shapes or the partial buffer do not allow it
 int gram_f32_tc(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
                 int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s);

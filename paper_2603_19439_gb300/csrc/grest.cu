@@ -335,12 +335,20 @@ void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, in
   prof_end(c, p, 1, 2.0 * n * a * b, 8.0 * n * (X == Y && a == b ? a : a + b));
 }
 
+// FP32 Gram of the mixed path: a narrow side (the projections X_bar^T Y, K
+// columns) on the CUDA cores, wider products on the tensor cores; false when
+// neither kernel takes the shape or alignment
+bool gram_f32_fast(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+                   int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s) {
+  if (n <= 0) return false;
+  if (std::min(a, b) <= 32 && gram_f32_narrow(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0) return true;
+  return gram_tc_supported(X, ldx, a, Y, ldy, b) && gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0;
+}
+
 void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
           int64_t ldc, bool sym) {
   int p = prof_begin(c);
-  bool done = false;
-  if (n > 0 && gram_tc_supported(X, ldx, a, Y, ldy, b))
-    done = gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) == 0;
+  const bool done = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream);
   if (!done) gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
   prof_end(c, p, 1, 2.0 * n * a * b, 4.0 * n * (X == Y && a == b ? a : a + b));
@@ -1698,9 +1706,7 @@ grest_status grest_gram_f32(grest_ctx* c, const float* X, int64_t ldx, int32_t a
     return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
-  bool done = false;
-  if (n > 0 && gram_tc_supported(X, ldx, a, Y, ldy, b))
-    done = gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) == 0;
+  const bool done = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream);
   if (!done) {
     if (gram_parts(n, a, b) * (int64_t)a * b > c->part_cap) return GREST_ERR_CAPACITY;
     gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);

@@ -232,11 +232,14 @@ def test_gram_entry_point(cuda):
 
 
 def test_gram_f32_tensor_core_entry_point(cuda):
-    """grest_gram_f32 (tcgen05, 3xTF32, FP32 accumulation over <= 256 rows,
-    FP64 partial sums) against a float64 product of the same FP32 inputs; the
+    """grest_gram_f32 against a float64 product of the same FP32 inputs; the
     bound is relative to |X|^T |Y| (the scale of the accumulated terms).
-    Includes ragged row counts, widths 1..256 and a misaligned view that must
-    fall back to the CUDA-core kernel."""
+    Products with a side of at most 32 columns take the narrow CUDA-core
+    kernel (FP32 FMAs, 256-row FP32 spans into double-float, FP64 partials;
+    a right-narrow product computed transposed), the others the tensor-core
+    kernel (tcgen05, 3xTF32, FP32 accumulation over <= 256 rows, FP64
+    partial sums).  Includes ragged row counts, widths 1..256 and a
+    misaligned view that must fall back to the generic CUDA-core kernel."""
     torch = cuda
     g, _ = wl.sbm_graph(200, 2, 0.1, 0.02, 71)
     rp, col, _ = g.csr()
@@ -244,7 +247,8 @@ def test_gram_f32_tensor_core_entry_point(cuda):
                    np.ones(4), 4)
     rng = np.random.default_rng(72)
     cases = [(1, 1, 1), (33, 7, 9), (100_003, 32, 200), (250_001, 232, 232), (70_000, 200, 32), (4097, 256, 256),
-             (65_536, 132, 164), (1000, 129, 17)]
+             (65_536, 132, 164), (1000, 129, 17), (300_001, 32, 256), (50_017, 20, 37), (80_000, 232, 31),
+             (40_000, 32, 32), (257, 3, 250)]
     for n, a, b in cases:
         X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
         Y = torch.tensor(rng.standard_normal((n, b)), dtype=torch.float32, device="cuda")
