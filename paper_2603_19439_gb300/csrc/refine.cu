@@ -43,13 +43,6 @@ __device__ __forceinline__ void df_madd(float& hi, float& lo, float ah, float al
   df_add(hi, lo, p, __fmaf_rn(al, x, pe));
 }
 
-// (hi, lo) += x (yh + yl)
-__device__ __forceinline__ void df_madd2(float& hi, float& lo, float x, float yh, float yl) {
-  const float p = __fmul_rn(x, yh);
-  const float pe = __fmaf_rn(x, yh, -p);
-  df_add(hi, lo, p, __fmaf_rn(x, yl, pe));
-}
-
 __device__ __forceinline__ void split(double v, float& h, float& l) {
   h = __double2float_rn(v);
   l = __double2float_rn(v - (double)h);
@@ -199,7 +192,23 @@ __global__ void __launch_bounds__(256) k_spmm_df_long(const int64_t* __restrict_
 // ---------------------------------------------------------------- Grams
 // part[block][i][j] = sum over the block's rows of x_i (yh_j + yl_j) (FP64),
 // Yl may be null; 32-row tiles of X and Y staged in shared memory.
+// Each dot product is accumulated by Dot2 (Ogita, Rump and Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26(6), 2005): the product
+// x yh is split exactly into p + pe by an FMA, p enters the running sum s by
+// an exact two-sum whose error goes, with pe and x yl, into a separate FP32
+// correction c; s + c is as accurate as a sum carried in twice the working
+// precision, at 11 FP32 operations per product.
 constexpr int kDfRows = 32;
+
+__device__ __forceinline__ void dot2_madd(float& s, float& c, float x, float yh, float yl) {
+  const float p = __fmul_rn(x, yh);
+  const float pe = __fmaf_rn(x, yh, -p);  // x yh = p + pe exactly
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p = t + e exactly
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, __fmaf_rn(x, yl, pe)));
+}
 
 // Thread t owns C entries (i, j) with i = t / 8 + 32 u and j = 4 (t mod 8) +
 // 32 v + 0..3 (u, v < k / 32 rounded up): per staged row, one x_i and a float4
@@ -241,10 +250,10 @@ __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ X, in
         for (int v = 0; v < NU; ++v) {
           const float4 yh = *(const float4*)&yhs[rr][tj + 32 * v];
           const float4 yl = *(const float4*)&yls[rr][tj + 32 * v];
-          df_madd2(hi[u][v][0], lo[u][v][0], xv, yh.x, yl.x);
-          df_madd2(hi[u][v][1], lo[u][v][1], xv, yh.y, yl.y);
-          df_madd2(hi[u][v][2], lo[u][v][2], xv, yh.z, yl.z);
-          df_madd2(hi[u][v][3], lo[u][v][3], xv, yh.w, yl.w);
+          dot2_madd(hi[u][v][0], lo[u][v][0], xv, yh.x, yl.x);
+          dot2_madd(hi[u][v][1], lo[u][v][1], xv, yh.y, yl.y);
+          dot2_madd(hi[u][v][2], lo[u][v][2], xv, yh.z, yl.z);
+          dot2_madd(hi[u][v][3], lo[u][v][3], xv, yh.w, yl.w);
         }
       }
     }
@@ -261,12 +270,17 @@ __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ X, in
       }
 }
 
+// C = sum of the partials in FP64: one warp per entry, lanes over blocks,
+// then a fixed shuffle tree (deterministic)
 __global__ void k_gram_df_reduce(const double* __restrict__ part, int64_t nb, int k, double* C, int64_t ldc) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= k * k) return;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)k * k) return;
   double s = 0.0;
-  for (int64_t b = 0; b < nb; ++b) s += part[b * (int64_t)k * k + e];
-  C[(int64_t)(e / k) * ldc + (e % k)] = s;
+  for (int64_t b = lane; b < nb; b += 32) s += part[b * (int64_t)k * k + w];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) C[(w / k) * ldc + (w % k)] = s;
 }
 
 // ---------------------------------------------------------------- U S
@@ -451,7 +465,7 @@ int gram_df(const float* X, int64_t ldx, const float* Yh, const float* Yl, int64
     k_gram_df<1><<<(unsigned)nb, 256, 0, s>>>(X, ldx, Yh, Yl, ldy, k, n, rpb, part);
   else
     k_gram_df<2><<<(unsigned)nb, 256, 0, s>>>(X, ldx, Yh, Yl, ldy, k, n, rpb, part);
-  k_gram_df_reduce<<<(unsigned)((k * k + 255) / 256), 256, 0, s>>>(part, nb, k, C, ldc);
+  k_gram_df_reduce<<<(unsigned)(((int64_t)k * k * 32 + 255) / 256), 256, 0, s>>>(part, nb, k, C, ldc);
   return 2;
 }
 
