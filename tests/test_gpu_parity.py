@@ -275,8 +275,8 @@ def test_gemm_f32_tensor_core_entry_point(cuda):
     against a float64 product of the same FP32 inputs: |Out - ref| <=
     4e-6 (|X| |alpha B|) + 2^-23 |beta Cin| elementwise.  Covers resident
     (a <= 64) and streamed B^T images, ragged row tails, a < 32, c up to 256,
-    an in-place update (Cin = Out), and a misaligned view that must fall back
-    to the CUDA-core kernel."""
+    beta 0 and not, in-place updates (Cin = Out), and a misaligned view that
+    must fall back to the CUDA-core kernel."""
     torch = cuda
     g, _ = wl.sbm_graph(200, 2, 0.1, 0.02, 71)
     rp, col, _ = g.csr()
@@ -285,7 +285,8 @@ def test_gemm_f32_tensor_core_entry_point(cuda):
     rng = np.random.default_rng(73)
     cases = [(1, 1, 1, 1.0, 0.0), (129, 7, 9, -1.0, 1.0), (100_003, 32, 200, -1.0, 1.0), (250_001, 200, 200, 1.0, 0.0),
              (70_000, 200, 100, 1.0, 0.0), (4097, 256, 256, 0.5, 0.0), (65_536, 132, 132, 1.0, 0.0),
-             (77_777, 164, 32, 1.0, 0.0), (1000, 33, 129, 2.0, -0.5), (40_000, 384, 64, 1.0, 0.0)]
+             (77_777, 164, 32, 1.0, 0.0), (1000, 33, 129, 2.0, -0.5), (40_000, 384, 64, 1.0, 0.0),
+             (250_000, 32, 256, 1.0, 0.0), (60_001, 32, 32, -1.0, 1.0), (9_999, 20, 37, 0.5, 2.0), (513, 3, 255, 1.0, 1.0)]
     for n, a, c, alpha, beta in cases:
         X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
         B = torch.tensor(rng.standard_normal((a, c)), dtype=torch.float64, device="cuda")
@@ -301,16 +302,16 @@ def test_gemm_f32_tensor_core_entry_point(cuda):
             bound += 2.0 ** -23 * np.abs(beta * Ch)
         err = np.abs(Out.double().cpu().numpy() - ref)
         assert np.all(err <= bound + 1e-30), (n, a, c, float((err / np.maximum(bound, 1e-30)).max()))
-    # in place: Out = Out - X B
-    n, a, c = 30_001, 32, 132
-    X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
-    B = torch.tensor(rng.standard_normal((a, c)), dtype=torch.float64, device="cuda")
-    W = torch.tensor(rng.standard_normal((n, c)), dtype=torch.float32, device="cuda")
-    W0 = W.double().cpu().numpy()
-    tr.gemm_f32(X, B, W, -1.0, 1.0, W)
-    Xh, Bh = X.double().cpu().numpy(), B.cpu().numpy()
-    err = np.abs(W.double().cpu().numpy() - (W0 - Xh @ Bh))
-    assert np.all(err <= 4e-6 * (np.abs(Xh) @ np.abs(Bh)) + 2.0 ** -23 * np.abs(W0))
+    # in place: Out = Out - X B (narrow and tensor-core kernels)
+    for n, a, c in ((30_001, 32, 132), (20_011, 48, 200)):
+        X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
+        B = torch.tensor(rng.standard_normal((a, c)), dtype=torch.float64, device="cuda")
+        W = torch.tensor(rng.standard_normal((n, c)), dtype=torch.float32, device="cuda")
+        W0 = W.double().cpu().numpy()
+        tr.gemm_f32(X, B, W, -1.0, 1.0, W)
+        Xh, Bh = X.double().cpu().numpy(), B.cpu().numpy()
+        err = np.abs(W.double().cpu().numpy() - (W0 - Xh @ Bh))
+        assert np.all(err <= 4e-6 * (np.abs(Xh) @ np.abs(Bh)) + 2.0 ** -23 * np.abs(W0)), (n, a, c)
     # misaligned X (column offset 1): CUDA-core fallback, same bound
     Z = torch.tensor(rng.standard_normal((5000, 40)), dtype=torch.float32, device="cuda")
     X = Z[:, 1:33]
