@@ -72,21 +72,37 @@ __device__ __forceinline__ void df_gather(const int32_t* __restrict__ col, const
       }
     }
     const int cnt = (int)((end - j0) < 32 ? (end - j0) : 32);
-    for (int k = 0; k < cnt; ++k) {
-      const int32_t c0 = __shfl_sync(0xffffffffu, mc, k);
-      const float* x0 = X + (int64_t)c0 * ldx;
-      if (COEF) {
-        const float ah = __shfl_sync(0xffffffffu, mh, k), al = __shfl_sync(0xffffffffu, ml, k);
+    // eight neighbours' rows are loaded before they are added (in order), so
+    // a warp keeps eight gathers in flight instead of one
+    for (int k0 = 0; k0 < cnt; k0 += 8) {
+      float xv[8][NCH], ahv[8], alv[8];
 #pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          const int c = ch * 32 + lane;
-          if (c < w) df_madd(hi[ch], lo[ch], ah, al, __ldg(x0 + c));
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        const int32_t c0 = __shfl_sync(0xffffffffu, mc, k & 31);
+        if (COEF) {
+          ahv[q] = __shfl_sync(0xffffffffu, mh, k & 31);
+          alv[q] = __shfl_sync(0xffffffffu, ml, k & 31);
         }
-      } else {
+        const float* x0 = X + (int64_t)c0 * ldx;
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
           const int c = ch * 32 + lane;
-          if (c < w) df_add(hi[ch], lo[ch], __ldg(x0 + c), 0.f);
+          xv[q][ch] = (k < cnt && c < w) ? __ldg(x0 + c) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (k0 + q >= cnt) break;  // warp-uniform
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int c = ch * 32 + lane;
+          if (c < w) {
+            if (COEF)
+              df_madd(hi[ch], lo[ch], ahv[q], alv[q], xv[q][ch]);
+            else
+              df_add(hi[ch], lo[ch], xv[q][ch], 0.f);
+          }
         }
       }
     }
@@ -286,7 +302,8 @@ __global__ void k_gram_df_reduce(const double* __restrict__ part, int64_t nb, in
 // ---------------------------------------------------------------- U S
 // Out (n x k, FP64) = X (n x k, FP32) S (k x k, FP64): one warp per row,
 // lane = output column (two columns for k > 32).
-// k <= 32: column `lane` of S (split into hi + lo) in registers.
+// k <= 32: column `lane` of S (split into hi + lo) in registers; each output
+// is a Dot2 sum over the k products.
 __global__ void __launch_bounds__(256) k_lift_df32(const float* __restrict__ X, int64_t ldx,
                                                    const double* __restrict__ S, int k, int64_t n,
                                                    double* __restrict__ Out, int64_t ldo) {
@@ -297,16 +314,27 @@ __global__ void __launch_bounds__(256) k_lift_df32(const float* __restrict__ X, 
     sh[q] = sl[q] = 0.f;
     if (q < k && lane < k) split(S[q * k + lane], sh[q], sl[q]);
   }
+  // two rows per pass (independent Dot2 chains), rows r and r + warps
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += 2 * warps) {
+    const int64_t r2 = r + warps;
+    const bool two = r2 < n;
     const float xv = lane < k ? X[r * ldx + lane] : 0.f;
-    float h = 0.f, l = 0.f;
+    const float xv2 = (two && lane < k) ? X[r2 * ldx + lane] : 0.f;
+    float h = 0.f, l = 0.f, h2 = 0.f, l2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       const float xq = __shfl_sync(0xffffffffu, xv, q);
-      if (q < k) df_madd(h, l, sh[q], sl[q], xq);
+      const float xq2 = __shfl_sync(0xffffffffu, xv2, q);
+      if (q < k) {
+        dot2_madd(h, l, xq, sh[q], sl[q]);
+        dot2_madd(h2, l2, xq2, sh[q], sl[q]);
+      }
     }
-    if (lane < k) Out[r * ldo + lane] = (double)h + (double)l;
+    if (lane < k) {
+      Out[r * ldo + lane] = (double)h + (double)l;
+      if (two) Out[r2 * ldo + lane] = (double)h2 + (double)l2;
+    }
   }
 }
 

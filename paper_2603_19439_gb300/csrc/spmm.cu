@@ -40,6 +40,30 @@ __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, co
     }
     const int cnt = (int)((end - j0) < 32 ? (end - j0) : 32);
     int k = 0;
+    if (NCH <= 2) {
+      // narrow blocks: eight neighbours' loads in flight per lane, added as
+      // two groups of four in order (the same sums as the loop below)
+      for (; k + 8 <= cnt; k += 8) {
+        int32_t cc[8];
+        T aa[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          cc[q] = __shfl_sync(0xffffffffu, mc, k + q);
+          aa[q] = __shfl_sync(0xffffffffu, ma, k + q);
+        }
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          int c = ch * 32 + lane;
+          if (c < w) {
+            T y[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) y[q] = (T)__ldg(X + (int64_t)(cc[q] - col_lo) * ldx + c);
+            acc.v[ch] += aa[0] * y[0] + aa[1] * y[1] + aa[2] * y[2] + aa[3] * y[3];
+            acc.v[ch] += aa[4] * y[4] + aa[5] * y[5] + aa[6] * y[6] + aa[7] * y[7];
+          }
+        }
+      }
+    }
     for (; k + 4 <= cnt; k += 4) {
       int32_t c0 = __shfl_sync(0xffffffffu, mc, k), c1 = __shfl_sync(0xffffffffu, mc, k + 1);
       int32_t c2 = __shfl_sync(0xffffffffu, mc, k + 2), c3 = __shfl_sync(0xffffffffu, mc, k + 3);
