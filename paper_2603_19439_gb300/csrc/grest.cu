@@ -1534,6 +1534,7 @@ grest_status grest_checkpoint(grest_ctx* c, void* buf, int64_t* bytes) {
   if (top > 0) CK(cudaMemcpyAsync(arena.data(), g.col, sizeof(int32_t) * top, cudaMemcpyDeviceToHost, s));
   if (has_val && top > 0) CK(cudaMemcpyAsync(varena.data(), g.val, sizeof(double) * top, cudaMemcpyDeviceToHost, s));
   uint8_t* b = static_cast<uint8_t*>(buf);
+  memset(b, 0, L.total);  // padding bytes too: equal states give equal checkpoints
   CK(cudaMemcpyAsync(b + L.deg, g.deg, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpy2DAsync(b + L.U, sizeof(double) * K, c->U, sizeof(double) * c->ldu, sizeof(double) * K, n,
                        cudaMemcpyDeviceToHost, s));
@@ -1562,7 +1563,6 @@ grest_status grest_checkpoint(grest_ctx* c, void* buf, int64_t* bytes) {
   h.has_val = has_val ? 1 : 0;
   h.cfg = c->cfg;
   memcpy(b, &h, sizeof(h));
-  memset(b + L.live + n, 0, L.total - (L.live + n));
   *bytes = (int64_t)L.total;
   return GREST_OK;
 }

@@ -75,6 +75,10 @@ def test_restore_continues_bit_identically(cuda, precision, op, weighted):
     s_b = torch.cuda.Stream()
     tr2 = G.Tracker.restore(blob, stream=s_b.cuda_stream)
     same(tr, tr2, "right after restore")
+    # the checkpoint is a function of the state: taken again, and taken from
+    # the restored context (whose slack layout differs), it is the same bytes
+    assert tr.checkpoint() == blob
+    assert tr2.checkpoint() == blob
     assert tr2.stats()["step"] == 3
     for t, b in enumerate(batches[3:]):
         sa = tr.update(b)
