@@ -196,17 +196,17 @@ def test_degenerate_batches(cuda):
     tr.close()
 
 
-def test_chung_lu_200k_nlap_one_step(cuda):
+def test_chung_lu_200k_nlap_steps(cuda):
     """Full-size normalized-Laplacian workload (n = 200,000, gamma 2.5, mean
     degree 16, K = 16, +0.5% nodes by preferential attachment, -0.1% edges):
-    one RSVD step against the oracle."""
-    g0, batches = wl.chung_lu_stream(200_000, 2.5, 16, 1, 0.005, 8, 0.001, seed=20260305, lcc=True)
+    three consecutive RSVD steps, each against the oracle."""
+    g0, batches = wl.chung_lu_stream(200_000, 2.5, 16, 3, 0.005, 8, 0.001, seed=20260305, lcc=True)
     tr, st, ocfg = U.make_pair(g0, 16, O.OP_NLAP, dense_limit=0)
-    b = batches[0]
-    st, info = O.grest_step(st, b, ocfg)
-    s = tr.update(b)
-    assert s["mode"] == 4 and s["m"] == info.m
-    U.compare(tr, st, info, O.OP_NLAP, 16, "cl200k")
+    for t, b in enumerate(batches):
+        st, info = O.grest_step(st, b, ocfg)
+        s = tr.update(b)
+        assert s["mode"] == 4 and s["m"] == info.m, t
+        U.compare(tr, st, info, O.OP_NLAP, 16, f"cl200k step {t}")
     tr.close()
 
 
