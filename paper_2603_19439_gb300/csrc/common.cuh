@@ -38,20 +38,32 @@ __device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(
 // host threads at once, so it only ever grows (under one lock): a launch with
 // fewer bytes stays valid whatever another thread reserves meanwhile.
 std::mutex& smem_attr_mutex();
+// Bytes already reserved for (kernel, device), read and written under
+// smem_attr_mutex(); nullptr when the table is full (then every call asks the
+// driver).
+size_t* smem_reserved_slot(const void* kernel, int dev);
 
 template <typename K>
 inline bool reserve_dynamic_smem(K kernel, size_t bytes) {
-  int dev = 0, optin = 0;
+  const void* k = reinterpret_cast<const void*>(kernel);
+  int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
   std::lock_guard<std::mutex> lock(smem_attr_mutex());
+  size_t* slot = smem_reserved_slot(k, dev);
+  if (slot && bytes <= *slot) return true;  // reserved before: no driver call
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return false;
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return false;
   if (bytes + fa.sharedSizeBytes > (size_t)optin) return false;
   if (bytes > (size_t)fa.maxDynamicSharedSizeBytes &&
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
     cudaGetLastError();
     return false;
+  }
+  if (slot) {
+    const size_t now = bytes > (size_t)fa.maxDynamicSharedSizeBytes ? bytes : (size_t)fa.maxDynamicSharedSizeBytes;
+    if (now > *slot) *slot = now;
   }
   return true;
 }

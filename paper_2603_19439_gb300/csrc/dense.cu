@@ -542,7 +542,10 @@ template <typename T>
 __global__ void k_zero_dead(T* X, int64_t ldx, int w, const uint8_t* live, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * w; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = e / w;
-    if (!live[r]) X[r * ldx + (e % w)] = (T)0;
+    if (!live[r]) {
+      T& x = X[r * ldx + (e % w)];
+      if (x != (T)0) x = (T)0;  // zeros of either sign stay as they are (restored states keep their bytes)
+    }
   }
 }
 

@@ -45,6 +45,21 @@ std::mutex& smem_attr_mutex() {
   static std::mutex mu;
   return mu;
 }
+
+size_t* smem_reserved_slot(const void* kernel, int dev) {  // caller holds smem_attr_mutex()
+  struct Slot {
+    const void* k;
+    int dev;
+    size_t bytes;
+  };
+  static Slot table[256];
+  static int used = 0;
+  for (int i = 0; i < used; ++i)
+    if (table[i].k == kernel && table[i].dev == dev) return &table[i].bytes;
+  if (used == 256) return nullptr;
+  table[used] = Slot{kernel, dev, 0};
+  return &table[used++].bytes;
+}
 }  // namespace grest
 
 struct grest_ctx {

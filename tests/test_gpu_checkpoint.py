@@ -25,6 +25,13 @@ def cuda():
     return torch
 
 
+def first_diff(a, b):
+    if len(a) != len(b):
+        return f"lengths {len(a)} and {len(b)}"
+    d = np.flatnonzero(np.frombuffer(a, np.uint8) != np.frombuffer(b, np.uint8))
+    return f"{d.size} bytes differ, the first at offset {d[0]} of {len(a)}" if d.size else "equal"
+
+
 def same(tr_a, tr_b, where):
     Ua, tha, la = tr_a.embedding()
     Ub, thb, lb = tr_b.embedding()
@@ -77,8 +84,10 @@ def test_restore_continues_bit_identically(cuda, precision, op, weighted):
     same(tr, tr2, "right after restore")
     # the checkpoint is a function of the state: taken again, and taken from
     # the restored context (whose slack layout differs), it is the same bytes
-    assert tr.checkpoint() == blob
-    assert tr2.checkpoint() == blob
+    again = tr.checkpoint()
+    assert again == blob, first_diff(again, blob)
+    restored = tr2.checkpoint()
+    assert restored == blob, first_diff(restored, blob)
     assert tr2.stats()["step"] == 3
     for t, b in enumerate(batches[3:]):
         sa = tr.update(b)
