@@ -303,13 +303,16 @@ grest_status grest_gram(grest_ctx *ctx, const double *X, int64_t ldx, int32_t a,
 
 /*
  * C = X^T Y for FP32 device blocks (X n x a, Y n x b, row-major, ldx, ldy),
- * FP64 result C (a x b, ldc), a, b <= 256: the Gram kernel of the
- * mixed-precision step.  On sm_100-class GPUs it runs on the tensor cores
- * (tcgen05 kind::tf32, each value split into two TF32 parts, three products,
- * FP32 accumulation over at most 256 rows, FP64 partial sums); blocks whose
- * base address or leading dimension is not 16-byte aligned use a CUDA-core
- * kernel with the same accumulation rule.  Runs on the context's stream and
- * uses its scratch; returns when C is complete.
+ * FP64 result C (a x b, ldc), a, b <= 256: the Gram kernels of the
+ * mixed-precision step.  When min(a, b) <= 32 (the projections X_bar^T Y) a
+ * CUDA-core kernel computes it (exact FP32 products inside the FMA, FP32 sums
+ * over at most 256 rows added into double-float, FP64 partial sums); wider
+ * products run on the tensor cores (tcgen05 kind::tf32, each value split into
+ * two TF32 parts, three products, FP32 accumulation over at most 256 rows,
+ * FP64 partial sums).  Blocks whose base address or leading dimension is not
+ * 16-byte aligned use a generic CUDA-core kernel with the same accumulation
+ * rule.  Runs on the context's stream and uses its scratch; returns when C
+ * is complete; GREST_ERR_TIMEOUT if a device-side wait gave up.
  */
 grest_status grest_gram_f32(grest_ctx *ctx, const float *X, int64_t ldx, int32_t a, const float *Y, int64_t ldy,
                             int32_t b, int64_t n, double *C, int64_t ldc);

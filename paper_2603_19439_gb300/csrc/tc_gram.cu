@@ -1,6 +1,7 @@
-// Tensor-core Gram product C = X^T Y for tall-skinny FP32 blocks (the
-// projection and CholQR Gram matrices of the mixed-precision step and
-// H = Z^T (M Z) of Alg. 1), on tcgen05 with accumulators in tensor memory.
+// Tensor-core Gram product C = X^T Y for tall-skinny FP32 blocks (the CholQR
+// Gram matrices of the mixed-precision step and H = Z^T (M Z) of Alg. 1; the
+// products with a side of at most 32 columns go to narrow_gram.cu), on
+// tcgen05 with accumulators in tensor memory.
 //
 // Precision: each FP32 value x is split into x_hi = tf32(x) and
 // x_lo = tf32(x - x_hi) (round to nearest), and x y ~ x_hi y_hi + x_hi y_lo +
