@@ -183,7 +183,7 @@ void worker(grest_server* sv) {
       lk.lock();
       sv->freeing -= g.bytes;
       if (s0 == GREST_OK) {
-        g.ckpt.swap(blob);
+        if (!g.removed) g.ckpt.swap(blob);  // removed while it was being evicted: nothing to keep
         g.ctx = nullptr;
         g.stream = nullptr;
         g.resident = false;
