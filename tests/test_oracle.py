@@ -4,6 +4,7 @@ Each test checks the oracle against something other than itself: the worked
 example of Fig. 1, closed-form spectra, brute-force dense eigendecompositions,
 Cauchy interlacing, the Rayleigh-Ritz optimality of Thm. 1, the Galerkin
 condition, Props. 1, 3 and 4, RSVD exactness for low-rank Delta_2 (Sec. 3.5),
+basis independence of the orthonormalization (pivoted QR against CholQR2),
 and an independent Philox implementation (numpy's).
 """
 import json
@@ -297,6 +298,33 @@ def test_ritz_vectors_beat_other_bases_of_the_subspace():
         P2 = Z @ Qr
         D = np.diag(np.diag(P2.T @ M @ P2))
         assert np.linalg.norm(M @ P2 - P2 @ D, 2) >= best - 1e-12
+
+
+def test_orth_against_matches_cholqr2_basis():
+    """Basis independence (the device path orthonormalizes by CholQR2, the
+    oracle by pivoted QR): Q = orth_against(X, V) spans the same space as a
+    Cholesky-based basis of (I - X X^T) V built here from its definition,
+    is orthonormal and orthogonal to X, and both bases give the same Ritz
+    values of M on [X, Q]."""
+    _, st2, info = stream_step()
+    M = info.M
+    rng = np.random.default_rng(5)
+    n = M.shape[0]
+    X = np.linalg.qr(rng.standard_normal((n, 6)))[0]
+    V = rng.standard_normal((n, 9))
+    Q, _, _ = O.orth_against(X, V, 1e-10)
+    assert Q.shape[1] == 9
+    W = V - X @ (X.T @ V)
+    W = W - X @ (X.T @ W)
+    for _ in range(2):  # CholQR2: W <- W R^-1 with R^T R = W^T W
+        R = np.linalg.cholesky(W.T @ W).T
+        W = np.linalg.solve(R.T, W.T).T
+    assert np.abs(Q.T @ Q - np.eye(9)).max() < 1e-13
+    assert np.abs(X.T @ Q).max() < 1e-13
+    assert np.abs(Q @ Q.T - W @ W.T).max() < 1e-12
+    ritz = lambda B: np.linalg.eigvalsh(B.T @ (M @ B))
+    ra, rb = ritz(np.hstack([X, Q])), ritz(np.hstack([X, W]))
+    assert np.abs(ra - rb).max() <= 1e-12 * np.abs(ra).max()
 
 
 # ------------------------------------------------------------ Props 1, 3, 4
