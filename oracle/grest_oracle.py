@@ -24,7 +24,7 @@ order and notation, in float64 with NumPy/SciPy library primitives
   Sec. 5 (downstream task)    subgraph centrality X_K exp(Lambda_K) X_K^T 1, top-J
                               sets and their overlap
 
-Readings where the paper is silent (each is restated in the design doc):
+Readings where the paper is silent, ambiguous or garbled:
   R1  EXACT projection (Eq. main2) is the default; LOWRANK (Eq. main3) is a mode.
   R2  default W block is P_perp(M_new X_bar) = P_perp(Delta X_bar) + P_perp(A_bar X_bar);
       it equals the paper's P_perp(Delta X_bar) when X holds exact eigenvectors.
