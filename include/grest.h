@@ -172,14 +172,21 @@ grest_status grest_config_default(grest_config *cfg, int32_t k);
  * undirected edge present in both rows), val (nullable; positive weights,
  * symmetric).  U0 (n x k row-major, orthonormal columns) and theta0 (k) are
  * Alg. 2's initial leading pairs from any eigensolver.  When both are NULL
- * the library computes them on the device: FP64 block Krylov (blocks of
- * k + max(8, k/2) columns, full reorthogonalization, Rayleigh-Ritz and
- * explicit restarts) until every tracked residual ||M x - theta x|| is at
- * most 1e-11 |theta_1| (GREST_ERR_NUMERIC if 100 restarts do not get there);
+ * the library computes them on the device in FP64: block Krylov rounds
+ * (blocks of k + max(8, k/2) columns, full reorthogonalization,
+ * Rayleigh-Ritz) until the block is close, then Chebyshev-filtered subspace
+ * iteration with the converged pairs locked (Zhou and Saad's scaled
+ * recurrence), until every tracked residual ||M x - theta x|| is at most
+ * 1e-11 |theta_1| (GREST_ERR_NUMERIC if 100 rounds do not get there);
  * graphs of at most 288 nodes are solved densely.  Device memory for this
  * is taken and released inside grest_init (about n * 600 doubles).  One NULL
  * and one not -> GREST_ERR_INVALID_ARG.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ * Errors: GREST_ERR_INVALID_ARG (null pointers, sizes, configuration fields,
+ * a malformed CSR: decreasing row pointers, out-of-range or duplicate
+ * columns, self loops, non-positive weights), GREST_ERR_UNSUPPORTED (mode
+ * combinations listed with GREST_PROJ_* above), GREST_ERR_OOM, GREST_ERR_CUDA;
+ * *out is NULL on any error.
  */
 grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowptr,
                         const int32_t *col, const double *val, const double *U0,
@@ -192,6 +199,17 @@ grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowpt
  * rank-K surrogate (Eq. main3), solve H F = F Theta, set X = Z F_K,
  * Lambda = Theta_K.  Returns when the step has finished on the device.
  * stats may be NULL.
+ * Errors: GREST_ERR_INVALID_ARG (null context or update, negative counts,
+ * null arrays for nonzero counts, weights for an unweighted context);
+ * GREST_ERR_INVALID_UPDATE (the batch breaks Sec. 2's definition of Delta:
+ * an existing edge inserted, a missing edge deleted, a duplicate, a self
+ * loop, an id out of range or removed) with the context unchanged;
+ * GREST_ERR_CAPACITY (node or edge capacity exceeded) with the context
+ * unchanged; GREST_ERR_UNSUPPORTED (node removal in the DELTA / LOWRANK
+ * modes; an exact new-node block wider than L + P); GREST_ERR_NUMERIC (fewer
+ * than k Ritz pairs or a Cholesky breakdown: the graph is updated, the
+ * previous pairs are kept); GREST_ERR_TIMEOUT (a bounded device-side wait
+ * gave up); GREST_ERR_OOM, GREST_ERR_CUDA.
  */
 grest_status grest_apply_update(grest_ctx *ctx, const grest_update *upd, grest_stats *stats);
 
