@@ -47,6 +47,26 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values of x (every rank gets it): the
+    slowest replica's time sets the whole job's time."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return tt.item()
+
+
+def replica_rate(t_local, steps, world, device="cuda"):
+    """(job time, whole-job updates/s) of `world` replicas that each applied
+    `steps` updates, rank r in t_local seconds: every replica's updates count,
+    over the slowest replica's time."""
+    t = max_over_ranks(t_local, world, device)
+    return t, world * steps / t
+
+
 def workload_desc(n):
     return (f"Chung-Lu power-law stream n={n:,} gamma={WL['gamma']} mean_degree={WL['mean_degree']} adjacency "
             f"K={WL['k']}, +{WL['grow_frac'] * 100:.1f}% nodes x {WL['edges_per_new_node']} PA edges and "
@@ -340,26 +360,18 @@ def run_grest(args):
         lat = sorted(a.elapsed_time(b) for a, b in ev)
         return t, lat, prof, last, clk
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        tt = torch.tensor([x], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return tt.item()
-
     if args.mixed_only:
         t64 = lat64 = prof64 = last64 = clk64 = None
         main = None
     else:
         t64, lat64, prof64, last64, clk64 = timed(tr64)
-        t64 = max_over_ranks(t64)
+        t64 = max_over_ranks(t64, world)
         main = dict(t=t64, lat=lat64, prof=prof64, last=last64, clk=clk64, tr=None, precision="fp64")
     tr64.close()
     res32 = None
     if tr32 is not None:
         t32, lat32, prof32, last32, clk32 = timed(tr32)
-        t32 = max_over_ranks(t32)
+        t32 = max_over_ranks(t32, world)
         res32 = dict(t=t32, lat=lat32, prof=prof32, last=last32, clk=clk32)
         main = dict(res32, precision="mixed")
     # ---- end to end through the public call from pinned host memory (headline path)
@@ -381,7 +393,7 @@ def run_grest(args):
         d2h += theta_h.nbytes
     e3.record(stream)
     barrier()
-    t_e2e = max_over_ranks(e2.elapsed_time(e3) * 1e-3)
+    t_e2e = max_over_ranks(e2.elapsed_time(e3) * 1e-3, world)
     if tr32 is not None:
         tr32.close()
     else:

@@ -27,3 +27,42 @@ def test_reference_arm_json_line():
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("Chung-Lu power-law stream n=1,000,000")
+
+
+def _replica_worker(rank, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=2)
+    t_local = [1.5, 2.5][rank]
+    t, rate = bench.replica_rate(t_local, 10, 2, device="cpu")
+    m = bench.max_over_ranks(float(rank), 2, device="cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+        json.dump({"t": t, "rate": rate, "m": m}, f)
+
+
+def test_replica_rate_over_two_gloo_ranks(tmp_path):
+    """The N > 1 timing rule on two CPU ranks (gloo): every rank gets the
+    slowest rank's time, and the whole-job rate counts both ranks' updates
+    over that time."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_replica_worker, args=(port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for r in range(2):
+        d = json.load(open(tmp_path / f"r{r}.json"))
+        assert d["t"] == 2.5 and d["rate"] == 2 * 10 / 2.5 and d["m"] == 1.0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under a multi-rank launch only rank 0 runs the oracle and prints; the
+    other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1"], cwd=ROOT,
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
