@@ -121,3 +121,38 @@ def test_checkpoint_calls_check_arguments_without_gpu(lib):
     assert L.grest_server_counters(None, None, None, None) == 1
     with pytest.raises(grest.GrestError):
         grest.checkpoint_embedding(bytes(junk))
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/grest.h compiles as C99 with warnings as errors, and a C
+    program links against libgrest.so and calls the host-only entry points
+    (defaults, status strings, argument checks) without a GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "grest.h"
+int main(void) {
+  grest_config cfg;
+  if (grest_config_default(&cfg, 16) != GREST_OK) return 1;
+  if (cfg.k != 16 || cfg.L != 100 || cfg.P != 100 || cfg.precision != GREST_FP64) return 2;
+  if (strcmp(grest_status_str(GREST_OK), "ok") != 0) return 3;
+  grest_ctx *ctx = NULL;
+  if (grest_init(NULL, 0, NULL, NULL, NULL, NULL, NULL, NULL, &ctx) != GREST_ERR_INVALID_ARG || ctx) return 4;
+  if (grest_restore(NULL, 0, NULL, &ctx) != GREST_ERR_INVALID_ARG) return 5;
+  printf("abi ok\n");
+  return 0;
+}
+''')
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib._name)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", libdir, "-lgrest", f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "abi ok", (r.returncode, r.stdout, r.stderr)
