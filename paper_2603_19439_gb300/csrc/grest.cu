@@ -1229,8 +1229,10 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   const int cm = c->cmax, mm = c->mmax;
   IK(dalloc(&c->Cm, 64 * 64)); IK(dalloc(&c->Cv, (int64_t)64 * (cm + 64))); IK(dalloc(&c->G, (int64_t)cm * cm));
   IK(dalloc(&c->T, (int64_t)cm * cm)); IK(dalloc(&c->H, (int64_t)mm * mm)); IK(dalloc(&c->F, (int64_t)mm * 64));
-  IK(dalloc(&c->XtM, (int64_t)64 * c->ldq)); IK(dalloc(&c->Gs, (int64_t)c->q * c->q));
-  IK(dalloc(&c->Uh, (int64_t)c->q * c->q)); IK(dalloc(&c->ritz, mm)); IK(dalloc(&c->th_new, 64));
+  // Gs, Uh: the RSVD's q x q problem and the refinement's K x K products
+  const int64_t qk = std::max(c->q, c->K);
+  IK(dalloc(&c->XtM, (int64_t)64 * c->ldq)); IK(dalloc(&c->Gs, qk * qk));
+  IK(dalloc(&c->Uh, qk * qk)); IK(dalloc(&c->ritz, mm)); IK(dalloc(&c->th_new, 64));
   IK(dalloc(&c->tmpk, 256)); IK(dalloc(&c->info, 64)); IK(dalloc(&c->resn, 64));
   c->part_cap = 8'000'000;  // FP64 partial sums of the split-K Gram kernels (64 MB)
   IK(dalloc(&c->part, c->part_cap)); IK(dalloc(&c->ipart, 304 * 64));

@@ -116,3 +116,20 @@ def test_mixed_check_flag_reports_fp64_residuals(cuda):
     r = residuals(M, Ug, thg).max() / abs(thg[0])
     assert abs(s["max_residual"] - r) <= 1e-9
     tr.close()
+
+
+def test_mixed_more_than_32_pairs(cuda):
+    """K = 40 tracked pairs with L + P = 32 < K: the refinement's K x K
+    products and double-float kernels in their two-columns-per-lane forms,
+    the projections on the tensor-core Gram, on a power-law stream with the
+    RSVD new-node block (normalized Laplacian: algebraic ordering, so no
+    +-theta near-ties at the K boundary)."""
+    g0, batches = wl.chung_lu_stream(3000, 2.4, 14, 2, 0.02, 6, 0.002, seed=21, lcc=True)
+    tr, st, ocfg = U.make_pair(g0, 40, O.OP_NLAP, L=20, P=12, seed=3, precision=G.MIXED, drop_tol=1e-3)
+    ocfg.drop_tol = 1e-3
+    for t, b in enumerate(batches):
+        st, info = O.grest_step(st, b, ocfg)
+        s = tr.update(b)
+        assert s["mode"] == 4 and s["m"] == info.m
+        compare_mixed(tr, st, info, O.OP_NLAP, 40, f"mixed K=40 step {t}")
+    tr.close()
