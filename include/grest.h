@@ -206,10 +206,12 @@ grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowpt
  * loop, an id out of range or removed) with the context unchanged;
  * GREST_ERR_CAPACITY (node or edge capacity exceeded) with the context
  * unchanged; GREST_ERR_UNSUPPORTED (node removal in the DELTA / LOWRANK
- * modes; an exact new-node block wider than L + P); GREST_ERR_NUMERIC (fewer
- * than k Ritz pairs or a Cholesky breakdown: the graph is updated, the
- * previous pairs are kept); GREST_ERR_TIMEOUT (a bounded device-side wait
- * gave up); GREST_ERR_OOM, GREST_ERR_CUDA.
+ * modes; an exact new-node block wider than L + P); GREST_ERR_NUMERIC: the
+ * graph is updated, and either the basis had fewer than k directions (the
+ * tracked pairs are then the previous ones, padded with zero rows for the
+ * new nodes) or the second CholQR pass lost rank (the pairs are updated from
+ * the smaller basis); GREST_ERR_TIMEOUT (a bounded device-side wait gave
+ * up); GREST_ERR_OOM, GREST_ERR_CUDA.
  */
 grest_status grest_apply_update(grest_ctx *ctx, const grest_update *upd, grest_stats *stats);
 

@@ -1368,8 +1368,10 @@ static grest_status apply_update_impl(grest_ctx* c, const grest_update* u, grest
     return map_dev_err(*c->h_err);
   }
   c->nnz = c->h_scal[5];
-  // committed: the graph now has N + S ids
+  // committed: the graph now has N + S ids; until the step's pairs replace
+  // them, the tracked pairs are the padded previous ones [X; 0]
   c->g.n = N + S;
+  if (S > 0) CK(cudaMemset2DAsync(c->U + N * c->ldu, sizeof(double) * c->ldu, 0, sizeof(double) * c->K, S, s));
   c->launches += graph_refresh_derived(c->g, c->gw, N + S, s);
   c->stats.rank_y = 0;
   st = c->cfg.precision == GREST_MIXED ? step_t<float>(c, N, S, u->n_del_nodes > 0)
