@@ -156,3 +156,40 @@ int main(void) {
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "abi ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_null_handles_rejected_without_gpu(lib):
+    """Every entry point that takes a context, batch or server handle returns
+    GREST_ERR_INVALID_ARG (1) for NULL before any device work, and the
+    destroy calls accept NULL."""
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    n, m, t, d = i64(), i32(), i64(), i32()
+    st = grest.Stats()
+    u = grest.Update()
+    assert L.grest_apply_update(None, ctypes.byref(u), None) == 1
+    assert L.grest_sync(None) == 1
+    assert L.grest_get_embedding(None, None, None, None, ctypes.byref(n), 0) == 1
+    assert L.grest_set_embedding(None, None, None, 0) == 1
+    assert L.grest_get_ritz_values(None, None, ctypes.byref(m)) == 1
+    assert L.grest_get_stats(None, ctypes.byref(st)) == 1
+    assert L.grest_centrality(None, 0, None, None, None, 0) == 1
+    assert L.grest_apply_operator(None, None, 1, None, 1, 1) == 1
+    assert L.grest_gram(None, None, 1, 1, None, 1, 1, 1, None, 1) == 1
+    assert L.grest_gram_f32(None, None, 1, 1, None, 1, 1, 1, None, 1) == 1
+    assert L.grest_gemm_f32(None, 1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None, 1) == 1
+    assert L.grest_gram_noalloc(None, 1, 1, None, 1, 1, 1, None, 1, None) == 1
+    assert L.grest_get_device_bytes(None, ctypes.byref(n)) == 1
+    assert L.grest_batch_apply_updates(None, None, None, None) == 1
+    assert L.grest_server_create(0, 0, ctypes.byref(ctypes.c_void_p())) == 1
+    assert L.grest_server_add_graph(None, None, 1, None, None, None, None, None, ctypes.byref(d)) == 1
+    assert L.grest_server_submit(None, 0, ctypes.byref(u), ctypes.byref(t)) == 1
+    assert L.grest_server_wait(None, 0, None, None, None, None) == 1
+    assert L.grest_server_poll(None, 0, ctypes.byref(d)) == 1
+    assert L.grest_server_remove_graph(None, 0) == 1
+    assert L.grest_server_get_embedding(None, 0, None, None, None, ctypes.byref(n)) == 1
+    assert L.grest_server_resident(None, None, None) == 1
+    L.grest_destroy(None)
+    L.grest_batch_destroy(None)
+    L.grest_server_destroy(None)
