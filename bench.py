@@ -447,9 +447,11 @@ def run_grest(args):
 
 
 def run_kernels(args):
-    """--kernels: CUDA-event times of the mixed path's tensor-core Gram and GEMM
-    entry points (grest_gram_f32, grest_gemm_f32) on n x w FP32 blocks of the
-    widths one 1M-node update uses; one JSON line (not the bench contract's)."""
+    """--kernels: CUDA-event times of the mixed path's Gram and GEMM entry
+    points (grest_gram_f32, grest_gemm_f32; each picks its kernel by shape:
+    the narrow CUDA-core Gram for a side of at most 32 columns, else the
+    tensor cores) on n x w FP32 blocks of the widths one 1M-node update uses;
+    one JSON line (not the bench contract's)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -711,7 +713,7 @@ def main():
     ap.add_argument("--evict", action="store_true",
                     help="--serve: checkpoint idle graphs to host memory when a waiting graph does not fit")
     ap.add_argument("--kernels", action="store_true",
-                    help="time the tensor-core Gram / GEMM entry points at the step's widths instead")
+                    help="time the mixed path's Gram / GEMM entry points at the step's widths instead")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")
     ap.add_argument("--mixed-only", action="store_true", help="skip the FP64 path")
     ap.add_argument("--nodes", type=int, default=WL["n"],
