@@ -20,7 +20,7 @@ def lib():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "grest.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(grest_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(grest_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -28,6 +28,12 @@ def test_exports_every_declared_symbol(lib):
     assert len(names) >= 10
     for n in names:
         assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    """The ctypes binding declares exactly the header's entry points."""
+    from paper_2603_19439_gb300 import grest
+    assert sorted(grest.EXPORTS) == header_functions()
 
 
 def test_status_strings_and_defaults(lib):
