@@ -1,22 +1,30 @@
 #!/usr/bin/env python3
-"""G-REST update throughput on the 1M-node power-law stream (one JSON line).
+"""G-REST update throughput on an evolving power-law graph (one JSON line).
 
-Workload (synthetic, seeded): Chung-Lu power-law graph, n = 1,000,000 nodes,
-degree exponent 2.3, mean degree 32, adjacency operator, K = 32 tracked pairs;
-each update adds 0.5% new nodes with 16 preferential-attachment edges each
-and deletes 0.1% of the edges uniformly (so S = 5,000 > L+P = 200 and the
-RSVD new-node basis of Sec. 3.5 is used, L = P = 100).  One step = one full
-G-REST update (graph update, basis, projection, eigensolve, lift) through the
-library's C ABI.
+Default workload (synthetic, seeded): Chung-Lu power-law graph,
+n = 1,000,000 nodes, degree exponent 2.3, mean degree 32, adjacency operator,
+K = 32 tracked pairs; each update adds 0.5% new nodes with 16
+preferential-attachment edges each and deletes 0.1% of the edges uniformly
+(so S = 5,000 > L+P = 200 and the RSVD new-node basis of Sec. 3.5 is used,
+L = P = 100).  One step = one full G-REST update (graph update, basis,
+projection, eigensolve, lift, and for the mixed arms the FP64 refinement)
+through the library's C ABI.  Three arms run the same stream from the same
+initial pairs: FP64, MIXED (the headline: FP32 blocks on the tensor cores,
+FP64 Cholesky, eigensolves and refinement) and MIXED_FAST (FP32 projected
+problems, double-float refinement); the mixed arms' accuracy against the
+FP64 arm is part of the line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grest|reference]
+                    [--workload cl1m|cl200k|sbm2k]
 
 `value` times K steps with the update batches already resident in device
 memory; `e2e` times K further steps through the same public call with the
 batches in pinned host memory (host->device copies inside the timed region)
-and a device->host read of the updated eigenvalues after every step.  Under
-torchrun every rank runs an independent replica (the update does not shard;
-there is no collective on the data path) and rank 0 prints the line.
+and a device->host read of the updated embedding (U and theta) after every
+step.  Under torchrun every rank runs an independent replica (the update
+does not shard; there is no collective on the data path) and rank 0 prints
+the line.  --workload cl200k / sbm2k run the other two single-graph
+workloads (FP64, with the oracle timed beside them).
 """
 import argparse
 import json
@@ -35,7 +43,21 @@ sys.path.insert(0, ROOT)
 METRIC = "G-REST updates/s at n=1M,k=32: mixed vs FP64 GPU path; p50/p99 update latency"
 WL = dict(n=1_000_000, gamma=2.3, mean_degree=32, k=32, grow_frac=0.005, edges_per_new_node=16,
           delete_frac=0.001, seed=20260306, L=100, P=100)
-SAMPLE_N = 100_000  # CPU-oracle sample of the same family
+# the three single-graph workloads: the 1M-node adjacency stream (the
+# headline), the 200k-node normalized-Laplacian stream and the SBM stream
+WORKLOADS = {
+    "cl1m": dict(kind="power_law", n=1_000_000, gamma=2.3, mean_degree=32, k=32, op=0, lcc=False, grow_frac=0.005,
+                 edges_per_new_node=16, delete_frac=0.001, seed=20260306, L=100, P=100,
+                 precisions=("fp64", "mixed", "mixed_fast"), metric=METRIC),
+    "cl200k": dict(kind="power_law", n=200_000, gamma=2.5, mean_degree=16, k=16, op=2, lcc=True, grow_frac=0.005,
+                   edges_per_new_node=8, delete_frac=0.001, seed=20260305, L=100, P=100, precisions=("fp64",),
+                   metric="G-REST updates/s, Chung-Lu n=200k normalized Laplacian k=16, FP64 GPU path"),
+    "sbm2k": dict(kind="sbm", n=2000, n_comm=4, p_in=0.05, p_out=0.005, k=8, op=0, n_new=50, n_rand=200,
+                  seed=20260304, L=100, P=100, precisions=("fp64",),
+                  metric="G-REST updates/s, SBM n=2,000 4 communities k=8, FP64 GPU path"),
+}
+# seconds of timed oracle work per CPU leg (bounded sample of the workload)
+CPU_BUDGET_S = 60.0
 # pivots of an FP32-accumulated Gram are resolved only to ~5e-4 R_00, so the mixed path drops below 1e-3
 MIXED_DROP_TOL = 1e-3
 # FP64 peak derived from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
@@ -67,17 +89,43 @@ def replica_rate(t_local, steps, world, device="cuda"):
     return t, world * steps / t
 
 
-def workload_desc(n):
-    return (f"Chung-Lu power-law stream n={n:,} gamma={WL['gamma']} mean_degree={WL['mean_degree']} adjacency "
-            f"K={WL['k']}, +{WL['grow_frac'] * 100:.1f}% nodes x {WL['edges_per_new_node']} PA edges and "
-            f"-{WL['delete_frac'] * 100:.1f}% edges per step, RSVD L=P={WL['L']}")
+OP_NAMES = {0: "adjacency", 1: "shifted Laplacian", 2: "normalized Laplacian"}
 
 
-def make_workload(n, steps, seed):
+def workload_desc(w, n=None):
+    n = n or w["n"]
+    if w["kind"] == "sbm":
+        return (f"SBM stream n={n:,} {w['n_comm']} equal communities p_in={w['p_in']} p_out={w['p_out']} "
+                f"{OP_NAMES[w['op']]} K={w['k']}, +{w['n_new']} nodes and +{w['n_rand']} random edges per step, "
+                f"exact new-node block")
+    return (f"Chung-Lu power-law stream n={n:,} gamma={w['gamma']} mean_degree={w['mean_degree']} "
+            f"{OP_NAMES[w['op']]}{' (largest component)' if w['lcc'] else ''} K={w['k']}, "
+            f"+{w['grow_frac'] * 100:.1f}% nodes x {w['edges_per_new_node']} PA edges and "
+            f"-{w['delete_frac'] * 100:.1f}% edges per step, RSVD L=P={w['L']}")
+
+
+def make_workload(w, steps, seed, n=None):
+    """(initial graph, `steps` update batches) of workload w."""
     from paper_2603_19439_gb300 import workloads as wl
-    g, batches = wl.power_law_workload(n, WL["gamma"], WL["mean_degree"], steps, WL["grow_frac"],
-                                       WL["edges_per_new_node"], WL["delete_frac"], seed)
-    return g, batches
+    if w["kind"] == "sbm":
+        return wl.sbm_stream(seed=seed, n0=n or w["n"], n_comm=w["n_comm"], p_in=w["p_in"], p_out=w["p_out"],
+                             steps=steps, n_new=w["n_new"], n_rand=w["n_rand"])
+    return wl.power_law_workload(n or w["n"], w["gamma"], w["mean_degree"], steps, w["grow_frac"],
+                                 w["edges_per_new_node"], w["delete_frac"], seed, lcc=w["lcc"])
+
+
+def batches_needed(steps, warmup):
+    """Batches one bench run applies to its headline tracker: W warm-up and
+    K timed steps with device-resident batches, then K end-to-end steps."""
+    return warmup + 2 * steps
+
+
+def stream_node_capacity(n0, batches):
+    """Node ids after every batch of the stream, plus slack.  Contexts are
+    created with this capacity so that no capacity growth (which the library
+    does on demand, with device-wide synchronizing frees) lands inside a timed
+    region."""
+    return int(n0) + sum(int(b.n_new) for b in batches) + 1024
 
 
 # ------------------------------------------------------------------ clocks
@@ -137,44 +185,71 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(steps, warmup=0):
-    """Time the FP64 CPU oracle on the n=SAMPLE_N member of the same workload
-    family; returns (seconds per step list, description)."""
+def oracle_initial_state(w, g):
+    """Oracle state at step 0 for a timed CPU sample.  Small graphs take the
+    oracle's own direct eigendecomposition.  For the large ones a direct
+    solve (ARPACK at n = 1M) alone takes minutes, so the initial basis is a
+    Rayleigh-Ritz approximation after four block power iterations (seeded);
+    the update step does the same work whatever the accuracy of its input
+    basis (the block sizes m = K + r_W + r_B do not depend on it)."""
     import oracle as O
     from paper_2603_19439_gb300 import workloads as wl
-    g, batches = make_workload(SAMPLE_N, steps + warmup, WL["seed"] + 7)
-    rp, col, _ = wl.csr_fast(g)
-    A = O.csr_from_arrays(g.n, rp, col)
-    import scipy.sparse.linalg as ssl
-    K = WL["k"]
-    ev, V = ssl.eigsh(A, k=K + 8, which="LM", tol=1e-10, v0=np.ones(g.n))
-    o = O.select_order(ev, O.OP_ADJ)[:K]
-    st = O.State(A=A, live=np.ones(g.n, bool), X=V[:, o], lam=ev[o])
-    cfg = O.Config(k=K, L=WL["L"], P=WL["P"], seed=WL["seed"])
+    rp, col, val = wl.csr_fast(g)
+    K, op = w["k"], w["op"]
+    if g.n <= 20_000:
+        return O.init_state(g.n, rp, col, val, K, op), "direct eigendecomposition"
+    A = O.csr_from_arrays(g.n, rp, col, val)
+    live = np.ones(g.n, bool)
+    M, _ = O.operator_matrix(A, live, op)
+    X = np.random.default_rng(w["seed"]).standard_normal((g.n, K + 8))
+    for _ in range(4):
+        X, _ = np.linalg.qr(M @ X)
+    ev, F = np.linalg.eigh(X.T @ (M @ X))
+    order = O.select_order(ev, op)[:K]
+    st = O.State(A=A, live=live, X=np.ascontiguousarray(X @ F[:, order]), lam=ev[order], step=0)
+    return st, "Rayleigh-Ritz basis after 4 block power iterations"
+
+
+def oracle_sample(w, max_steps, budget_s=CPU_BUDGET_S, stream=None):
+    """Time the FP64 CPU oracle on the workload itself (no size scaling):
+    consecutive update steps of the same seeded stream the GPU arm runs, at
+    most max_steps of them and no more once budget_s seconds of timed work
+    are spent (at least one).  stream: (graph, batches) already generated.
+    Returns (seconds per timed step, description of the sample)."""
+    import oracle as O
+    g, batches = stream if stream is not None else make_workload(w, max(1, max_steps), w["seed"])
+    batches = batches[:max(1, max_steps)]
+    st, how = oracle_initial_state(w, g)
+    cfg = O.Config(k=w["k"], op=w["op"], L=w["L"], P=w["P"], seed=w["seed"])
     times = []
-    for i, b in enumerate(batches):
+    for b in batches:
         t0 = time.perf_counter()
         st, _ = O.grest_step(st, b, cfg)
-        if i >= warmup:
-            times.append(time.perf_counter() - t0)
-    return times
+        times.append(time.perf_counter() - t0)
+        if sum(times) >= budget_s:
+            break
+    desc = (f"{len(times)} consecutive FP64 oracle update steps of the n={g.n:,} workload itself (no scaling; "
+            f"initial basis: {how}); NumPy/SciPy BLAS on all host cores, scipy.sparse products single-threaded; "
+            f"bounded at {budget_s:.0f} s of timed work")
+    return times, desc
 
 
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
-    times = oracle_sample(args.steps, args.warmup)
+    w = WORKLOADS[args.workload]
+    times, sample = oracle_sample(w, args.steps)
     t = sum(times)
-    ups_sample = len(times) / t
-    value = ups_sample * SAMPLE_N / WL["n"]  # linear-in-n scaling to the 1M workload
+    value = len(times) / t
     cores = os.cpu_count()
-    sample = (f"{len(times)} FP64 oracle steps on the n={SAMPLE_N:,} member of the same workload family "
-              f"({ups_sample:.4f} updates/s there), scaled by n to n={WL['n']:,}")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
-            "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+    line = {"impl": "reference", "metric": w["metric"], "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(WL["n"]), "precision": "fp64", "sample_n": SAMPLE_N},
+            "config": {"workload": workload_desc(w), "precision": "fp64",
+                       "steps_requested": args.steps, "warmup_requested": args.warmup,
+                       "note": "the oracle is CPU code: it has no warm-up effect, and its steps are a bounded "
+                               "sample of the requested ones"},
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -269,6 +344,59 @@ def initial_pairs(tr, n, k, torch):
     return np.ascontiguousarray(V[:, order]), ev[order]
 
 
+def pair_diagnostics(tr, U, theta, torch):
+    """Residuals of the tracked pairs on the current graph: per pair
+    ||M u - theta u|| / |theta_1| with M u from the library's FP64 SpMM
+    (grest_apply_operator); the Galerkin residual max |U^T (M U - U Theta)|
+    / |theta_1| and the orthonormality max |U^T U - I|.  Diagnostics of the
+    bench line only (outside every timed region)."""
+    X = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    Y = torch.empty_like(X)
+    tr.apply_operator(X, Y)
+    th = torch.from_numpy(np.ascontiguousarray(theta)).cuda()
+    R = Y - X * th
+    scale = float(abs(theta[0]))
+    res = (torch.linalg.vector_norm(R, dim=0) / scale).cpu().numpy()
+    gal = float((X.T @ R).abs().max()) / scale
+    orth = float((X.T @ X - torch.eye(X.shape[1], dtype=X.dtype, device=X.device)).abs().max())
+    del X, Y, R
+    return {"residual": res, "galerkin": gal, "orth_err": orth}
+
+
+def subspace_sin(Ua, Ub, torch):
+    """Sine of the largest principal angle between span(Ua) and span(Ub)
+    (both orthonormal): the 2-norm of Ub - Ua (Ua^T Ub)."""
+    if Ua.shape[1] == 0:
+        return 0.0
+    A = torch.from_numpy(np.ascontiguousarray(Ua)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(Ub)).cuda()
+    P = B - A @ (A.T @ B)
+    ev = torch.linalg.eigvalsh(P.T @ P)
+    return float(max(float(ev[-1]), 0.0) ** 0.5)
+
+
+def cluster_cut(theta, op, gap=1e-6):
+    """Largest j <= K such that tracked values j-1 and j are separated by more
+    than gap * |theta_1| (in the tracking order: |theta| for the adjacency)."""
+    key = np.abs(theta) if op == 0 else np.asarray(theta)
+    scale = max(abs(theta[0]), 1e-300)
+    for j in range(len(theta), 0, -1):
+        if j == len(theta) or abs(key[j - 1] - key[j]) > gap * scale:
+            return j
+    return 0
+
+
+PRECISIONS = {"fp64": ("FP64", 1e-7), "mixed": ("MIXED", 1e-3), "mixed_fast": ("MIXED_FAST", 1e-3)}
+PRECISION_DESC = {
+    "fp64": "FP64 blocks, products, projected problems",
+    "mixed": "FP32 blocks, FP32 SpMM, 3xTF32 tensor-core Grams / block updates with FP64 partial sums; FP64 "
+             "pivoted Cholesky, FP64 m x m and RSVD eigensolves, FP64 Rayleigh-Ritz refinement in span(U) "
+             "(FP64 SpMM of U, FP64 Grams and lift)",
+    "mixed_fast": "as mixed, but FP32 pivoted Cholesky and eigensolves, and the refinement's N x K products in "
+                  "double-float (FP32 hi + lo) arithmetic",
+}
+
+
 def run_grest(args):
     import torch
     rank, world, local = env_rank()
@@ -281,30 +409,32 @@ def run_grest(args):
     from paper_2603_19439_gb300 import grest as G
     from paper_2603_19439_gb300 import workloads as wl
 
-    n, K, W, steps = args.nodes, WL["k"], args.warmup, args.steps
+    w = WORKLOADS[args.workload]
+    n, K, W, steps = args.nodes or w["n"], w["k"], args.warmup, args.steps
+    precs = [p for p in w["precisions"] if not (args.fp64_only and p != "fp64") and
+             not (args.mixed_only and p == "fp64") and not (args.no_fast and p == "mixed_fast")]
+    if not precs:
+        raise SystemExit("no precision arm selected")
+    headline = "mixed" if "mixed" in precs else precs[0]
     t0 = time.time()
-    g, batches = make_workload(n, W + 2 * steps, WL["seed"] + 1000 * rank)
-    rp, col, _ = wl.csr_fast(g)
+    g, batches = make_workload(w, batches_needed(steps, W), w["seed"] + 1000 * rank, n=n)
+    rp, col, val = wl.csr_fast(g)
     t_gen = time.time() - t0
     stream = torch.cuda.current_stream()
     t0 = time.time()
-    common = dict(stream=stream.cuda_stream, L=WL["L"], P=WL["P"], seed=WL["seed"], flags=G.FLAG_PROFILE,
-                  node_capacity=int(g.n * 1.2) + 4096)
+    common = dict(stream=stream.cuda_stream, op=w["op"], L=w["L"], P=w["P"], seed=w["seed"], flags=G.FLAG_PROFILE,
+                  node_capacity=stream_node_capacity(g.n, batches))
     if args.init == "device":
         # the library's own FP64 block Krylov solver (grest_init without U0 / theta0)
-        tr64 = G.Tracker(g.n, rp, col, None, None, None, K, precision=G.FP64, **common)
+        tr64 = G.Tracker(g.n, rp, col, val, None, None, K, precision=G.FP64, **common)
         torch.cuda.synchronize()
         t_pairs = time.time() - t0
         U0, th0, _ = tr64.embedding()
     else:
-        tr64 = G.Tracker(g.n, rp, col, None, np.zeros((g.n, K)), np.zeros(K), K, precision=G.FP64, **common)
+        tr64 = G.Tracker(g.n, rp, col, val, np.zeros((g.n, K)), np.zeros(K), K, precision=G.FP64, **common)
         U0, th0 = initial_pairs(tr64, g.n, K, torch)
         tr64.set_embedding(U0, th0)
         t_pairs = time.time() - t0
-    tr32 = None
-    if not args.fp64_only:
-        tr32 = G.Tracker(g.n, rp, col, None, U0, th0, K, precision=G.MIXED, drop_tol=MIXED_DROP_TOL, **common)
-    t_init = time.time() - t0
 
     def dev_batch(b):
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
@@ -356,90 +486,112 @@ def run_grest(args):
         e1.record(stream)
         barrier()
         clk = clocks.stop()
-        t = e0.elapsed_time(e1) * 1e-3
+        t = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
         lat = sorted(a.elapsed_time(b) for a, b in ev)
-        return t, lat, prof, last, clk
+        return dict(t=t, lat=lat, prof=prof, last=last, clk=clk)
 
-    if args.mixed_only:
-        t64 = lat64 = prof64 = last64 = clk64 = None
-        main = None
-    else:
-        t64, lat64, prof64, last64, clk64 = timed(tr64)
-        t64 = max_over_ranks(t64, world)
-        main = dict(t=t64, lat=lat64, prof=prof64, last=last64, clk=clk64, tr=None, precision="fp64")
-    tr64.close()
-    res32 = None
-    if tr32 is not None:
-        t32, lat32, prof32, last32, clk32 = timed(tr32)
-        t32 = max_over_ranks(t32, world)
-        res32 = dict(t=t32, lat=lat32, prof=prof32, last=last32, clk=clk32)
-        main = dict(res32, precision="mixed")
-    # ---- end to end through the public call from pinned host memory (headline path)
-    tr_e2e = tr32
-    if tr_e2e is None:
-        tr_e2e = G.Tracker(g.n, rp, col, None, U0, th0, K, precision=G.FP64, **common)
-        for b in dev[:W + steps]:
-            tr_e2e.update(b, on_device=True)
+    t_init = time.time() - t0
+    results, tr_head = {}, None
+    for p in precs:
+        name, tol = PRECISIONS[p]
+        tr = tr64 if p == "fp64" else G.Tracker(g.n, rp, col, val, U0, th0, K, precision=getattr(G, name),
+                                                drop_tol=tol, **common)
+        r = timed(tr)
+        r["U"], r["theta"], _ = tr.embedding()
+        r["diag"] = pair_diagnostics(tr, r["U"], r["theta"], torch)
+        results[p] = r
+        if p == headline:
+            tr_head = tr
+        elif tr is not tr64:
+            tr.close()
+    if tr_head is not tr64:
+        tr64.close()
+    # ---- end to end through the public call from pinned host memory (headline arm)
+    cap = stream_node_capacity(g.n, batches)
+    U_h = torch.empty((cap, K), dtype=torch.float64).pin_memory().numpy()
     theta_h = torch.empty(K, dtype=torch.float64).pin_memory().numpy()
     h2d = d2h = 0
     barrier()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
+    nn = G.C.c_int64()
     for b in host:
-        tr_e2e.update(b, on_device=False)
-        tr_e2e.lib.grest_get_embedding(tr_e2e.h, None, theta_h.ctypes.data, None, G.C.byref(G.C.c_int64()), 0)
+        tr_head.update(b, on_device=False)
+        tr_head.lib.grest_get_embedding(tr_head.h, U_h.ctypes.data, theta_h.ctypes.data, None, G.C.byref(nn), 0)
         h2d += 4 * (2 * b.n_ins + 2 * b.n_del + b.del_nodes.size)
-        d2h += theta_h.nbytes
+        d2h += 8 * (nn.value * K + K)
     e3.record(stream)
     barrier()
     t_e2e = max_over_ranks(e2.elapsed_time(e3) * 1e-3, world)
-    if tr32 is not None:
-        tr32.close()
-    else:
-        tr_e2e.close()
+    tr_head.close()
     if rank != 0:
         return 0
 
-    def summary(r):
+    r64 = results.get("fp64")
+
+    def accuracy(r):
+        d = r["diag"]
+        out = {"max_residual": float(d["residual"].max()), "galerkin": d["galerkin"], "orth_err": d["orth_err"],
+               "norm": "residuals / |theta_1| with M u from the library's FP64 SpMM, after the last timed step"}
+        if r64 is not None and r is not r64:
+            th, th64 = r["theta"], r64["theta"]
+            j = cluster_cut(th64, w["op"])
+            out.update({
+                "theta_rel_vs_fp64": float(np.max(np.abs(th - th64)) / abs(th64[0])),
+                "sin_angle_vs_fp64": subspace_sin(r64["U"], r["U"], torch),
+                "sin_angle_vs_fp64_cut": subspace_sin(r64["U"][:, :j], r["U"][:, :j], torch), "cut": j,
+                "residual_diff_vs_fp64": float(np.max(np.abs(d["residual"] - r64["diag"]["residual"]))),
+                "m": r["last"]["m"], "m_fp64": r64["last"]["m"]})
+        return out
+
+    def summary(p, r):
         return {"updates_per_s": world * steps / r["t"], "ms_per_step": 1e3 * r["t"] / steps,
                 "p50_ms": float(np.percentile(r["lat"], 50)), "p99_ms": float(np.percentile(r["lat"], 99)),
+                "precision": PRECISION_DESC[p], "drop_tol": PRECISIONS[p][1],
                 "phase_ms_per_step": {G.PROF_CLASSES[i]: float(r["prof"]["ms"][i] / steps) for i in range(5)},
+                "kernel_launches_per_step": r["prof"]["launches"] / steps,
                 "last_step": {k: r["last"][k] for k in ("m", "rank_q", "rank_y", "mode", "n_nodes", "nnz",
-                                                        "pivot_kept_min", "boundary_gap", "ms_refine")}}
+                                                        "pivot_kept_min", "boundary_gap", "ms_refine")},
+                "accuracy": accuracy(r),
+                "roofline": roofline(r["prof"]["ms"] / steps, r["prof"]["work"] / steps, r["prof"]["bytes"] / steps,
+                                     r["prof"]["n"] / steps, os.path.join(ROOT, "profiles", "traffic.json"),
+                                     "fp64" if p == "fp64" else "mixed"),
+                "clocks": r["clk"]}
 
+    main = results[headline]
+    arms = {p: summary(p, r) for p, r in results.items()}
     value = world * steps / main["t"]
     res = {
-        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": steps, "warmup": W,
+        "metric": w["metric"], "value": value, "unit": "updates/s", "n_gpus": world, "steps": steps, "warmup": W,
         "ms_per_step": 1e3 * main["t"] / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if main["precision"] == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(n), "precision": main["precision"], "k": K, "n0": g.n,
-                   "nnz0": int(rp[-1]), "l2": "inputs larger than L2 (graph and N x m blocks are GBs); no flush",
-                   "parallelism": f"replicas{world}",
-                   "mixed_drop_tol": MIXED_DROP_TOL},
+        "dtype": "f64" if headline == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, n), "precision": headline,
+                   "precision_detail": PRECISION_DESC[headline], "k": K, "n0": g.n,
+                   "nnz0": int(rp[-1]), "l2": "inputs larger than L2 (graph and N x m blocks are GBs); no flush"
+                   if g.n >= 200_000 else "inputs smaller than L2; no flush (the step is launch-bound)",
+                   "parallelism": f"replicas{world}", "node_capacity": common["node_capacity"]},
         "latency_ms": {"p50": float(np.percentile(main["lat"], 50)), "p99": float(np.percentile(main["lat"], 99)),
                        "min": main["lat"][0], "max": main["lat"][-1]},
-        "mixed": summary(res32) if res32 else None,
-        "fp64": summary(dict(t=t64, lat=lat64, prof=prof64, last=last64)) if t64 else None,
+        "accuracy": arms[headline]["accuracy"],
+        "arms": arms,
         "e2e": {"value": world * steps / t_e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
-                "d2h_bytes_per_step": d2h // steps, "precision": main["precision"]},
+                "d2h_bytes_per_step": d2h // steps, "precision": headline,
+                "returns": "U (N' x K FP64) and theta after every step"},
         "gpu_launches": int(main["prof"]["launches"]),
-        "roofline": roofline(main["prof"]["ms"] / steps, main["prof"]["work"] / steps, main["prof"]["bytes"] / steps,
-                             main["prof"]["n"] / steps, os.path.join(ROOT, "profiles", "traffic.json"),
-                             main["precision"]),
-        "clocks": main["clk"], "clocks_fp64": clk64,
+        "roofline": arms[headline]["roofline"],
+        "clocks": main["clk"],
         "init_s": {"generate": t_gen, "initial_pairs": t_pairs, "initial_pairs_method":
                    "device block Krylov" if args.init == "device" else "ARPACK on the library SpMM",
                    "contexts": t_init},
     }
+    if "fp64" in arms and headline != "fp64":
+        res["roofline_fp64"] = arms["fp64"]["roofline"]
     if not args.no_cpu_baseline and world == 1:
-        times = oracle_sample(2)
+        times, sample = oracle_sample(w, steps, stream=(g, batches))
         ups = len(times) / sum(times)
-        res["cpu_baseline"] = {"value": ups * SAMPLE_N / n, "unit": "updates/s", "cores": os.cpu_count(),
-                               "kind": "oracle",
-                               "sample": f"{len(times)} FP64 oracle steps on the n={SAMPLE_N:,} member of the same "
-                                         f"family ({ups:.4f} updates/s there), scaled by n to n={n:,}; "
-                                         f"BLAS on all cores, scipy.sparse products single-threaded"}
+        res["cpu_baseline"] = {"value": ups, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": sample}
     print(json.dumps(res), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -462,7 +614,7 @@ def run_kernels(args):
     rp, col, _ = g.csr()
     X0 = np.linalg.qr(np.random.default_rng(0).standard_normal((200, 4)))[0]
     tr = G.Tracker(g.n, rp, col, None, X0, np.ones(4), 4)
-    n, reps, out = args.nodes, 10, {"gram": [], "gemm": []}
+    n, reps, out = args.nodes or WL["n"], 10, {"gram": [], "gemm": []}
 
     def timed(fn):
         for _ in range(3):
@@ -549,7 +701,7 @@ def run_batched(args):
             rp, col, val = g.csr()
             extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
             trackers[i] = G.Tracker(g.n, rp, col, val, None, None, K, stream=streams[i].cuda_stream, L=20, P=20,
-                                    node_capacity=int(g.n * 1.1) + 1024, **extra)
+                                    node_capacity=stream_node_capacity(g.n, batches[i]), **extra)
 
     pool = [threading.Thread(target=make) for _ in range(args.threads)]
     for t in pool:
@@ -636,8 +788,8 @@ def run_serve(args):
         sv.set_eviction(True)
     t0 = time.time()
     extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
-    gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=int(g.n * 1.2) + 4096, **extra)
-            for g, k in zip(graphs, ks)]
+    gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=stream_node_capacity(
+                g.n, [b for gi, b in reqs if gi == i]), **extra) for i, (g, k) in enumerate(zip(graphs, ks))]
     # calibration: one request per graph at once (admission and device initial pairs happen here)
     tc = time.perf_counter()
     cal = [sv.submit(gids[gi], b) for gi, b in reqs[:ng]]
@@ -714,11 +866,15 @@ def main():
                     help="--serve: checkpoint idle graphs to host memory when a waiting graph does not fit")
     ap.add_argument("--kernels", action="store_true",
                     help="time the mixed path's Gram / GEMM entry points at the step's widths instead")
-    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision path")
-    ap.add_argument("--mixed-only", action="store_true", help="skip the FP64 path")
-    ap.add_argument("--nodes", type=int, default=WL["n"],
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision arms")
+    ap.add_argument("--mixed-only", action="store_true", help="skip the FP64 arm")
+    ap.add_argument("--no-fast", action="store_true", help="skip the MIXED_FAST arm")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cl1m",
+                    help="cl1m: the 1M-node adjacency stream (default); cl200k: 200k-node normalized Laplacian; "
+                         "sbm2k: the SBM stream")
+    ap.add_argument("--nodes", type=int, default=None,
                     help="graph size of the same workload family (smaller sizes are for profiler captures; "
-                         "the reported metric is defined at the default 1,000,000)")
+                         "the reported metric is defined at the workload's own size)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

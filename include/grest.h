@@ -44,7 +44,7 @@ typedef enum {
   GREST_ERR_INVALID_ARG = 1,     /* bad pointer, size or configuration field */
   GREST_ERR_INVALID_UPDATE = 2,  /* batch violates Sec. 2's definition of Delta */
   GREST_ERR_OOM = 3,             /* device allocation failed */
-  GREST_ERR_CAPACITY = 4,        /* node or edge capacity of the context exceeded */
+  GREST_ERR_CAPACITY = 4,        /* a fixed limit exceeded (2^31 - 1 node ids, a caller buffer) */
   GREST_ERR_NUMERIC = 5,         /* fewer than K Ritz pairs, or a Cholesky broke down */
   GREST_ERR_CUDA = 6,            /* CUDA runtime error (no device, launch failure) */
   GREST_ERR_TIMEOUT = 7,         /* a bounded device-side wait expired */
@@ -66,7 +66,19 @@ enum {
   GREST_SUB_AUTO = 3    /* GREST3 when S <= L+P, RSVD otherwise (default)              */
 };
 
-enum { GREST_FP64 = 0, GREST_MIXED = 1 };                 /* arithmetic of the step */
+/* Arithmetic of the step.
+ * GREST_FP64: every block and product in FP64.
+ * GREST_MIXED: N x w blocks stored in FP32; SpMM in FP32; the Grams and
+ *   block updates on the tensor cores (3xTF32, FP32 accumulation, FP64
+ *   partial sums); the pivoted Cholesky, the m x m and RSVD eigensolves in
+ *   FP64; then one Rayleigh-Ritz refinement in span(U) with FP64 products
+ *   (M U, U^T U, U^T M U and the lift), so the result is orthonormal and
+ *   Galerkin-consistent to FP64 accuracy.
+ * GREST_MIXED_FAST: as GREST_MIXED, but the projected problems are solved in
+ *   FP32 arithmetic (their entries come from FP32 blocks) and the
+ *   refinement's N x K products run in double-float arithmetic (FP32 hi + lo
+ *   pairs, about 48 significant bits) on the FP32 pipes. */
+enum { GREST_FP64 = 0, GREST_MIXED = 1, GREST_MIXED_FAST = 2 };
 /* Projected operator: EXACT forms H = Z^T M_new Z (Eq. main2); LOWRANK forms
  * the paper's surrogate H = (X_bar^T Z)^T Lambda (X_bar^T Z) + Z^T Delta Z
  * (Eq. main3, Alg. 2 as printed), where Delta = M_new - M_old (M_old padded
@@ -75,7 +87,7 @@ enum { GREST_FP64 = 0, GREST_MIXED = 1 };                 /* arithmetic of the s
  * W block: RESID uses P_perp (M_new X_bar); DELTA the paper's P_perp (Delta X_bar)
  * (Sec. 3.3).  LOWRANK and DELTA are available for GREST_OP_ADJ and
  * GREST_OP_LAP, for batches without node removal (GREST_ERR_UNSUPPORTED
- * otherwise); LOWRANK runs in the FP64 path only. */
+ * otherwise); LOWRANK runs in GREST_FP64 only. */
 enum { GREST_PROJ_EXACT = 0, GREST_PROJ_LOWRANK = 1 };
 enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };
 
@@ -88,15 +100,17 @@ typedef struct {
   int32_t k;           /* K, number of tracked pairs, 1 <= k <= 64                      */
   int32_t subspace;    /* GREST_SUB_*                                                  */
   int32_t L, P;        /* RSVD rank and oversampling (Sec. 3.5); L+P <= 256             */
-  int32_t precision;   /* GREST_FP64 | GREST_MIXED                                      */
+  int32_t precision;   /* GREST_FP64 | GREST_MIXED | GREST_MIXED_FAST                   */
   int32_t projection;  /* GREST_PROJ_*                                                 */
   int32_t w_block;     /* GREST_WB_*                                                   */
   uint32_t flags;      /* GREST_FLAG_*                                                 */
   uint64_t seed;       /* key of the counter-based generator that draws Omega          */
   double drop_tol;     /* a basis direction is dropped when its pivot R_kk is at most   *
                         * drop_tol * max(R_00, |theta_1|) (|theta_1| ~ ||M||_2)         */
-  int64_t node_capacity;   /* maximum number of node ids; 0 = 1.25 x initial + 1024     */
-  int64_t nnz_capacity;    /* directed-edge arena size;   0 = 2 x initial + 2^20        */
+  int64_t node_capacity;   /* initial node-id capacity; 0 = 1.25 x initial + 1024;     *
+                            * grows by 1.5x when a batch needs more (see below)         */
+  int64_t nnz_capacity;    /* initial directed-edge arena; 0 = 2 x initial + 2^20;     *
+                            * compacted into a larger arena when a batch needs more    */
   int64_t max_batch_edges; /* largest n_ins + n_del per update; 0 = 2^20 (grows on demand) */
 } grest_config;
 
@@ -204,7 +218,7 @@ grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowpt
  * GREST_ERR_INVALID_UPDATE (the batch breaks Sec. 2's definition of Delta:
  * an existing edge inserted, a missing edge deleted, a duplicate, a self
  * loop, an id out of range or removed) with the context unchanged;
- * GREST_ERR_CAPACITY (node or edge capacity exceeded) with the context
+ * GREST_ERR_CAPACITY (more than 2^31 - 1 node ids) with the context
  * unchanged; GREST_ERR_UNSUPPORTED (node removal in the DELTA / LOWRANK
  * modes; an exact new-node block wider than L + P); GREST_ERR_NUMERIC: the
  * graph is updated, and either the basis had fewer than k directions (the
@@ -212,6 +226,15 @@ grest_status grest_init(const grest_config *cfg, int64_t n, const int64_t *rowpt
  * new nodes) or the second CholQR pass lost rank (the pairs are updated from
  * the smaller basis); GREST_ERR_TIMEOUT (a bounded device-side wait gave
  * up); GREST_ERR_OOM, GREST_ERR_CUDA.
+ * Growth: Alg. 2 appends S ids per step, so the context grows instead of
+ * failing.  A batch whose N + S exceeds the node capacity first moves every
+ * per-node array (the CSR row arrays, X and the N x w blocks) to
+ * max(N + S, 1.5 x capacity) ids; a batch whose merged rows do not fit the
+ * edge arena is applied again after the arena is compacted into one of
+ * max(1.5 x size, 2 x compacted + the batch's need + 2^20) entries.  Both
+ * allocate before they release, so an allocation failure returns
+ * GREST_ERR_OOM with the context unchanged; both make the call synchronize
+ * the device (cudaFree).  Results do not depend on the capacities.
  */
 grest_status grest_apply_update(grest_ctx *ctx, const grest_update *upd, grest_stats *stats);
 
@@ -378,9 +401,15 @@ grest_status grest_gemm_f32(grest_ctx *ctx, int64_t n, int32_t a, int32_t c, dou
  * every partial a call reads is written earlier in the same call, so nothing
  * needs clearing.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  The work is enqueued on cuda_stream
- * (NULL = legacy default stream) and C is complete when that stream's work
- * is; the call itself does not synchronize.
+ * call before any stream capture.  With CUDA's lazy module loading (the
+ * default since CUDA 12.2) the array is brought onto a device by that first
+ * call, not when the library is loaded, so the first call can fail
+ * (GREST_ERR_CUDA) if the caller's pool has already taken all device
+ * memory: make one call on each device before the pool reserves memory.
+ * The work is enqueued on cuda_stream (NULL = legacy default stream) and C
+ * is complete when that stream's work is; the call itself does not
+ * synchronize.  A CUDA error already pending on the calling host thread is
+ * returned as GREST_ERR_CUDA before anything is enqueued.
  */
 grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const double *Y, int64_t ldy, int32_t b,
                                 int64_t n, double *C, int64_t ldc, void *cuda_stream);

@@ -1,10 +1,15 @@
 """Build libgrest.so in-tree with nvcc for sm_103a (GB300).
 
 Every translation unit under csrc/ is compiled in parallel to an object file
-under _build/, then linked into paper_2603_19439_gb300/libgrest.so.  A rebuild
-happens only when a source or header is newer than the library.
+under _build/, then linked into paper_2603_19439_gb300/libgrest.so.  The
+library is rebuilt unless a stamp written by the last build of it matches the
+sources, the headers, the flags and this machine's architecture: a library
+copied in from elsewhere (another machine, another checkout) is never trusted
+because of its modification time.
 """
+import hashlib
 import os
+import platform
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
 
@@ -26,15 +31,34 @@ def _nvcc():
     return "nvcc"
 
 
-def _newest_input():
-    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    return max(os.path.getmtime(p) for p in paths)
+STAMP = os.path.join(BUILD, "libgrest.stamp")
+
+
+def _input_hash():
+    """Hash of every source and header, the compiler flags and the machine."""
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for f in sorted(os.listdir(d)):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS + SOURCES).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+def _stamp_of(lib):
+    """The input hash recorded for this very file (its size and mtime included)."""
+    st = os.stat(lib)
+    return f"{_input_hash()} {st.st_size} {st.st_mtime_ns}"
 
 
 def build(force=False, verbose=False):
     """Compile and link libgrest.so; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
+    if not force and os.path.exists(LIB) and os.path.exists(STAMP):
+        with open(STAMP) as fh:
+            if fh.read().strip() == _stamp_of(LIB):
+                return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
@@ -55,6 +79,8 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(_stamp_of(LIB))
     return LIB
 
 

@@ -26,6 +26,7 @@ enum DevErr : int32_t {
   DERR_CAPACITY = 9,     // edge arena exhausted
   DERR_NUMERIC = 10,     // Cholesky breakdown / rank below K
   DERR_TIMEOUT = 11,     // a bounded device-side wait expired
+  DERR_ARENA = 12,       // edge arena too small for this batch (the host grows it and retries)
 };
 
 __device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
@@ -150,6 +151,13 @@ int delta_apply(const Csr& g, const GraphWork& w, int op, const float* X, int64_
                 int64_t N, int64_t N2, const double* dmax_old, cudaStream_t s);
 // total row length over rows [0, n) into *out (device int64)
 int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s);
+// Arena compaction, in two parts.  graph_compact_plan writes the compacted
+// row offsets (slot of len + len/4 + 4 entries per row, rows in id order) to
+// w.rowflag[0..n] (total at [n]).  graph_compact_copy copies rows [0, n) into
+// new_col / new_val (at least that total) and rewrites row_off, row_cap and
+// arena_top; the caller then replaces g.col / g.val.  Each returns launches.
+int graph_compact_plan(const Csr& g, GraphWork& w, int64_t n, cudaStream_t s);
+int graph_compact_copy(Csr& g, const GraphWork& w, int64_t n, int32_t* new_col, double* new_val, cudaStream_t s);
 
 // spmm.cu
 // Y[r0:r1) = (M X)[r0:r1) for rows r0..r1, w columns; when col_lo > 0 only

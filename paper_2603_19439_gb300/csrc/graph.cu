@@ -331,7 +331,7 @@ __global__ void k_need(const int32_t* touched, const int64_t* n_touched, int64_t
 
 __global__ void k_check_arena(const int64_t* need_scan, int64_t max_t, const int64_t* arena_top, int64_t nnz_cap,
                               int32_t* err) {
-  if (*arena_top + need_scan[max_t] > nnz_cap) set_err(err, DERR_CAPACITY);
+  if (*arena_top + need_scan[max_t] > nnz_cap) set_err(err, DERR_ARENA);
 }
 
 // --- commit staged rows (only reached by a fully valid batch)
@@ -375,6 +375,38 @@ __global__ void __launch_bounds__(256) k_commit_rows(const int32_t* touched, con
     __syncthreads();
   }
 }
+
+// --- arena compaction: fresh slots of len + len/4 + 4 entries, in row order
+__global__ void k_compact_caps(const int32_t* row_len, int64_t n, int64_t* caps) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < n) {
+    const int64_t l = row_len[r];
+    caps[r] = l + l / 4 + 4;
+  }
+}
+
+// one warp per row; a row's offset is rewritten by the warp that read it
+__global__ void __launch_bounds__(256) k_compact_copy(int64_t n, const int64_t* off_scan, int64_t* row_off,
+                                                      const int32_t* row_len, int32_t* row_cap, const int32_t* col,
+                                                      const double* val, int32_t* ncol, double* nval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    const int64_t o = row_off[r], no = off_scan[r];
+    const int32_t l = row_len[r];
+    for (int32_t j = lane; j < l; j += 32) {
+      ncol[no + j] = col[o + j];
+      if (val) nval[no + j] = val[o + j];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      row_off[r] = no;
+      row_cap[r] = (int32_t)(off_scan[r + 1] - no);
+    }
+  }
+}
+
+__global__ void k_set_top(int64_t* arena_top, const int64_t* off_scan, int64_t n) { *arena_top = off_scan[n]; }
 
 __global__ void k_bump_arena(int64_t* arena_top, const int64_t* need_scan, int64_t max_t, const int32_t* err) {
   if (!*err) *arena_top += need_scan[max_t];
@@ -504,6 +536,19 @@ int graph_count_nnz(const Csr& g, int64_t n, int64_t* out, cudaStream_t s) {
   if (nb < 1) nb = 1;
   k_sum_len<<<nb, 256, 0, s>>>(g.row_len, n, reinterpret_cast<unsigned long long*>(out));
   return 1;
+}
+
+int graph_compact_plan(const Csr& g, GraphWork& w, int64_t n, cudaStream_t s) {
+  const int T = 256;
+  k_compact_caps<<<blocks_for(n, T), T, 0, s>>>(g.row_len, n, w.rowflag);
+  return 1 + exclusive_scan_i64(w.rowflag, w.rowflag, n, w.scan_tmp, s);
+}
+
+int graph_compact_copy(Csr& g, const GraphWork& w, int64_t n, int32_t* new_col, double* new_val, cudaStream_t s) {
+  k_compact_copy<<<capped(blocks_for(n * 32, 256), 152 * 8), 256, 0, s>>>(n, w.rowflag, g.row_off, g.row_len,
+                                                                          g.row_cap, g.col, g.val, new_col, new_val);
+  k_set_top<<<1, 1, 0, s>>>(g.arena_top, w.rowflag, n);
+  return 2;
 }
 
 int graph_refresh_derived(Csr& g, GraphWork& w, int64_t n, cudaStream_t s) {

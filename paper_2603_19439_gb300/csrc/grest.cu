@@ -164,10 +164,18 @@ cudaError_t dalloc(T** p, size_t count) {
   return dmalloc((void**)p, sizeof(T) * count);
 }
 
+// release a buffer of `bytes` that dmalloc / dalloc counted
+void dfree(void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  t_dev_bytes -= bytes;
+}
+
 grest_status map_dev_err(int32_t e) {
   switch (e) {
     case DERR_NONE: return GREST_OK;
     case DERR_CAPACITY: return GREST_ERR_CAPACITY;
+    case DERR_ARENA: return GREST_ERR_CAPACITY;
     case DERR_NUMERIC: return GREST_ERR_NUMERIC;
     case DERR_TIMEOUT: return GREST_ERR_TIMEOUT;
     default: return GREST_ERR_INVALID_UPDATE;
@@ -199,17 +207,22 @@ void free_ctx(grest_ctx* c) {
 grest_status ensure_batch(grest_ctx* c, int64_t n_edges, int64_t n_dn) {
   if (n_edges > c->b_cap) {
     int64_t cap = std::max<int64_t>(n_edges, 2 * c->b_cap);
-    cudaFree(c->b_iu); cudaFree(c->b_iv); cudaFree(c->b_du); cudaFree(c->b_dv); cudaFree(c->b_w);
+    if (c->b_iu) {
+      const size_t o = (size_t)std::max<int64_t>(c->b_cap, 1);
+      dfree(c->b_iu, 4 * o); dfree(c->b_iv, 4 * o); dfree(c->b_du, 4 * o); dfree(c->b_dv, 4 * o); dfree(c->b_w, 8 * o);
+    }
     c->b_iu = c->b_iv = c->b_du = c->b_dv = nullptr;
     c->b_w = nullptr;
+    c->b_cap = 0;
     CK(dalloc(&c->b_iu, cap)); CK(dalloc(&c->b_iv, cap)); CK(dalloc(&c->b_du, cap)); CK(dalloc(&c->b_dv, cap));
     CK(dalloc(&c->b_w, cap));
     c->b_cap = cap;
   }
   if (n_dn > c->b_dn_cap) {
     int64_t cap = std::max<int64_t>(n_dn, 2 * c->b_dn_cap);
-    cudaFree(c->b_dn);
+    if (c->b_dn) dfree(c->b_dn, 4 * (size_t)std::max<int64_t>(c->b_dn_cap, 1));
     c->b_dn = nullptr;
+    c->b_dn_cap = 0;
     CK(dalloc(&c->b_dn, cap));
     c->b_dn_cap = cap;
   }
@@ -220,15 +233,23 @@ grest_status ensure_graph_work(grest_ctx* c, int64_t entries) {
   GraphWork& w = c->gw;
   if (entries > w.ent_cap) {
     int64_t cap = std::max<int64_t>(entries, 2 * w.ent_cap);
-    cudaFree(w.ekey); cudaFree(w.ew); cudaFree(w.eins); cudaFree(w.edel);
+    const size_t old = (size_t)std::max<int64_t>(w.ent_cap, 1);
+    if (w.ekey) {
+      dfree(w.ekey, sizeof(uint64_t) * old); dfree(w.ew, sizeof(double) * old);
+      dfree(w.eins, sizeof(int32_t) * old); dfree(w.edel, sizeof(double) * old);
+    }
     w.ekey = nullptr; w.ew = nullptr; w.eins = nullptr; w.edel = nullptr;
+    w.ent_cap = 0;
     CK(dalloc(&w.ekey, cap)); CK(dalloc(&w.ew, cap)); CK(dalloc(&w.eins, cap)); CK(dalloc(&w.edel, cap));
     w.ent_cap = cap;
   }
   int64_t tneed = c->g.nnz_cap + w.ent_cap;
   if (tneed > w.tmp_cap) {
-    cudaFree(w.tmp_col); cudaFree(w.tmp_val);
+    const size_t old = (size_t)std::max<int64_t>(w.tmp_cap, 1);
+    if (w.tmp_col) dfree(w.tmp_col, sizeof(int32_t) * old);
+    if (w.tmp_val) dfree(w.tmp_val, sizeof(double) * old);
     w.tmp_col = nullptr; w.tmp_val = nullptr;
+    w.tmp_cap = 0;
     CK(dalloc(&w.tmp_col, tneed));
     if (c->g.val) CK(dalloc(&w.tmp_val, tneed));
     w.tmp_cap = tneed;
@@ -236,11 +257,130 @@ grest_status ensure_graph_work(grest_ctx* c, int64_t entries) {
   return GREST_OK;
 }
 
+// Per-node arrays for `cap` ids.  Alg. 2 appends S ids per step, so a context
+// that keeps receiving batches outgrows any fixed capacity; grow_nodes moves
+// every array listed here to a larger capacity.  keep: state that carries
+// over between steps (its first n rows are copied); the rest is per-step
+// scratch.
+struct NodeArray {
+  void** slot;
+  size_t per_node, extra;
+  bool keep;
+};
+
+std::vector<NodeArray> node_arrays(grest_ctx* c) {
+  Csr& g = c->g;
+  GraphWork& w = c->gw;
+  std::vector<NodeArray> a = {
+      {(void**)&g.row_off, 8, 0, true},  {(void**)&g.row_len, 4, 0, true},   {(void**)&g.row_cap, 4, 0, true},
+      {(void**)&g.live, 1, 0, true},     {(void**)&g.deg, 8, 0, true},       {(void**)&g.dis, 8, 0, true},
+      {(void**)&w.long_rows, 4, 0, true},{(void**)&c->U, 8 * (size_t)c->ldu, 0, true},
+      {(void**)&w.cnt, 4, 4, false},     {(void**)&w.seg, 8, 8, false},      {(void**)&w.cursor, 4, 0, false},
+      {(void**)&w.delflag, 1, 0, false}, {(void**)&w.rowflag, 8, 8, false},  {(void**)&w.touched, 4, 0, false},
+      {(void**)&w.tmp_off, 8, 8, false}, {(void**)&w.need, 8, 8, false},     {(void**)&w.new_len, 4, 0, false},
+      {(void**)&c->Un, 8 * (size_t)c->ldu, 0, false},
+      {&c->Zv, c->esz * (size_t)c->ldz, 0, false}, {&c->MZv, c->esz * (size_t)c->ldz, 0, false},
+      {&c->V2v, c->esz * (size_t)c->ldv, 0, false},
+      {&c->Yrv, c->esz * (size_t)c->ldq, 0, false}, {&c->Yr2v, c->esz * (size_t)c->ldq, 0, false}};
+  if (c->U32) a.push_back({(void**)&c->U32, 4 * (size_t)c->ldu, 0, false});
+  if (c->Rres) a.push_back({(void**)&c->Rres, 8 * (size_t)c->ldu, 0, false});
+  return a;
+}
+
+// Grow the node capacity to at least `need` ids (1.5x steps).  Every new
+// buffer is allocated before an old one is released, so a failed
+// allocation returns GREST_ERR_OOM with the context unchanged.
+grest_status grow_nodes(grest_ctx* c, int64_t need) {
+  const int64_t old_cap = c->g.n_cap, n = c->g.n;
+  int64_t cap = std::max<int64_t>(need, old_cap + old_cap / 2);
+  cap = std::min<int64_t>(round_up(cap, 1024), (int64_t)INT32_MAX);
+  if (cap < need) return GREST_ERR_CAPACITY;
+  std::vector<NodeArray> arrs = node_arrays(c);
+  std::vector<void*> fresh(arrs.size() + 1, nullptr);
+  auto release = [&]() {
+    for (size_t i = 0; i < arrs.size(); ++i) dfree(fresh[i], arrs[i].per_node * cap + arrs[i].extra);
+    dfree(fresh.back(), scan_temp_bytes(cap + 1));
+  };
+  for (size_t i = 0; i < arrs.size(); ++i) {
+    if (dmalloc(&fresh[i], arrs[i].per_node * cap + arrs[i].extra) != cudaSuccess) {
+      cudaGetLastError();
+      fresh[i] = nullptr;
+      release();
+      return GREST_ERR_OOM;
+    }
+  }
+  if (dmalloc(&fresh.back(), scan_temp_bytes(cap + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    fresh.back() = nullptr;
+    release();
+    return GREST_ERR_OOM;
+  }
+  cudaStream_t s = c->stream;
+  for (size_t i = 0; i < arrs.size(); ++i)
+    if (arrs[i].keep && n > 0)
+      CK(cudaMemcpyAsync(fresh[i], *arrs[i].slot, arrs[i].per_node * n, cudaMemcpyDeviceToDevice, s));
+  for (size_t i = 0; i < arrs.size(); ++i)  // live: ids >= n are not in use
+    if (arrs[i].slot == (void**)&c->g.live) CK(cudaMemsetAsync(static_cast<uint8_t*>(fresh[i]) + n, 0, cap - n, s));
+  CK(cudaStreamSynchronize(s));
+  for (size_t i = 0; i < arrs.size(); ++i) {
+    dfree(*arrs[i].slot, arrs[i].per_node * old_cap + arrs[i].extra);
+    *arrs[i].slot = fresh[i];
+  }
+  dfree(c->gw.scan_tmp, scan_temp_bytes(old_cap + 1));
+  c->gw.scan_tmp = fresh.back();
+  if (c->cent_buf) {  // centrality scratch: allocated again at the next call
+    cudaFree(c->cent_buf);
+    c->cent_buf = nullptr;
+  }
+  c->g.n_cap = cap;
+  c->cfg.node_capacity = cap;
+  return GREST_OK;
+}
+
+// Grow the edge arena: every row is copied, compacted, into an arena of
+// max(1.5 nnz_cap, 2 compacted + extra + 2^20) entries (the holes left by
+// rows that moved are reclaimed).  The row order inside each row is kept, so
+// later products sum in the same order.  On OOM the context is unchanged.
+grest_status grow_arena(grest_ctx* c, int64_t n, int64_t extra) {
+  Csr& g = c->g;
+  cudaStream_t s = c->stream;
+  c->launches += graph_compact_plan(g, c->gw, n, s);
+  CK(cudaMemcpyAsync(c->h_scal + 6, c->gw.rowflag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t total = c->h_scal[6];
+  const int64_t cap = std::max<int64_t>(g.nnz_cap + g.nnz_cap / 2, 2 * total + extra + (1 << 20));
+  int32_t* ncol = nullptr;
+  double* nval = nullptr;
+  if (dalloc(&ncol, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return GREST_ERR_OOM;
+  }
+  if (g.val && dalloc(&nval, cap) != cudaSuccess) {
+    cudaGetLastError();
+    dfree(ncol, sizeof(int32_t) * cap);
+    return GREST_ERR_OOM;
+  }
+  c->launches += graph_compact_copy(g, c->gw, n, ncol, nval, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  dfree(g.col, sizeof(int32_t) * g.nnz_cap);
+  if (g.val) dfree(g.val, sizeof(double) * g.nnz_cap);
+  g.col = ncol;
+  g.val = nval;
+  g.nnz_cap = cap;
+  c->cfg.nnz_capacity = cap;
+  return ensure_graph_work(c, c->gw.ent_cap);  // merge staging is sized by the arena
+}
+
 grest_status ensure_S(grest_ctx* c, int64_t S) {
   if (S <= c->S_cap) return GREST_OK;
   int64_t cap = std::max<int64_t>(S, 2 * c->S_cap);
-  cudaFree(c->Omv); cudaFree(c->EtMv);
+  if (c->Omv) {
+    dfree(c->Omv, c->esz * c->S_cap * c->ldq);
+    dfree(c->EtMv, c->esz * c->S_cap * c->ldq);
+  }
   c->Omv = c->EtMv = nullptr;
+  c->S_cap = 0;
   CK(dmalloc((void**)&c->Omv, c->esz * cap * c->ldq));
   CK(dmalloc((void**)&c->EtMv, c->esz * cap * c->ldq));
   c->S_cap = cap;
@@ -399,6 +539,14 @@ void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* thet
   prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
+// Arithmetic of the projected problems (pivoted Cholesky, m x m and q x q
+// eigensolves): FP32 only in GREST_MIXED_FAST, whose Grams are FP32-accurate
+// (reading R15); FP64 in GREST_MIXED and GREST_FP64.
+template <typename T>
+bool small_f32(const grest_ctx* c) {
+  return sizeof(T) == sizeof(float) && c->cfg.precision == GREST_MIXED_FAST;
+}
+
 template <typename T>
 T* Zp(grest_ctx* c) { return static_cast<T*>(c->Zv); }
 template <typename T>
@@ -432,7 +580,7 @@ grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
   int p = prof_begin(c);
   c->launches += pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot,
-                               sizeof(T) == sizeof(float), c->stream);
+                               small_f32<T>(c), c->stream);
   prof_end(c, p, 3, (double)w * w * w / 3.0 + (double)w * w * w / 3.0);
   int rank = w;
   if (read_rank) {
@@ -600,6 +748,42 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   return GREST_OK;
 }
 
+// Mixed path, A11 in FP64 arithmetic (GREST_MIXED): X64 = U32 widened
+// exactly, MU = M U32 with FP64 products and sums, G = X64^T X64 and
+// H' = X64^T MU as FP64 Grams; then the same K x K Rayleigh-Ritz problem as
+// refine_mixed (FP64), and X = X64 (T F'') as an FP64 GEMM.  The previous
+// pairs in U are no longer read at this point of the step, so U holds MU
+// until the lift overwrites it.
+grest_status refine_mixed_f64(grest_ctx* c, int64_t N2) {
+  cudaStream_t s = c->stream;
+  const int K = c->K;
+  const int64_t ldu = c->ldu;
+  double* X64 = c->Un;
+  double* MU = c->U;
+  int p = prof_begin(c);
+  convert_f32_to_f64(c->U32, ldu, X64, ldu, N2, K, s);
+  c->launches += 1;
+  prof_end(c, p, 2, 0.0, 12.0 * N2 * K);
+  spmm(c, c->U32, ldu, MU, ldu, K, 0, N2, 0);
+  gram(c, X64, ldu, K, X64, ldu, K, N2, c->G, K, true);
+  gram(c, X64, ldu, K, MU, ldu, K, N2, c->H, K, false);
+  p = prof_begin(c);
+  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
+  k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
+  symmetrize(c->Uh, K, K, s);
+  c->launches += 2;
+  prof_end(c, p, 3, 4.0 * K * K * K);
+  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
+  k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
+  c->launches += 1;
+  gemm(c, N2, K, K, 1.0, X64, ldu, c->Gs, K, 0.0, static_cast<const double*>(nullptr), 0, c->U, ldu);
+  p = prof_begin(c);
+  c->launches += sign_normalize_fast(c->U, ldu, K, N2, c->part, c->ipart, s);
+  prof_end(c, p, 2, 0.0, 16.0 * N2 * K);
+  CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+  return GREST_OK;
+}
+
 template <typename T>
 grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   const int64_t N2 = N + S;
@@ -698,7 +882,7 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
         // left singular vectors of B_s via eig(B_s B_s^T), L leading
         gram(c, EtM, ldq, rY, EtM, ldq, rY, S, c->Gs, rY, true);
         const int Lp = std::min(c->Lr, rY);
-        eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16, sizeof(T) == sizeof(float));
+        eig(c, c->Gs, rY, rY, Lp, GREST_OP_LAP, c->tmpk, c->Uh, Lp, c->ritz, c->info + 16, small_f32<T>(c));
         // S.4: R = M U_hat
         gemm(c, N2, rY, Lp, 1.0, Yr, ldq, c->Uh, Lp, 0.0, static_cast<const T*>(nullptr), 0, B, ldz);
         cb = Lp;
@@ -743,7 +927,7 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   c->launches += 1;
   CK(cudaEventRecord(c->ev[5], s));
   // A9: leading K eigenpairs of H (Alg. 1)
-  eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, sizeof(T) == sizeof(float));
+  eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, small_f32<T>(c));
   CK(cudaEventRecord(c->ev[6], s));
   // A10: X = Z F_K, sign normalization
   if constexpr (sizeof(T) == sizeof(double)) {
@@ -756,8 +940,8 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   } else {
     gemm(c, N2, m, K, 1.0, Z, ldz, c->F, K, 0.0, static_cast<const T*>(nullptr), 0, c->U32, c->ldu);
     CK(cudaEventRecord(c->ev[7], s));
-    // A11: FP64 refinement
-    grest_status st2 = refine_mixed(c, N2);
+    // A11: FP64-accurate refinement (FP64 products, or double-float ones in GREST_MIXED_FAST)
+    grest_status st2 = c->cfg.precision == GREST_MIXED_FAST ? refine_mixed(c, N2) : refine_mixed_f64(c, N2);
     if (st2 != GREST_OK) return st2;
     CK(cudaEventRecord(c->ev[8], s));
   }
@@ -1124,7 +1308,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   if (cfg->k < 1 || cfg->k > 64 || cfg->op < 0 || cfg->op > 2 || cfg->L < 1 || cfg->P < 0 || cfg->L + cfg->P > 256 ||
       cfg->subspace < 0 || cfg->subspace > 3 || !(cfg->drop_tol > 0.0) || cfg->k > n)
     return GREST_ERR_INVALID_ARG;
-  if ((cfg->precision != GREST_FP64 && cfg->precision != GREST_MIXED) ||
+  if ((cfg->precision != GREST_FP64 && cfg->precision != GREST_MIXED && cfg->precision != GREST_MIXED_FAST) ||
       (cfg->projection != GREST_PROJ_EXACT && cfg->projection != GREST_PROJ_LOWRANK) ||
       (cfg->w_block != GREST_WB_RESID && cfg->w_block != GREST_WB_DELTA))
     return GREST_ERR_INVALID_ARG;
@@ -1133,7 +1317,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   // refinement in the mixed path
   if ((cfg->projection == GREST_PROJ_LOWRANK || cfg->w_block == GREST_WB_DELTA) && cfg->op == GREST_OP_NLAP)
     return GREST_ERR_UNSUPPORTED;
-  if (cfg->projection == GREST_PROJ_LOWRANK && cfg->precision == GREST_MIXED) return GREST_ERR_UNSUPPORTED;
+  if (cfg->projection == GREST_PROJ_LOWRANK && cfg->precision != GREST_FP64) return GREST_ERR_UNSUPPORTED;
   if ((U0 == nullptr) != (theta0 == nullptr)) return GREST_ERR_INVALID_ARG;
   const int64_t nnz = rowptr[n];
   for (int64_t i = 0; i < n; ++i)
@@ -1219,12 +1403,12 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
     if (ensure_batch(c, mb, 1024) != GREST_OK) { free_ctx(c); return GREST_ERR_OOM; }
   }
   IK(dalloc(&c->U, nc * c->ldu)); IK(dalloc(&c->Un, nc * c->ldu)); IK(dalloc(&c->theta, 64));
-  c->esz = cfg->precision == GREST_MIXED ? sizeof(float) : sizeof(double);
+  c->esz = cfg->precision != GREST_FP64 ? sizeof(float) : sizeof(double);
   IK(dmalloc((void**)&c->Zv, c->esz * nc * c->ldz)); IK(dmalloc((void**)&c->MZv, c->esz * nc * c->ldz));
   IK(dmalloc((void**)&c->V2v, c->esz * nc * c->ldv));
   IK(dmalloc((void**)&c->Yrv, c->esz * nc * c->ldq)); IK(dmalloc((void**)&c->Yr2v, c->esz * nc * c->ldq));
   IK(dmalloc((void**)&c->Idv, c->esz * (int64_t)c->q * c->ldq));
-  if (cfg->precision == GREST_MIXED) IK(dalloc(&c->U32, nc * c->ldu));
+  if (cfg->precision != GREST_FP64) IK(dalloc(&c->U32, nc * c->ldu));
   if (cfg->flags & GREST_FLAG_CHECK) IK(dalloc(&c->Rres, nc * c->ldu));
   const int cm = c->cmax, mm = c->mmax;
   IK(dalloc(&c->Cm, 64 * 64)); IK(dalloc(&c->Cv, (int64_t)64 * (cm + 64))); IK(dalloc(&c->G, (int64_t)cm * cm));
@@ -1310,12 +1494,16 @@ static grest_status apply_update_impl(grest_ctx* c, const grest_update* u, grest
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
   cudaStream_t s = c->stream;
   const int64_t N = c->g.n, S = u->n_new_nodes;
-  if (N + S > c->g.n_cap) return GREST_ERR_CAPACITY;
   if (N + S > INT32_MAX) return GREST_ERR_CAPACITY;
-  grest_status st = ensure_batch(c, std::max(u->n_ins, u->n_del), u->n_del_nodes);
-  if (st != GREST_OK) return st;
   c->prof_n = 0;
   c->launches = 0;
+  grest_status st = GREST_OK;
+  if (N + S > c->g.n_cap) {
+    st = grow_nodes(c, N + S);
+    if (st != GREST_OK) return st;
+  }
+  st = ensure_batch(c, std::max(u->n_ins, u->n_del), u->n_del_nodes);
+  if (st != GREST_OK) return st;
   CK(cudaEventRecord(c->ev[0], s));
   const cudaMemcpyKind kind = u->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (u->n_ins > 0) {
@@ -1350,22 +1538,36 @@ static grest_status apply_update_impl(grest_ctx* c, const grest_update* u, grest
   bd.del_u = c->b_du;
   bd.del_v = c->b_dv;
   bd.dn = c->b_dn;
-  CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
   c->batch_new_edges = u->n_ins;
   if (delta_modes) CK(cudaMemcpyAsync(c->dmax_old, c->g.dmax, sizeof(double), cudaMemcpyDeviceToDevice, s));
-  {
-    int p = prof_begin(c);
-    c->launches += graph_apply_batch(c->g, c->gw, bd, c->err, s);
-    prof_end(c, p, 4, 0.0);
-  }
-  c->launches += graph_count_nnz(c->g, N + S, c->gw.scalars + 5, s);
-  CK(cudaMemcpyAsync(c->h_scal + 5, c->gw.scalars + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaGetLastError());
-  st = read_back(c, 0);
-  if (st != GREST_OK) return st;
-  if (*c->h_err) {
-    c->prof_n = 0;
-    return map_dev_err(*c->h_err);
+  // A batch that does not fit the edge arena changes nothing (the commit is
+  // skipped); the arena is then compacted into a larger one and the batch
+  // applied again.
+  for (int attempt = 0;; ++attempt) {
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), s));
+    {
+      int p = prof_begin(c);
+      c->launches += graph_apply_batch(c->g, c->gw, bd, c->err, s);
+      prof_end(c, p, 4, 0.0);
+    }
+    c->launches += graph_count_nnz(c->g, N + S, c->gw.scalars + 5, s);
+    CK(cudaMemcpyAsync(c->h_scal + 5, c->gw.scalars + 5, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_scal + 7, c->gw.tmp_off + (N + S), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaGetLastError());
+    st = read_back(c, 0);
+    if (st != GREST_OK) return st;
+    if (*c->h_err == DERR_ARENA && attempt == 0) {
+      // the merged rows of this batch need at most 1.5x their staged length plus a rounding slot each
+      const int64_t staged = c->h_scal[7];
+      st = grow_arena(c, N, staged + staged / 2 + 24 * (N + S));
+      if (st != GREST_OK) return st;
+      continue;
+    }
+    if (*c->h_err) {
+      c->prof_n = 0;
+      return map_dev_err(*c->h_err);
+    }
+    break;
   }
   c->nnz = c->h_scal[5];
   // committed: the graph now has N + S ids; until the step's pairs replace
@@ -1374,7 +1576,7 @@ static grest_status apply_update_impl(grest_ctx* c, const grest_update* u, grest
   if (S > 0) CK(cudaMemset2DAsync(c->U + N * c->ldu, sizeof(double) * c->ldu, 0, sizeof(double) * c->K, S, s));
   c->launches += graph_refresh_derived(c->g, c->gw, N + S, s);
   c->stats.rank_y = 0;
-  st = c->cfg.precision == GREST_MIXED ? step_t<float>(c, N, S, u->n_del_nodes > 0)
+  st = c->cfg.precision != GREST_FP64 ? step_t<float>(c, N, S, u->n_del_nodes > 0)
                                        : step_t<double>(c, N, S, u->n_del_nodes > 0);
   CK(cudaGetLastError());
   if (st != GREST_OK) return st;

@@ -45,12 +45,17 @@ extern "C" grest_status grest_gram_noalloc(const double* X, int64_t ldx, int32_t
                                            int32_t b, int64_t n, double* C, int64_t ldc, void* cuda_stream) {
   if (!X || !Y || !C || a < 1 || b < 1 || n < 1 || ldx < a || ldy < b || ldc < b) return GREST_ERR_INVALID_ARG;
   if (a > 256 || b > 256) return GREST_ERR_CAPACITY;  // a * b partials must fit the fixed scratch
+  // a launch error left pending on this host thread by earlier work is
+  // reported as such before anything is enqueued (and is not cleared)
+  if (cudaPeekAtLastError() != cudaSuccess) return GREST_ERR_CUDA;
   double* scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return GREST_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // with a, b <= 256 one chunk's partials (a * b <= 65,536 doubles) always
+  // fit, so the capped launcher takes every shape accepted above
   if (grest::gram_f64_capped(X, ldx, a, Y, ldy, b, n, C, ldc, scratch, kNoAllocScratchDoubles, s) != 0)
-    return GREST_ERR_CAPACITY;
-  e = cudaGetLastError();
+    return GREST_ERR_INVALID_ARG;
+  e = cudaGetLastError();  // only this call's launches can have set it
   return e == cudaSuccess ? GREST_OK : GREST_ERR_CUDA;
 }

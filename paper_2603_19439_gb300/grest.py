@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgrest.so")
 
 OP_ADJ, OP_LAP, OP_NLAP = 0, 1, 2
 SUB_GREST2, SUB_GREST3, SUB_RSVD, SUB_AUTO = 0, 1, 2, 3
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FAST = 0, 1, 2
 PROJ_EXACT, PROJ_LOWRANK = 0, 1
 WB_RESID, WB_DELTA = 0, 1
 FLAG_CHECK = 1
@@ -160,11 +160,37 @@ def default_config(k, **kw):
     return cfg
 
 
+def check_gram_args(X, Y, C, in_dtype, where, out_dtype="float64", require_cuda=True):
+    """Raise GrestError(invalid argument) unless X (n x a) and Y (n x b) are
+    2-D torch tensors of in_dtype and C (at least a x b) one of out_dtype, all
+    with unit inner stride, X and Y with equal row counts, all on a CUDA
+    device.  The kernels read n rows of X and Y and write a x b entries of C
+    through raw pointers, so a short Y or a small C would be an out-of-bounds
+    access on the device."""
+    for t, dt in ((X, in_dtype), (Y, in_dtype), (C, out_dtype)):
+        if not hasattr(t, "data_ptr") or t.dim() != 2 or str(t.dtype) != "torch." + dt:
+            raise GrestError(1, where)
+        if t.stride(1) != 1 or t.stride(0) < t.shape[1]:
+            raise GrestError(1, where)
+    if X.shape[0] != Y.shape[0] or X.shape[0] < 1 or X.shape[1] < 1 or Y.shape[1] < 1:
+        raise GrestError(1, where)
+    if C.shape[0] < X.shape[1] or C.shape[1] < Y.shape[1]:
+        raise GrestError(1, where)
+    if require_cuda and not (X.is_cuda and Y.is_cuda and C.is_cuda):
+        raise GrestError(1, where)
+
+
 def gram_noalloc(X, Y, C, stream=None):
     """C = X^T Y through grest_gram_noalloc (no device allocation inside the
     library); X, Y, C are torch CUDA float64 tensors, row-major.  Enqueued on
-    `stream` (a cudaStream_t handle or None); the caller synchronizes."""
+    `stream` (a cudaStream_t handle), by default torch's current stream of
+    the current device, so that it is ordered after the writes to X and Y;
+    the caller synchronizes."""
+    check_gram_args(X, Y, C, "float64", "grest_gram_noalloc")
     lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
     st = lib.grest_gram_noalloc(X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(), Y.stride(0), Y.shape[1],
                                 X.shape[0], C.data_ptr(), C.stride(0), stream)
     if st != 0:
@@ -427,6 +453,7 @@ class Tracker:
 
     def gram(self, X, Y, C):
         """C = X^T Y for torch CUDA float64 tensors (row-major)."""
+        check_gram_args(X, Y, C, "float64", "grest_gram")
         st = self.lib.grest_gram(self.h, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(), Y.stride(0), Y.shape[1],
                                  X.shape[0], C.data_ptr(), C.stride(0))
         if st != 0:
@@ -434,6 +461,7 @@ class Tracker:
 
     def gram_f32(self, X, Y, C):
         """C (float64) = X^T Y for torch CUDA float32 tensors (row-major)."""
+        check_gram_args(X, Y, C, "float32", "grest_gram_f32")
         st = self.lib.grest_gram_f32(self.h, X.data_ptr(), X.stride(0), X.shape[1], Y.data_ptr(), Y.stride(0),
                                      Y.shape[1], X.shape[0], C.data_ptr(), C.stride(0))
         if st != 0:

@@ -10,23 +10,59 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"], cwd=ROOT,
-                       capture_output=True, text=True, timeout=900)
+    """The reference arm's line, on the SBM workload (the oracle finishes it in
+    seconds; the 1M-node default differs only in the workload it times)."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "sbm2k", "--steps", "2",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
     d = json.loads(lines[0])
     assert d["impl"] == "reference"
-    assert d["metric"].startswith("G-REST updates/s at n=1M,k=32")
+    assert d["metric"].startswith("G-REST updates/s, SBM n=2,000")
     assert d["unit"] == "updates/s" and d["higher_is_better"] is True
-    assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] >= 3
+    assert d["n_gpus"] == 1 and 1 <= d["steps"] <= 2 and d["config"]["steps_requested"] == 2
     assert d["value"] > 0 and d["dtype"] == "f64" and d["data"] == "synthetic"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert "no scaling" in cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("Chung-Lu power-law stream n=1,000,000")
+    assert d["config"]["workload"].startswith("SBM stream n=2,000")
+
+
+def test_default_workload_is_the_1m_stream():
+    sys.path.insert(0, ROOT)
+    import bench
+    w = bench.WORKLOADS["cl1m"]
+    assert w["metric"].startswith("G-REST updates/s at n=1M,k=32")
+    assert bench.workload_desc(w).startswith("Chung-Lu power-law stream n=1,000,000 gamma=2.3 mean_degree=32 adjacency")
+    assert (w["k"], w["L"], w["P"], w["op"]) == (32, 100, 100, 0)
+    assert w["precisions"] == ("fp64", "mixed", "mixed_fast")
+
+
+def test_capacity_covers_the_driver_run():
+    """--steps 20 --warmup 5: the headline tracker applies W + K device-batch
+    steps and K end-to-end steps, 45 batches of +0.5% nodes (about 1.25 n).
+    The contexts are created with room for all of them, so no growth (and no
+    device-wide synchronizing free) falls inside a timed region."""
+    sys.path.insert(0, ROOT)
+    import bench
+    w = bench.WORKLOADS["cl1m"]
+    nb = bench.batches_needed(20, 5)
+    assert nb == 45
+    g, batches = bench.make_workload(w, nb, w["seed"], n=20_000)
+    assert len(batches) == nb
+    n_final = g.n + sum(int(b.n_new) for b in batches)
+    assert n_final > 1.2 * g.n  # more than round numbers like 1.2 n would hold
+    cap = bench.stream_node_capacity(g.n, batches)
+    assert cap >= n_final
+    # every prefix fits too (the FP64 arm stops after W + K batches)
+    run = g.n
+    for b in batches:
+        run += int(b.n_new)
+        assert run <= cap
 
 
 def _replica_worker(rank, port, out_dir):

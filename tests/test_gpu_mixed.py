@@ -1,5 +1,7 @@
-"""GPU parity of the mixed-precision path (FP32 blocks, FP64 small dense and
-FP64 refinement) against the FP64 CPU oracle on the same seeded inputs.
+"""GPU parity of the mixed-precision paths against the FP64 CPU oracle on the
+same seeded inputs: GREST_MIXED (FP32 blocks and tensor-core products, FP64
+projected problems, FP64 refinement) and GREST_MIXED_FAST (the same with FP32
+projected problems and a double-float refinement); every test runs both.
 
 Tolerances (reading of the precision targets): tracked values within
 1e-6 * |theta_1| of the oracle's; per pair, the residual ||M u - theta u||
@@ -17,6 +19,7 @@ from paper_2603_19439_gb300 import workloads as wl
 from tests import gpu_util as U
 
 pytestmark = pytest.mark.gpu
+PRECISIONS = pytest.mark.parametrize("prec", [G.MIXED, G.MIXED_FAST], ids=["mixed", "mixed_fast"])
 
 THETA_TOL = 1e-6
 RES_TOL = 1e-6
@@ -55,13 +58,14 @@ def compare_mixed(tr, st, info, op, k, where):
     return np.max(np.abs(rg - ro)) / scale
 
 
-def test_mixed_fig1_exact(cuda):
+@PRECISIONS
+def test_mixed_fig1_exact(cuda, prec):
     import json, os
     d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig1_example.json")))
     edges = [(a - 1, b - 1) for a, b in d["edges_before"]]
     g = wl.EdgeSetGraph(6, wl.keys_of([e[0] for e in edges], [e[1] for e in edges]))
     for op in (O.OP_ADJ, O.OP_LAP, O.OP_NLAP):
-        tr, st, ocfg = U.make_pair(g, 3, op, subspace=G.SUB_GREST3, precision=G.MIXED, drop_tol=1e-3)
+        tr, st, ocfg = U.make_pair(g, 3, op, subspace=G.SUB_GREST3, precision=prec, drop_tol=1e-3)
         ocfg.drop_tol = 1e-3
         ins = np.array([(a - 1, b - 1) for a, b in d["added_edges_old"] + d["added_edges_new"]], np.int32)
         dels = np.array([(a - 1, b - 1) for a, b in d["deleted_edges"]], np.int32)
@@ -76,9 +80,10 @@ def test_mixed_fig1_exact(cuda):
         tr.close()
 
 
-def test_mixed_sbm_stream(cuda):
+@PRECISIONS
+def test_mixed_sbm_stream(cuda, prec):
     g0, batches = wl.sbm_stream()
-    tr, st, ocfg = U.make_pair(g0, 8, O.OP_ADJ, precision=G.MIXED, drop_tol=1e-3)
+    tr, st, ocfg = U.make_pair(g0, 8, O.OP_ADJ, precision=prec, drop_tol=1e-3)
     ocfg.drop_tol = 1e-3
     worst = 0.0
     for t, b in enumerate(batches):
@@ -89,9 +94,10 @@ def test_mixed_sbm_stream(cuda):
     tr.close()
 
 
-def test_mixed_rsvd_nlap_stream(cuda):
+@PRECISIONS
+def test_mixed_rsvd_nlap_stream(cuda, prec):
     g0, batches = wl.chung_lu_stream(4000, 2.5, 12, 3, 0.02, 6, 0.002, seed=11, lcc=True)
-    tr, st, ocfg = U.make_pair(g0, 8, O.OP_NLAP, L=20, P=12, seed=5, precision=G.MIXED, drop_tol=1e-3)
+    tr, st, ocfg = U.make_pair(g0, 8, O.OP_NLAP, L=20, P=12, seed=5, precision=prec, drop_tol=1e-3)
     ocfg.drop_tol = 1e-3
     for t, b in enumerate(batches):
         st, info = O.grest_step(st, b, ocfg)
@@ -101,11 +107,12 @@ def test_mixed_rsvd_nlap_stream(cuda):
     tr.close()
 
 
-def test_mixed_check_flag_reports_fp64_residuals(cuda):
+@PRECISIONS
+def test_mixed_check_flag_reports_fp64_residuals(cuda, prec):
     """GREST_FLAG_CHECK: orthonormality and Galerkin residual of the refined
     pairs are at FP64 level; the max residual matches the one computed here."""
     g0, batches = wl.sbm_stream(n0=600, steps=2, n_new=20, n_rand=60)
-    tr, st, ocfg = U.make_pair(g0, 6, O.OP_ADJ, precision=G.MIXED, drop_tol=1e-3, flags=G.FLAG_CHECK)
+    tr, st, ocfg = U.make_pair(g0, 6, O.OP_ADJ, precision=prec, drop_tol=1e-3, flags=G.FLAG_CHECK)
     ocfg.drop_tol = 1e-3
     for b in batches:
         st, info = O.grest_step(st, b, ocfg)
@@ -118,14 +125,15 @@ def test_mixed_check_flag_reports_fp64_residuals(cuda):
     tr.close()
 
 
-def test_mixed_more_than_32_pairs(cuda):
+@PRECISIONS
+def test_mixed_more_than_32_pairs(cuda, prec):
     """K = 40 tracked pairs with L + P = 32 < K: the refinement's K x K
     products and double-float kernels in their two-columns-per-lane forms,
     the projections on the tensor-core Gram, on a power-law stream with the
     RSVD new-node block (normalized Laplacian: algebraic ordering, so no
     +-theta near-ties at the K boundary)."""
     g0, batches = wl.chung_lu_stream(3000, 2.4, 14, 2, 0.02, 6, 0.002, seed=21, lcc=True)
-    tr, st, ocfg = U.make_pair(g0, 40, O.OP_NLAP, L=20, P=12, seed=3, precision=G.MIXED, drop_tol=1e-3)
+    tr, st, ocfg = U.make_pair(g0, 40, O.OP_NLAP, L=20, P=12, seed=3, precision=prec, drop_tol=1e-3)
     ocfg.drop_tol = 1e-3
     for t, b in enumerate(batches):
         st, info = O.grest_step(st, b, ocfg)

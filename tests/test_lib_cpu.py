@@ -199,3 +199,36 @@ def test_null_handles_rejected_without_gpu(lib):
     L.grest_destroy(None)
     L.grest_batch_destroy(None)
     L.grest_server_destroy(None)
+
+
+def test_gram_bindings_reject_bad_tensors_before_the_library():
+    """grest_gram / grest_gram_f32 / grest_gram_noalloc take raw pointers, so
+    the binding checks shapes, dtypes, strides and the device before the
+    call: a short Y or a small C would otherwise be read or written out of
+    bounds on the GPU."""
+    torch = pytest.importorskip("torch")
+    from paper_2603_19439_gb300 import grest
+    f64 = torch.float64
+    X, Y, C = torch.zeros((50, 4), dtype=f64), torch.zeros((50, 3), dtype=f64), torch.zeros((4, 3), dtype=f64)
+    grest.check_gram_args(X, Y, C, "float64", "t", require_cuda=False)  # well formed
+    bad = [
+        (X, torch.zeros((49, 3), dtype=f64), C),            # Y shorter than X
+        (X, Y, torch.zeros((3, 3), dtype=f64)),             # C has fewer rows than X has columns
+        (X, Y, torch.zeros((4, 2), dtype=f64)),             # C has fewer columns than Y
+        (X.float(), Y, C),                                  # dtype
+        (X, Y, C.float()),                                  # output dtype
+        (X.t(), torch.zeros((4, 3), dtype=f64), C),         # inner stride != 1
+        (X[:, None, :], Y, C),                              # not 2-D
+        (torch.zeros((0, 4), dtype=f64), torch.zeros((0, 3), dtype=f64), C),  # no rows
+    ]
+    for args in bad:
+        with pytest.raises(grest.GrestError) as e:
+            grest.check_gram_args(*args, "float64", "t", require_cuda=False)
+        assert e.value.code == 1
+    # host tensors are rejected by the public wrappers (a CUDA device is required)
+    with pytest.raises(grest.GrestError) as e:
+        grest.gram_noalloc(X, Y, C)
+    assert e.value.code == 1
+    with pytest.raises(grest.GrestError) as e:
+        grest.check_gram_args(X.float(), Y.float(), C, "float32", "grest_gram_f32")
+    assert e.value.code == 1
