@@ -196,10 +196,15 @@ def random_graph(n, p, seed):
 
 @pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP, O.OP_NLAP])
 def test_exact_when_subspace_is_whole_space(op):
+    """With K = 7, N = 14 and S = 4, the basis [X_bar, W, B] has up to
+    2K + S = 18 = N' columns; when it spans the whole space, H = Z^T M Z is
+    similar to M, so every Ritz value is an eigenvalue of the dense operator
+    and the tracked pairs are the exact leading ones."""
     rng = np.random.default_rng(1)
+    hits = 0
     for trial in range(4):
         g = random_graph(14, 0.35, 10 + trial)
-        K = 5
+        K = 7
         rp, col, _ = g.csr()
         st = O.init_state(g.n, rp, col, None, K, op)
         b = wl.random_churn_batch(g, 4, 3, 3, rng)
@@ -207,11 +212,16 @@ def test_exact_when_subspace_is_whole_space(op):
         Md = O.dense_operator(st2.A, st2.live, op)
         ev, V = np.linalg.eigh(Md)
         o = O.select_order(ev, op)
-        Zr = np.linalg.matrix_rank(info.Z)
+        assert np.linalg.matrix_rank(info.Z) == info.m
         if info.m == Md.shape[0]:
+            hits += 1
+            assert np.allclose(np.sort(info.ritz_all), np.sort(ev), atol=1e-11)
             assert np.allclose(st2.lam, ev[o[:K]], atol=1e-11)
-        # Ritz values always interlace (Cauchy): see the dedicated test
-        assert Zr == info.m
+            # the tracked subspace is the exact one where the K / K+1 boundary is separated
+            key = np.abs(ev[o]) if op == O.OP_ADJ else ev[o]
+            if abs(key[K - 1] - key[K]) > 1e-6:
+                assert sin_angle(V[:, o[:K]], st2.X) < 1e-9
+    assert hits >= 3, f"the whole-space case was reached in {hits} of 4 trials"
 
 
 @pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP, O.OP_NLAP])
@@ -374,17 +384,33 @@ def test_prop4_rank_bound_of_delta2():
 
 # ------------------------------------------------------- modes and readings
 
-def test_resid_block_equals_delta_block_at_exact_eigvecs():
-    """Reading R2: P_perp(M_new X_bar) = P_perp(Delta X_bar) + P_perp(A_bar X_bar),
-    and A_bar X_bar = X_bar Lambda when X is exact, so both blocks give one Z."""
+def _alpha(A, live, op):
+    return O.operator_matrix(A, live, op)[1]
+
+
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP])
+def test_resid_block_equals_delta_block_at_exact_eigvecs(op):
+    """Reading R2: P_perp(M_new X_bar) = P_perp(Delta X_bar) + P_perp(M_old X_bar)
+    with M_old padded by zero rows, and M_old X_bar = X_bar Lambda when X is
+    exact, so both blocks give one Z.  For the shifted Laplacian (Sec. 4.2)
+    the batch raises d_max, so Delta carries the change of alpha = 2 d_max on
+    every old diagonal entry besides the degree changes (reading R9)."""
     rng = np.random.default_rng(7)
     g = random_graph(70, 0.12, 31)
     rp, col, _ = g.csr()
     K = 5
-    st = O.init_state(g.n, rp, col, None, K, O.OP_ADJ)  # exact (dense eigh)
+    st = O.init_state(g.n, rp, col, None, K, op)  # exact (dense eigh)
     b = wl.random_churn_batch(g, 5, 6, 4, rng)
-    s1, i1 = O.grest_step(st, b, O.Config(k=K, w_block=O.WB_RESID, subspace=O.SUB_GREST3), keep=True)
-    s2, i2 = O.grest_step(st, b, O.Config(k=K, w_block=O.WB_DELTA, subspace=O.SUB_GREST3), keep=True)
+    if op == O.OP_LAP:  # three new edges at the node of largest degree: d_max and alpha grow
+        hub = int(np.argmax(np.diff(rp)))
+        others = [v for v in range(g.n) if v != hub and not g.has(wl.keys_of(np.array([hub]), np.array([v])))[0]]
+        extra = np.array(others[:3], np.int32)
+        b = wl.Batch(b.n_new, np.concatenate([b.ins_u, np.full(3, hub, np.int32)]),
+                     np.concatenate([b.ins_v, extra]), b.del_u, b.del_v, b.del_nodes)
+    s1, i1 = O.grest_step(st, b, O.Config(k=K, op=op, w_block=O.WB_RESID, subspace=O.SUB_GREST3), keep=True)
+    s2, i2 = O.grest_step(st, b, O.Config(k=K, op=op, w_block=O.WB_DELTA, subspace=O.SUB_GREST3), keep=True)
+    if op == O.OP_LAP:
+        assert _alpha(s1.A, s1.live, op) > _alpha(st.A, st.live, op)
     assert i1.m == i2.m
     assert np.allclose(s1.lam, s2.lam, rtol=1e-10, atol=1e-12)
     assert sin_angle(i1.Z, i2.Z) < 1e-8
@@ -412,16 +438,32 @@ def test_rsvd_equals_exact_when_delta2_low_rank():
     assert sin_angle(ex.X, rs.X) < 1e-8
 
 
-def test_lowrank_equals_exact_when_all_pairs_tracked():
-    """Eq. (main3) replaces A_bar by X_bar Lambda X_bar^T; with K = N that is exact."""
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP])
+def test_lowrank_equals_exact_when_all_pairs_tracked(op):
+    """Eq. (main3) replaces M_old by X_bar Lambda X_bar^T; with K = N that is
+    exact, so H = (X_bar^T Z)^T Lambda (X_bar^T Z) + Z^T Delta Z equals
+    Z^T M_new Z.  For the shifted Laplacian this fixes Delta's diagonal:
+    alpha_new - alpha_old minus the degree change on old rows, and
+    alpha_new - d on the rows of new nodes (reading R9); the batch adds
+    nodes and raises d_max so both are exercised."""
     rng = np.random.default_rng(9)
     g = random_graph(12, 0.4, 51)
     rp, col, _ = g.csr()
     K = 12
-    st = O.init_state(g.n, rp, col, None, K, O.OP_ADJ)
+    st = O.init_state(g.n, rp, col, None, K, op)
     b = wl.random_churn_batch(g, 2, 2, 2, rng)
-    e1, _ = O.grest_step(st, b, O.Config(k=K, projection=O.PROJ_EXACT, subspace=O.SUB_GREST3))
-    e2, _ = O.grest_step(st, b, O.Config(k=K, projection=O.PROJ_LOWRANK, subspace=O.SUB_GREST3))
+    if op == O.OP_LAP:
+        hub = int(np.argmax(np.diff(rp)))
+        free = [v for v in range(g.n) if v != hub and not g.has(wl.keys_of(np.array([hub]), np.array([v])))[0]
+                and not any({hub, v} == {int(a), int(c)} for a, c in zip(b.ins_u, b.ins_v))]
+        b = wl.Batch(b.n_new, np.concatenate([b.ins_u, np.array([hub, hub], np.int32)]),
+                     np.concatenate([b.ins_v, np.array([12, free[0]], np.int32)]), b.del_u, b.del_v, b.del_nodes)
+    e1, i1 = O.grest_step(st, b, O.Config(k=K, op=op, projection=O.PROJ_EXACT, subspace=O.SUB_GREST3))
+    e2, i2 = O.grest_step(st, b, O.Config(k=K, op=op, projection=O.PROJ_LOWRANK, subspace=O.SUB_GREST3))
+    if op == O.OP_LAP:
+        assert _alpha(e1.A, e1.live, op) > _alpha(st.A, st.live, op)
+    assert b.n_new == 2
+    assert np.allclose(i1.ritz_all, i2.ritz_all, atol=1e-11)
     assert np.allclose(e1.lam, e2.lam, atol=1e-11)
 
 
@@ -431,24 +473,64 @@ def test_grest2_subspace_ignores_new_node_block():
     assert info.m <= 2 * 6
 
 
-def test_node_deletion_reading():
-    """Reading R11: the result equals G-REST run on the live principal submatrix."""
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP, O.OP_NLAP])
+def test_node_deletion_reading(op):
+    """Reading R11 on a step that removes nodes: removed ids have zero rows
+    in X and M; the Ritz values interlace the spectrum of the live principal
+    submatrix (Cauchy: Z restricted to the live rows is orthonormal); the
+    Galerkin condition holds; and the output is orthonormal."""
     rng = np.random.default_rng(10)
-    g = random_graph(16, 0.4, 61)
+    g = random_graph(40, 0.2, 61)
     rp, col, _ = g.csr()
-    K = 4
-    st = O.init_state(g.n, rp, col, None, K, O.OP_ADJ)
-    b = wl.random_churn_batch(g, 3, 2, 2, rng, n_del_nodes=2)
-    st2, info = O.grest_step(st, b, O.Config(k=K, subspace=O.SUB_GREST3), keep=True)
+    K = 5
+    st = O.init_state(g.n, rp, col, None, K, op)
+    b = wl.random_churn_batch(g, 3, 4, 3, rng, n_del_nodes=3)
+    st2, info = O.grest_step(st, b, O.Config(k=K, op=op, subspace=O.SUB_GREST3), keep=True)
     dead = np.asarray(b.del_nodes)
+    assert dead.size == 3
     assert np.all(st2.X[dead] == 0) and not st2.live[dead].any()
-    Md = O.dense_operator(st2.A, st2.live, O.OP_ADJ)
+    Md = O.dense_operator(st2.A, st2.live, op)
     assert np.all(Md[dead] == 0) and np.all(Md[:, dead] == 0)
     livei = np.flatnonzero(st2.live)
-    ev = np.linalg.eigvalsh(Md[np.ix_(livei, livei)])
-    o = O.select_order(ev, O.OP_ADJ)
-    if info.m == livei.size:
+    Z = info.Z
+    assert np.all(Z[dead] == 0)
+    assert np.abs(Z.T @ Z - np.eye(Z.shape[1])).max() < 1e-13
+    lam = np.sort(np.linalg.eigvalsh(Md[np.ix_(livei, livei)]))[::-1]
+    th = np.sort(info.ritz_all)[::-1]
+    m = th.size
+    assert np.all(th <= lam[:m] + 1e-10) and np.all(th[::-1] >= lam[::-1][:m] - 1e-10)
+    R = Md @ st2.X - st2.X * st2.lam
+    assert np.abs(Z.T @ R).max() < 1e-10 * max(1.0, abs(st2.lam).max())
+    assert np.abs(st2.X.T @ st2.X - np.eye(K)).max() < 1e-13
+
+
+@pytest.mark.parametrize("op", [O.OP_ADJ, O.OP_LAP, O.OP_NLAP])
+def test_node_deletion_exact_on_whole_live_space(op):
+    """Reading R11 with exactness: N = 10, two nodes removed and S = 2 added,
+    K = 4, so [X_bar, W, B] (at most 2K + S = 10 columns) can span all 10 live
+    ids; then the tracked pairs are exactly the leading pairs of the live
+    principal submatrix, which only holds if the masked X_bar was
+    re-orthonormalized correctly."""
+    hits = 0
+    for trial in range(4):
+        rng = np.random.default_rng(100 + trial)
+        g = random_graph(10, 0.5, 70 + trial)
+        rp, col, _ = g.csr()
+        K = 4
+        st = O.init_state(g.n, rp, col, None, K, op)
+        b = wl.random_churn_batch(g, 2, 2, 1, rng, n_del_nodes=2)
+        st2, info = O.grest_step(st, b, O.Config(k=K, op=op, subspace=O.SUB_GREST3), keep=True)
+        livei = np.flatnonzero(st2.live)
+        assert livei.size == 10
+        if info.m != livei.size:
+            continue
+        hits += 1
+        Md = O.dense_operator(st2.A, st2.live, op)
+        ev = np.linalg.eigvalsh(Md[np.ix_(livei, livei)])
+        o = O.select_order(ev, op)
+        assert np.allclose(np.sort(info.ritz_all), np.sort(ev), atol=1e-11)
         assert np.allclose(st2.lam, ev[o[:K]], atol=1e-11)
+    assert hits >= 2, f"the whole-live-space case was reached in {hits} of 4 trials"
 
 
 def test_ordering_and_signs():
