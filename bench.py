@@ -281,12 +281,12 @@ def roofline(prof_ms, prof_work, prof_bytes, prof_launch, traffic_file, precisio
         ms = float(prof_ms[cls])
         if ms <= 0:
             return None
-        if name in ("spmm", "graph") or (precision == "mixed" and name in ("gram", "gemm")):
+        if name in ("spmm", "graph") or (precision != "fp64" and name in ("gram", "gemm")):
             return {"bound": "hbm", "unit": "GB/s", "achieved": prof_bytes[cls] / (ms * 1e-3) / 1e9, "peak": hbm,
                     "peak_source": hbm_src}
         if precision == "fp64" or name == "small":
             peak, src = FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"
-            if precision == "mixed":
+            if precision == "mixed_fast":  # its projected problems run in FP32 arithmetic
                 peak, src = FP32_PEAK_TFLOPS, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (derived)"
             return {"bound": "alu", "unit": "TFLOP/s", "achieved": prof_work[cls] / (ms * 1e-3) / 1e12, "peak": peak,
                     "peak_source": src}
@@ -555,8 +555,7 @@ def run_grest(args):
                                                         "pivot_kept_min", "boundary_gap", "ms_refine")},
                 "accuracy": accuracy(r),
                 "roofline": roofline(r["prof"]["ms"] / steps, r["prof"]["work"] / steps, r["prof"]["bytes"] / steps,
-                                     r["prof"]["n"] / steps, os.path.join(ROOT, "profiles", "traffic.json"),
-                                     "fp64" if p == "fp64" else "mixed"),
+                                     r["prof"]["n"] / steps, os.path.join(ROOT, "profiles", "traffic.json"), p),
                 "clocks": r["clk"]}
 
     main = results[headline]

@@ -184,6 +184,13 @@ void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy,
 // partials fit in part_cap doubles; returns -1 when even one chunk does not fit.
 int gram_f64_capped(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
                     int64_t ldc, double* part, int64_t part_cap, cudaStream_t s);
+// G = X^T X and H = X^T Y for n x k FP64 blocks X, Y (shared ld, k <= 64),
+// computing only the upper triangles (H is taken as symmetric: X^T M X for a
+// symmetric M) and writing both in full (k x k, ld k).  part must hold
+// 2 k^2 doubles per row chunk (at most part_cap in all).  Returns the number
+// of kernels launched, -1 when nothing fits.
+int gram_pair_sym_f64(const double* X, const double* Y, int64_t ld, int k, int64_t n, double* G, double* H,
+                      double* part, int64_t part_cap, cudaStream_t s);
 // Out (n x c, ldo) = beta * Cin (n x c, ldc) + alpha * X (n x a, ldx) * B (a x c, row-major ldb).
 void gemm_nn_f64(int64_t n, int a, int c, double alpha, const double* X, int64_t ldx, const double* B,
                  int64_t ldb, double beta, const double* Cin, int64_t ldc, double* Out, int64_t ldo,

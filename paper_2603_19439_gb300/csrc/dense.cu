@@ -752,6 +752,104 @@ void gram_reduce_launch(const double* part, int64_t chunks, int a, int b, double
     k_gram_reduce<<<(unsigned)cdiv(tot, 256), 256, 0, s>>>(part, chunks, a, b, C, ldc, false, 64, 64);
 }
 
+namespace {
+
+// Upper triangles of G = X^T X and H = X^T Y (k <= 64 columns) over one row
+// chunk.  The work is split into 4 x 4 blocks (bi <= bj) of G and of H, one
+// per thread, so every warp except the last does only needed products: on
+// this part an FP64 warp instruction costs its sub-partition the same
+// whatever its active lanes.
+constexpr int kPairRows = 32;
+
+__global__ void __launch_bounds__(288) k_gram_pair_upper(const double* __restrict__ X, const double* __restrict__ Y,
+                                                         int64_t ld, int k, int64_t n, int64_t rows_per_chunk,
+                                                         double* __restrict__ part) {
+  __shared__ double Xs[kPairRows][64 + 1];
+  __shared__ double Ys[kPairRows][64 + 1];
+  const int nb = (k + 3) / 4, npairs = nb * (nb + 1) / 2;
+  const int t = threadIdx.x;
+  const bool active = t < 2 * npairs;
+  const int which = t < npairs ? 0 : 1;  // 0: X^T X, 1: X^T Y
+  int pi = active ? t - which * npairs : 0, bi = 0;
+  while (pi >= nb - bi) { pi -= nb - bi; ++bi; }
+  const int bj = bi + pi;
+  const int64_t chunk = blockIdx.x;
+  const int64_t rbeg = chunk * rows_per_chunk;
+  const int64_t rend = rbeg + rows_per_chunk < n ? rbeg + rows_per_chunk : n;
+  double acc[4][4] = {};
+  for (int64_t r0 = rbeg; r0 < rend; r0 += kPairRows) {
+    for (int e = t; e < kPairRows * k; e += blockDim.x) {
+      const int rr = e / k, cc = e % k;
+      const int64_t r = r0 + rr;
+      Xs[rr][cc] = r < rend ? X[r * ld + cc] : 0.0;
+      Ys[rr][cc] = r < rend ? Y[r * ld + cc] : 0.0;
+    }
+    for (int e = t; e < kPairRows * (nb * 4 - k); e += blockDim.x) {  // zero the padding columns
+      const int rr = e / (nb * 4 - k), cc = k + e % (nb * 4 - k);
+      Xs[rr][cc] = 0.0;
+      Ys[rr][cc] = 0.0;
+    }
+    __syncthreads();
+    if (active) {
+      double (*B)[64 + 1] = which ? Ys : Xs;
+#pragma unroll 4
+      for (int kk = 0; kk < kPairRows; ++kk) {
+        double xa[4], yb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          xa[u] = Xs[kk][bi * 4 + u];
+          yb[u] = B[kk][bj * 4 + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  double* P = part + (chunk * 2 + which) * (int64_t)k * k;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = bi * 4 + u, j = bj * 4 + v;
+      if (i < k && j < k) P[(int64_t)i * k + j] = acc[u][v];
+    }
+}
+
+// G and H in full: entry (i, j) is read from the computed block of the upper
+// triangle, (j, i) when block (i/4, j/4) lies below the diagonal
+__global__ void k_gram_pair_reduce(const double* __restrict__ part, int64_t chunks, int k, double* G, double* H) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * k * k) return;
+  const int which = e / (k * k), ij = e % (k * k), i = ij / k, j = ij % k;
+  const int src = (i / 4 <= j / 4) ? ij : j * k + i;
+  double sum = 0.0;
+  for (int64_t c = 0; c < chunks; ++c) sum += part[(c * 2 + which) * (int64_t)k * k + src];
+  (which ? H : G)[ij] = sum;
+}
+
+}  // namespace
+
+int gram_pair_sym_f64(const double* X, const double* Y, int64_t ld, int k, int64_t n, double* G, double* H,
+                      double* part, int64_t part_cap, cudaStream_t s) {
+  if (k < 1 || k > 64 || n < 1) return -1;
+  const int nb = (k + 3) / 4;
+  const int threads = (2 * nb * (nb + 1) / 2 + 31) / 32 * 32;
+  int64_t chunks = 152 * 4;
+  const int64_t slabs = cdiv(n, kPairRows);
+  if (chunks > slabs) chunks = slabs;
+  if (chunks > part_cap / (2 * (int64_t)k * k)) chunks = part_cap / (2 * (int64_t)k * k);
+  if (chunks < 1) return -1;
+  const int64_t rpc = cdiv(cdiv(n, chunks), kPairRows) * kPairRows;
+  chunks = cdiv(n, rpc);
+  k_gram_pair_upper<<<(unsigned)chunks, threads, 0, s>>>(X, Y, ld, k, n, rpc, part);
+  k_gram_pair_reduce<<<(unsigned)cdiv(2 * (int64_t)k * k, 256), 256, 0, s>>>(part, chunks, k, G, H);
+  return 2;
+}
+
 void gram_f64(const double* X, int64_t ldx, int a, const double* Y, int64_t ldy, int b, int64_t n, double* C,
               int64_t ldc, double* part, bool symmetric, cudaStream_t s) {
   gram_t<double>(X, ldx, a, Y, ldy, b, n, C, ldc, part, symmetric, 0, s);

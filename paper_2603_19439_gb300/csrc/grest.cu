@@ -749,8 +749,9 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
 }
 
 // Mixed path, A11 in FP64 arithmetic (GREST_MIXED): X64 = U32 widened
-// exactly, MU = M U32 with FP64 products and sums, G = X64^T X64 and
-// H' = X64^T MU as FP64 Grams; then the same K x K Rayleigh-Ritz problem as
+// exactly, MU = M X64 with FP64 products and sums, G = X64^T X64 and
+// H' = X64^T MU as FP64 Grams (upper triangles only: both are symmetric,
+// H' because M is); then the same K x K Rayleigh-Ritz problem as
 // refine_mixed (FP64), and X = X64 (T F'') as an FP64 GEMM.  The previous
 // pairs in U are no longer read at this point of the step, so U holds MU
 // until the lift overwrites it.
@@ -764,9 +765,12 @@ grest_status refine_mixed_f64(grest_ctx* c, int64_t N2) {
   convert_f32_to_f64(c->U32, ldu, X64, ldu, N2, K, s);
   c->launches += 1;
   prof_end(c, p, 2, 0.0, 12.0 * N2 * K);
-  spmm(c, c->U32, ldu, MU, ldu, K, 0, N2, 0);
-  gram(c, X64, ldu, K, X64, ldu, K, N2, c->G, K, true);
-  gram(c, X64, ldu, K, MU, ldu, K, N2, c->H, K, false);
+  spmm(c, X64, ldu, MU, ldu, K, 0, N2, 0);
+  p = prof_begin(c);
+  const int nl = gram_pair_sym_f64(X64, MU, ldu, K, N2, c->G, c->H, c->part, c->part_cap, s);
+  if (nl < 0) return GREST_ERR_CAPACITY;
+  c->launches += nl;
+  prof_end(c, p, 1, 2.0 * N2 * K * (K + 1), 16.0 * N2 * K);
   p = prof_begin(c);
   c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
