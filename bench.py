@@ -748,13 +748,18 @@ def run_batched(args):
 def run_serve(args):
     """--serve: the serving loop (grest_server_*) under a Poisson stream of
     update requests for many resident Chung-Lu graphs.  Graph i: n
-    log-uniform on [10,000, 200,000], mean degree 16, gamma 2.3, K uniform on
-    {16..32}, FP64.  A request carries E edges, E log-uniform on [100, 10,000]
-    (capped at 5% of the graph's edges): a quarter attaches new nodes (8 edges
-    each), half are uniform inserts, a quarter uniform deletes.  The arrival
-    rate is 80% of the rate the server sustained on one request per graph
-    submitted at once.  Latency = arrival -> completion.  One JSON line."""
-    import threading
+    log-uniform on [--serve-nmin, --serve-nmax] (10,000 .. 2,000,000), mean
+    degree 16, gamma 2.3, K uniform on {16..32}.  A request carries E edges,
+    E log-uniform on [100, --serve-emax] (100,000; capped at 10% of the
+    graph's edges): a quarter attaches new nodes (8 edges each), half are
+    uniform inserts, a quarter uniform deletes.  Each precision arm (mixed,
+    then FP64) serves the same graphs from the same initial pairs and the
+    same requests: one calibration round (one request per graph at once,
+    admissions included) sets the sustained rate, and the measured stream
+    arrives as a Poisson process at 80% of it.  Latency = arrival ->
+    completion.  With --hbm-budget-gb below the resident total, graphs are
+    admitted as memory frees up (--evict: idle graphs are checkpointed to
+    host memory).  One JSON line."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -766,7 +771,7 @@ def run_serve(args):
     t0 = time.time()
     graphs, ks = [], []
     for i in range(ng):
-        n = int(np.exp(rng.uniform(np.log(10000), np.log(200000))))
+        n = int(np.exp(rng.uniform(np.log(args.serve_nmin), np.log(args.serve_nmax))))
         graphs.append(wl.chung_lu_graph(n, 2.3, 16, 20260308 + i))
         ks.append(int(rng.integers(16, 33)))
     # requests: a calibration round (one per graph) and then nreq Poisson arrivals
@@ -775,71 +780,82 @@ def run_serve(args):
     reqs = []
     for gi in order:
         gb = copies[gi]
-        E = int(np.exp(rng.uniform(np.log(100), np.log(10000))))
-        E = max(8, min(E, gb.n_edges // 20))
+        E = int(np.exp(rng.uniform(np.log(100), np.log(args.serve_emax))))
+        E = max(8, min(E, gb.n_edges // 10))
         b = wl.random_churn_batch(gb, max(1, E // 32), E // 2, E // 4, rng, new_edges_per_node=8)
         gb.apply(b)
         reqs.append((gi, b))
+    del copies
+    csrs = [wl.csr_fast(g) for g in graphs]
     t_gen = time.time() - t0
-    budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else 1 << 50
-    sv = G.Server(n_workers=args.threads, hbm_budget=budget)
-    if args.evict:
-        sv.set_eviction(True)
+    # initial pairs once per graph (the library's FP64 device solver), shared by both arms
     t0 = time.time()
-    extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if args.batched_precision == "mixed" else {}
-    gids = [sv.add_graph(g.n, *wl.csr_fast(g), k, node_capacity=stream_node_capacity(
-                g.n, [b for gi, b in reqs if gi == i]), **extra) for i, (g, k) in enumerate(zip(graphs, ks))]
-    # calibration: one request per graph at once (admission and device initial pairs happen here)
-    tc = time.perf_counter()
-    cal = [sv.submit(gids[gi], b) for gi, b in reqs[:ng]]
-    for t in cal:
-        sv.wait(t)
-    t_cal = time.perf_counter() - tc
-    # the sustained rate, measured on a second round without the admission cost
-    tc = time.perf_counter()
-    second = [(gi, b) for gi, b in reqs[ng:2 * ng]]
-    cal2 = [sv.submit(gids[gi], b) for gi, b in second]
-    for t in cal2:
-        sv.wait(t)
-    cap = len(second) / (time.perf_counter() - tc)
-    rate = 0.8 * cap
-    stream = reqs[2 * ng:]
-    gaps = rng.exponential(1.0 / rate, size=len(stream))
-    arrivals = []
-    tickets = []
-    start = time.perf_counter()
-    for (gi, b), gap in zip(stream, gaps):
-        target = (arrivals[-1] if arrivals else start) + gap
-        now = time.perf_counter()
-        if target > now:
-            time.sleep(target - now)
-        arrivals.append(time.perf_counter())
-        tickets.append(sv.submit(gids[gi], b))
-    lat = []
-    codes = []
-    for t in tickets:
-        code, _, wait_ms, run_ms = sv.wait(t)
-        codes.append(code)
-        lat.append(wait_ms + run_ms)
-    wall = time.perf_counter() - start
-    used, nres = sv.resident()
-    adm, evc, rst = sv.counters()
+    pairs = []
+    for g, (rp, col, val), k in zip(graphs, csrs, ks):
+        tr = G.Tracker(g.n, rp, col, val, None, None, k)
+        U0, th0, _ = tr.embedding()
+        tr.close()
+        pairs.append((U0, th0))
+    t_pairs = time.time() - t0
+    gaps = rng.exponential(1.0, size=nreq)
+    budget = int(args.hbm_budget_gb * 1e9) if args.hbm_budget_gb > 0 else 1 << 50
+    arms = {}
+    for prec in args.serve_precisions.split(","):
+        sv = G.Server(n_workers=args.threads, hbm_budget=budget)
+        if args.evict:
+            sv.set_eviction(True)
+        extra = dict(precision=G.MIXED, drop_tol=MIXED_DROP_TOL) if prec == "mixed" else {}
+        gids = [sv.add_graph(g.n, rp, col, val, k, U0=U0, theta0=th0,
+                             node_capacity=stream_node_capacity(g.n, [b for gi, b in reqs if gi == i]), **extra)
+                for i, (g, (rp, col, val), k, (U0, th0)) in enumerate(zip(graphs, csrs, ks, pairs))]
+        # calibration: one request per graph at once (admissions happen here)
+        tc = time.perf_counter()
+        cal = [sv.submit(gids[gi], b) for gi, b in reqs[:ng]]
+        cal_codes = [sv.wait(t)[0] for t in cal]
+        t_cal = time.perf_counter() - tc
+        cap = ng / t_cal
+        rate = 0.8 * cap
+        stream = reqs[ng:]
+        arrivals, tickets = [], []
+        start = time.perf_counter()
+        for (gi, b), gap in zip(stream, gaps / rate):
+            target = (arrivals[-1] if arrivals else start) + gap
+            now = time.perf_counter()
+            if target > now:
+                time.sleep(target - now)
+            arrivals.append(time.perf_counter())
+            tickets.append(sv.submit(gids[gi], b))
+        lat, codes, runs = [], [], []
+        for t in tickets:
+            code, _, wait_ms, run_ms = sv.wait(t)
+            codes.append(code)
+            lat.append(wait_ms + run_ms)
+            runs.append(run_ms)
+        wall = time.perf_counter() - start
+        used, nres = sv.resident()
+        adm, evc, rst = sv.counters()
+        arms[prec] = {"updates_per_s": len(stream) / wall, "arrival_rate_per_s": rate, "sustained_rate_per_s": cap,
+                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                     "max": float(np.max(lat))},
+                      "run_ms": {"p50": float(np.percentile(runs, 50)), "p99": float(np.percentile(runs, 99))},
+                      "failed": int(sum(c != 0 for c in codes) + sum(c != 0 for c in cal_codes)),
+                      "resident_graphs_at_end": nres, "resident_bytes_at_end": used,
+                      "admissions": adm, "evictions": evc, "restores": rst,
+                      "calibration_round_s": t_cal}
+        sv.close()
+    head = "mixed" if "mixed" in arms else next(iter(arms))
     line = {"metric": f"G-REST serving: {ng} resident Chung-Lu graphs, Poisson update requests",
-            "value": len(stream) / wall, "unit": "updates/s", "n_gpus": 1, "requests": len(stream),
-            "higher_is_better": True, "dtype": "f64" if args.batched_precision == "fp64" else "f32+f64",
-            "data": "synthetic", "workers": args.threads,
-            "arrival_rate_per_s": rate, "sustained_rate_per_s": cap,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(np.max(lat))},
-            "failed": int(sum(c != 0 for c in codes)), "resident_graphs": nres, "resident_bytes": used,
+            "value": arms[head]["updates_per_s"], "unit": "updates/s", "n_gpus": 1, "requests": nreq,
+            "higher_is_better": True, "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+            "workers": args.threads, "precision": head,
+            "latency_ms": arms[head]["latency_ms"], "arms": arms,
             "hbm_budget_bytes": budget if args.hbm_budget_gb > 0 else None, "eviction": bool(args.evict),
-            "admissions": adm, "evictions": evc, "restores": rst,
             "config": {"workload": "serving Chung-Lu", "graphs": ng, "nodes_total": int(sum(g.n for g in graphs)),
-                       "K": "16..32", "edges_per_request": "100..10,000 log-uniform (<= 5% of the graph)"},
-            "setup_s": {"generate": t_gen, "first_round_with_admission": t_cal, "add": time.time() - t0},
-            "note": "latency = arrival -> completion; the first round (contexts and device initial pairs) "
-                    "is not in the measured stream"}
-    sv.close()
+                       "nodes_min": int(min(g.n for g in graphs)), "nodes_max": int(max(g.n for g in graphs)),
+                       "K": "16..32", "edges_per_request": f"100..{args.serve_emax:,} log-uniform (<= 10% of the graph)"},
+            "setup_s": {"generate": t_gen, "initial_pairs": t_pairs},
+            "note": "latency = arrival -> completion; the calibration round (admissions) is not in the measured "
+                    "stream; both arms serve the same graphs, initial pairs and requests"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -859,6 +875,10 @@ def main():
     ap.add_argument("--threads", type=int, default=16, help="--batched: host threads")
     ap.add_argument("--serve", action="store_true", help="the serving loop under Poisson update requests")
     ap.add_argument("--requests", type=int, default=256, help="--serve: measured requests")
+    ap.add_argument("--serve-nmin", type=int, default=10_000, help="--serve: smallest graph (log-uniform sizes)")
+    ap.add_argument("--serve-nmax", type=int, default=2_000_000, help="--serve: largest graph")
+    ap.add_argument("--serve-emax", type=int, default=100_000, help="--serve: largest request (edges)")
+    ap.add_argument("--serve-precisions", default="mixed,fp64", help="--serve: arms, in order")
     ap.add_argument("--hbm-budget-gb", type=float, default=0.0,
                     help="--serve: device-memory budget of the resident graphs (0 = unlimited)")
     ap.add_argument("--evict", action="store_true",

@@ -65,6 +65,72 @@ def test_server_results_equal_updates_alone():
         Ub, thb, lb = sv.embedding(gids[i])
         assert np.array_equal(Ua, Ub) and np.array_equal(tha, thb) and np.array_equal(la, lb), i
         tr.close()
+        # and every served result matches the FP64 oracle run on the same requests (Alg. 2 per request)
+        so = st
+        for t in range(3):
+            so, info = O.grest_step(so, rounds[t][i], O.Config(k=k))
+        oracle_close(Ub, thb, lb, so, info, k, f"graph {i}")
+    sv.close()
+
+
+def oracle_close(U, th, live, st, info, k, where, theta_tol=1e-10, angle_tol=1e-8):
+    """FP64 parity of a served result with the oracle: tracked values within
+    theta_tol |theta_1|, the tracked subspace (cut at separated clusters)
+    within a sin angle of angle_tol."""
+    from tests import gpu_util as U_
+    scale = abs(st.lam[0])
+    assert np.array_equal(live, st.live), where
+    assert np.max(np.abs(th - st.lam)) <= theta_tol * scale, f"{where}: {np.max(np.abs(th - st.lam)) / scale:.2e}"
+    j = U_.cluster_cut(info.ritz_all, O.OP_ADJ, k)
+    ang = U_.sin_angle(st.X[:, :j], U[:, :j])
+    assert ang <= angle_tol, f"{where}: sin angle {ang:.2e}"
+
+
+def test_mixed_server_matches_oracle_under_admission():
+    """The mixed-precision path served under a budget that holds two of four
+    graphs at once (admission and eviction to host memory exercised): every
+    request succeeds, each graph's result equals its updates applied alone,
+    and matches the FP64 oracle within the mixed path's tolerances."""
+    k = 8
+    items = graphs_and_pairs(4, 700, k)
+    rng = np.random.default_rng(11)
+    copies = [g.copy() for g, _ in items]
+    reqs = []
+    for t in range(3):
+        for i, gb in enumerate(copies):
+            b = wl.random_churn_batch(gb, 6, 24, 12, rng)
+            gb.apply(b)
+            reqs.append((i, b))
+    kw = dict(precision=G.MIXED, drop_tol=1e-3)
+    probe = max(items, key=lambda it: it[0].n)
+    pt = G.Tracker(probe[0].n, *probe[0].csr(), probe[1].X, probe[1].lam, k, **kw)
+    nbytes = pt.device_bytes()
+    pt.close()
+    sv = G.Server(n_workers=3, hbm_budget=int(2.2 * nbytes))
+    sv.set_eviction(True)
+    gids = [sv.add_graph(g.n, *g.csr(), k, U0=st.X, theta0=st.lam, **kw) for g, st in items]
+    tickets = [sv.submit(gids[i], b) for i, b in reqs]
+    assert all(sv.wait(t)[0] == 0 for t in tickets)
+    adm, evc, rst = sv.counters()
+    assert evc >= 1 and rst >= 1
+    for i, (g, st) in enumerate(items):
+        Ub, thb, lb = sv.embedding(gids[i])
+        tr = G.Tracker(g.n, *g.csr(), st.X, st.lam, k, **kw)
+        so = st
+        ocfg = O.Config(k=k, drop_tol=1e-3)
+        for j, b in reqs:
+            if j == i:
+                tr.update(b)
+                so, info = O.grest_step(so, b, ocfg)
+        Ua, tha, _ = tr.embedding()
+        tr.close()
+        assert np.array_equal(Ua, Ub) and np.array_equal(tha, thb), i
+        scale = abs(so.lam[0])
+        assert np.max(np.abs(thb - so.lam)) <= 1e-6 * scale, i
+        M, _ = O.operator_matrix(so.A, so.live, O.OP_ADJ)
+        rg = np.linalg.norm(M @ Ub - Ub * thb, axis=0)
+        ro = np.linalg.norm(M @ so.X - so.X * so.lam, axis=0)
+        assert np.max(np.abs(rg - ro)) <= 1e-6 * scale, i
     sv.close()
 
 
