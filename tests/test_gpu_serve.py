@@ -96,7 +96,7 @@ def test_mixed_server_matches_oracle_under_admission():
     rng = np.random.default_rng(11)
     copies = [g.copy() for g, _ in items]
     reqs = []
-    for t in range(3):
+    for t in range(4):
         for i, gb in enumerate(copies):
             b = wl.random_churn_batch(gb, 6, 24, 12, rng)
             gb.apply(b)
@@ -109,10 +109,15 @@ def test_mixed_server_matches_oracle_under_admission():
     sv = G.Server(n_workers=3, hbm_budget=int(2.2 * nbytes))
     sv.set_eviction(True)
     gids = [sv.add_graph(g.n, *g.csr(), k, U0=st.X, theta0=st.lam, **kw) for g, st in items]
-    tickets = [sv.submit(gids[i], b) for i, b in reqs]
-    assert all(sv.wait(t)[0] == 0 for t in tickets)
+    # three rounds at once (two graphs fit; the others are admitted as graphs
+    # go idle and are evicted), then a fourth round after all of them: it
+    # restores the graphs evicted meanwhile
+    first = [sv.submit(gids[i], b) for i, b in reqs[:12]]
+    assert all(sv.wait(t)[0] == 0 for t in first)
+    last = [sv.submit(gids[i], b) for i, b in reqs[12:]]
+    assert all(sv.wait(t)[0] == 0 for t in last)
     adm, evc, rst = sv.counters()
-    assert evc >= 1 and rst >= 1
+    assert evc >= 2 and rst >= 1
     for i, (g, st) in enumerate(items):
         Ub, thb, lb = sv.embedding(gids[i])
         tr = G.Tracker(g.n, *g.csr(), st.X, st.lam, k, **kw)
