@@ -418,6 +418,62 @@ grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const d
 void grest_destroy(grest_ctx *ctx);
 
 /*
+ * Groups: one update of many small graphs at once, Alg. 2 per graph, with
+ * every stage of the step (graph update, SpMM, Grams, block updates, the
+ * pivoted Cholesky factorizations, the eigensolves) run as ONE grouped launch
+ * for all graphs of the group.  Each graph's shapes (node count, new-node
+ * block mode, CholQR ranks, basis width m) stay in device memory, so an
+ * update of the whole group needs no host synchronization inside it: the
+ * launch sequence is captured once as a CUDA graph and replayed for every
+ * later update.  After the first successful update an autotuner times the
+ * launch shapes of the SpMM and GEMM stages that compute every row the same
+ * way (grid size, rows per warp) and keeps the fastest for the group's shape
+ * bucket, so tuning never changes a result.  Each graph's result depends only
+ * on its own data: updating it in any group, or alone in a group of one,
+ * gives bit-identical pairs.
+ *
+ * grest_group_create loads n_graphs graphs from checkpoints written by
+ * grest_checkpoint (host buffers, read only, not kept).  All must share k,
+ * op, L, P, subspace and drop_tol; the group computes in FP64 whatever the
+ * checkpoints' precision.  Supported: unweighted graphs without removed
+ * nodes, the EXACT projection and the RESID block, and 2k + L + P <= 64
+ * columns (k + max(L+P, L) + k <= 64); else GREST_ERR_UNSUPPORTED.  Each
+ * graph gets capacity_factor (1 .. 64) times its node ids and edge slots,
+ * fixed for the life of the group; a batch of a graph may carry up to a
+ * quarter of its nonzeros in edits.  Errors: GREST_ERR_INVALID_ARG (a buffer
+ * that is not a checkpoint, mismatched configurations), GREST_ERR_OOM,
+ * GREST_ERR_CUDA.
+ *
+ * grest_group_apply_updates applies updates[i] (host arrays; no node
+ * removal, no weights: else GREST_ERR_UNSUPPORTED) to graph i of the group.
+ * status (nullable, n_graphs entries) gets each graph's result; stats
+ * (nullable) each graph's step diagnostics (no timings).  A graph whose batch
+ * is invalid (Sec. 2's definition of Delta) or does not fit its capacity is
+ * left unchanged with GREST_ERR_INVALID_UPDATE / GREST_ERR_CAPACITY; the
+ * others are updated.  Returns GREST_OK, or the first failing graph's status.
+ * Returns when the update has finished on the device.
+ *
+ * grest_group_get_embedding copies graph i's (X_K, Lambda_K) to host memory
+ * (U: n x k row-major, or NULL; theta: k, or NULL); *n_out = its node count.
+ * grest_group_get_ritz_values: graph i's m Ritz values of the last update in
+ * tracking order (ritz may be NULL to query m).  grest_group_info reports
+ * whether the update is captured as a CUDA graph, the kernel launches of one
+ * update of the whole group, whether the autotuner has run, and the chosen
+ * SpMM grid, rows per warp and GEMM grid (each pointer nullable).
+ * grest_group_destroy releases the group (NULL is ignored).
+ */
+typedef struct grest_group grest_group;
+grest_status grest_group_create(int32_t n_graphs, const void *const *ckpts, const int64_t *ckpt_bytes,
+                                double capacity_factor, grest_group **out);
+grest_status grest_group_apply_updates(grest_group *group, const grest_update *updates, grest_status *status,
+                                       grest_stats *stats);
+grest_status grest_group_get_embedding(grest_group *group, int32_t i, double *U, double *theta, int64_t *n_out);
+grest_status grest_group_get_ritz_values(grest_group *group, int32_t i, double *ritz, int32_t *m);
+grest_status grest_group_info(grest_group *group, int32_t *captured, int32_t *launches_per_update, int32_t *tuned,
+                              int32_t *spmm_blocks, int32_t *spmm_rows_per_warp, int32_t *gemm_blocks);
+void grest_group_destroy(grest_group *group);
+
+/*
  * Batches: many independent graphs, one update each per call.  A batch
  * refers to existing contexts (it owns none of them; destroy them after the
  * batch); each context should have its own non-blocking CUDA stream so that

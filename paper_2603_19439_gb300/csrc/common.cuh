@@ -98,6 +98,25 @@ struct OpParams {
   const uint8_t* live;
 };
 
+// ------------------------------------------------------------ checkpoints
+// A checkpoint written by grest_checkpoint, read in place (host pointers into
+// the buffer): the compact CSR, the maintained degrees, the pairs and the
+// configuration.  ckpt_view returns false for a buffer that is not one.
+struct CkptView {
+  int64_t n, nnz, step;
+  int32_t K;
+  bool has_val;
+  grest_config cfg;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const double* deg;
+  const double* U;      // n x K row-major
+  const double* theta;  // K
+  const uint8_t* live;  // n
+};
+bool ckpt_view(const void* buf, int64_t bytes, CkptView* v);
+
 // ------------------------------------------------------------ launchers
 // scan.cu
 size_t scan_temp_bytes(int64_t n);

@@ -1731,6 +1731,33 @@ bool ckpt_parse(const void* buf, int64_t bytes, CkptHeader* h, CkptLayout* L) {
 
 }  // namespace
 
+}  // extern "C"
+
+namespace grest {
+bool ckpt_view(const void* buf, int64_t bytes, CkptView* v) {
+  CkptHeader h;
+  CkptLayout L;
+  if (!v || !ckpt_parse(buf, bytes, &h, &L)) return false;
+  const uint8_t* b = static_cast<const uint8_t*>(buf);
+  v->n = h.n;
+  v->nnz = h.nnz;
+  v->step = h.step;
+  v->K = h.K;
+  v->has_val = h.has_val != 0;
+  v->cfg = h.cfg;
+  v->rowptr = reinterpret_cast<const int64_t*>(b + L.rowptr);
+  v->col = reinterpret_cast<const int32_t*>(b + L.col);
+  v->val = v->has_val ? reinterpret_cast<const double*>(b + L.val) : nullptr;
+  v->deg = reinterpret_cast<const double*>(b + L.deg);
+  v->U = reinterpret_cast<const double*>(b + L.U);
+  v->theta = reinterpret_cast<const double*>(b + L.theta);
+  v->live = b + L.live;
+  return true;
+}
+}  // namespace grest
+
+extern "C" {
+
 grest_status grest_checkpoint(grest_ctx* c, void* buf, int64_t* bytes) {
   if (!c || !bytes) return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;

@@ -75,7 +75,8 @@ EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sy
            "grest_server_add_graph", "grest_server_submit", "grest_server_wait", "grest_server_poll", "grest_server_remove_graph",
            "grest_server_get_embedding", "grest_server_resident", "grest_server_destroy", "grest_checkpoint",
            "grest_restore", "grest_checkpoint_embedding", "grest_server_set_eviction", "grest_server_counters",
-           "grest_destroy", "grest_status_str"]
+           "grest_group_create", "grest_group_apply_updates", "grest_group_get_embedding", "grest_group_get_ritz_values",
+           "grest_group_info", "grest_group_destroy", "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -125,12 +126,19 @@ def load_library(path=None):
     lib.grest_checkpoint_embedding.argtypes = [vp, i64, vp, vp, vp, C.POINTER(i64), C.POINTER(i32)]
     lib.grest_server_set_eviction.argtypes = [vp, i32]
     lib.grest_server_counters.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.grest_group_create.argtypes = [i32, C.POINTER(vp), C.POINTER(i64), C.c_double, C.POINTER(vp)]
+    lib.grest_group_apply_updates.argtypes = [vp, C.POINTER(Update), C.POINTER(i32), C.POINTER(Stats)]
+    lib.grest_group_get_embedding.argtypes = [vp, i32, vp, vp, C.POINTER(i64)]
+    lib.grest_group_get_ritz_values.argtypes = [vp, i32, vp, C.POINTER(i32)]
+    lib.grest_group_info.argtypes = [vp] + [C.POINTER(i32)] * 6
+    lib.grest_group_destroy.argtypes = [vp]
+    lib.grest_group_destroy.restype = None
     lib.grest_destroy.argtypes = [vp]
     lib.grest_destroy.restype = None
     lib.grest_status_str.argtypes = [i32]
     lib.grest_status_str.restype = C.c_char_p
     for f in EXPORTS[:-2]:
-        if f not in ("grest_destroy", "grest_batch_destroy", "grest_server_destroy"):
+        if f not in ("grest_destroy", "grest_batch_destroy", "grest_server_destroy", "grest_group_destroy"):
             getattr(lib, f).restype = i32
     if path is None:
         _lib = lib
@@ -261,6 +269,79 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.grest_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Many small graphs updated together by grouped launches (grest_group_*):
+    one launch per stage for all graphs, the update captured as a CUDA graph,
+    launch shapes autotuned.  Built from checkpoints (bytes) of trackers."""
+
+    def __init__(self, checkpoints, capacity_factor=1.25):
+        self.lib = load_library()
+        self._blobs = [np.frombuffer(b, np.uint8) for b in checkpoints]
+        n = len(self._blobs)
+        ptrs = (C.c_void_p * n)(*[b.ctypes.data for b in self._blobs])
+        sizes = (C.c_int64 * n)(*[b.size for b in self._blobs])
+        h = C.c_void_p()
+        st = self.lib.grest_group_create(n, ptrs, sizes, float(capacity_factor), C.byref(h))
+        self._blobs = None
+        if st != 0:
+            raise GrestError(st, "grest_group_create")
+        self.h = h
+        self.n = n
+        self.k = int(np.frombuffer(checkpoints[0][12:16], np.int32)[0])
+
+    def update(self, batches):
+        """Apply batches[i] (host arrays) to graph i.  Returns (per-graph status
+        codes, per-graph step diagnostics); raises only on a call error."""
+        if len(batches) != self.n:
+            raise ValueError("one update per graph")
+        keep = [_batch_arrays(b, False) for b in batches]
+        ups = (Update * self.n)(*[_update_struct(b, a, False) for b, a in zip(batches, keep)])
+        status = (C.c_int32 * self.n)()
+        stats = (Stats * self.n)()
+        st = self.lib.grest_group_apply_updates(self.h, ups, status, stats)
+        codes = [int(x) for x in status]
+        if st != 0 and all(c == 0 for c in codes):
+            raise GrestError(st, "grest_group_apply_updates")
+        return codes, [s.as_dict() for s in stats]
+
+    def embedding(self, i):
+        n = C.c_int64()
+        st = self.lib.grest_group_get_embedding(self.h, int(i), None, None, C.byref(n))
+        if st != 0:
+            raise GrestError(st, "grest_group_get_embedding")
+        U, th = np.empty((n.value, self.k)), np.empty(self.k)
+        st = self.lib.grest_group_get_embedding(self.h, int(i), _ptr(U), _ptr(th), C.byref(n))
+        if st != 0:
+            raise GrestError(st, "grest_group_get_embedding")
+        return U, th
+
+    def ritz_values(self, i):
+        m = C.c_int32()
+        self.lib.grest_group_get_ritz_values(self.h, int(i), None, C.byref(m))
+        out = np.empty(m.value)
+        self.lib.grest_group_get_ritz_values(self.h, int(i), _ptr(out), C.byref(m))
+        return out
+
+    def info(self):
+        v = [C.c_int32() for _ in range(6)]
+        st = self.lib.grest_group_info(self.h, *[C.byref(x) for x in v])
+        if st != 0:
+            raise GrestError(st, "grest_group_info")
+        keys = ("captured", "launches_per_update", "tuned", "spmm_blocks", "spmm_rows_per_warp", "gemm_blocks")
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.grest_group_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -232,3 +232,24 @@ def test_gram_bindings_reject_bad_tensors_before_the_library():
     with pytest.raises(grest.GrestError) as e:
         grest.check_gram_args(X.float(), Y.float(), C, "float32", "grest_gram_f32")
     assert e.value.code == 1
+
+
+def test_group_create_rejects_bad_arguments_without_gpu(lib):
+    """grest_group_create checks its arguments on the host before any device
+    call: no graphs, null arrays, a capacity factor below 1, a buffer that is
+    not a checkpoint."""
+    import numpy as np
+    from paper_2603_19439_gb300 import grest
+    L = grest.load_library()
+    h = ctypes.c_void_p()
+    junk = np.zeros(256, np.uint8)
+    ptrs = (ctypes.c_void_p * 1)(junk.ctypes.data)
+    sizes = (ctypes.c_int64 * 1)(junk.size)
+    assert L.grest_group_create(0, ptrs, sizes, 1.25, ctypes.byref(h)) == 1
+    assert L.grest_group_create(1, None, sizes, 1.25, ctypes.byref(h)) == 1
+    assert L.grest_group_create(1, ptrs, sizes, 0.5, ctypes.byref(h)) == 1
+    assert L.grest_group_create(1, ptrs, sizes, 1.25, ctypes.byref(h)) == 1  # not a checkpoint
+    assert h.value is None
+    assert L.grest_group_apply_updates(None, None, None, None) == 1
+    assert L.grest_group_info(None, None, None, None, None, None, None) == 1
+    L.grest_group_destroy(None)
