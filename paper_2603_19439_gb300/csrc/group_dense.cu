@@ -20,20 +20,25 @@ namespace grp {
 namespace {
 
 // ------------------------------------------------------------------ SpMM
-template <int SEL, int NCH>
+// LPR lanes per row (32, 16 or 8: narrow blocks put several rows in a warp,
+// since an FP64 warp instruction costs the same for any active lanes); the
+// autotuned rows-per-warp factor only changes which warp takes which rows
+template <int SEL, int NCH, int LPR>
 __global__ void __launch_bounds__(256) k_g_spmm(GPools P) {
   const int g = blockIdx.y;
   const SpmmOp op = spmm_op(SEL, P, g);
   if (!op.on) return;
   const GState& st = P.st[g];
   const GMeta& mt = P.meta[g];
-  const int lane = threadIdx.x & 31;
+  const int lane = (threadIdx.x & 31) % LPR, sub = (threadIdx.x & 31) / LPR;
+  constexpr int SUBS = 32 / LPR;
   const int rpw = P.spmm_rows_per_warp;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int32_t* colb = P.col + mt.edge_off;
   const bool nl = P.op == GREST_OP_NLAP;
-  for (int64_t r00 = op.r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * rpw; r00 < op.r1;
-       r00 += warps * rpw) {
+  const int64_t step = warps * SUBS * rpw;
+  for (int64_t r00 = op.r0 + (((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * SUBS + sub) * rpw;
+       r00 < op.r1; r00 += step) {
     for (int64_t r = r00; r < r00 + rpw && r < op.r1; ++r) {
       const int64_t gr = mt.node_off + r;
       const int32_t* c = colb + P.row_off[gr];
@@ -48,7 +53,7 @@ __global__ void __launch_bounds__(256) k_g_spmm(GPools P) {
         const double* xr = op.X + (int64_t)(nb - op.col_lo) * op.ldx;
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
-          const int cc = ch * 32 + lane;
+          const int cc = ch * LPR + lane;
           if (cc < op.w) acc[ch] = nl ? fma(a, xr[cc], acc[ch]) : acc[ch] + xr[cc];
         }
       }
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(256) k_g_spmm(GPools P) {
       double* y = op.Y + (r - op.r0) * op.ldy;
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
-        const int cc = ch * 32 + lane;
+        const int cc = ch * LPR + lane;
         if (cc < op.w) {
           double v = scale * acc[ch];
           if (diag) v += dcoef * xd[cc];
@@ -72,34 +77,74 @@ __global__ void __launch_bounds__(256) k_g_spmm(GPools P) {
 }
 
 // ------------------------------------------------------------------ Gram
+// An FP64 warp instruction costs its sub-partition the same whatever its
+// active lanes, so the 4 x 4 output tiles are packed densely onto threads
+// (only tiles bi <= bj for a symmetric product: X^T X, and H = Z^T M Z with
+// M symmetric), and narrow products spread the slab's rows over R thread
+// groups whose sums are added in a fixed order at the end.
+__device__ __forceinline__ bool gram_sym(int sel, const GramOp& op) {
+  return sel == GR_H || (op.X == op.Y && op.a == op.b && op.ldx == op.ldy);
+}
+
+struct GramTiling {
+  int nbi, nbj, ntask, R;
+};
+__device__ __forceinline__ GramTiling gram_tiling(const GramOp& op, bool sym) {
+  GramTiling t;
+  t.nbi = (op.a + 3) / 4;
+  t.nbj = (op.b + 3) / 4;
+  t.ntask = sym ? t.nbi * (t.nbi + 1) / 2 : t.nbi * t.nbj;
+  t.R = 256 / t.ntask;
+  if (t.R > kGramRows) t.R = kGramRows;
+  if (t.R < 1) t.R = 1;
+  return t;
+}
+
 template <int SEL>
 __global__ void __launch_bounds__(256) k_g_gram(GPools P) {
   const int g = blockIdx.y, p = blockIdx.x;
   const GramOp op = gram_op(SEL, P, g);
   if (!op.on) return;
-  __shared__ double Xs[kGramRows][kMaxW + 1];
-  __shared__ double Ys[kGramRows][kMaxW + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __shared__ double stg[2 * kGramRows * (kMaxW + 1)];  // X and Y slabs, then the row groups' sums
+  double (*Xs)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(stg);
+  double (*Ys)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(stg + kGramRows * (kMaxW + 1));
+  const bool sym = gram_sym(SEL, op);
+  const GramTiling tl = gram_tiling(op, sym);
+  const int t = threadIdx.x, task = t % tl.ntask, rg = t / tl.ntask;
+  const bool active = rg < tl.R;
+  int bi = 0, bj = 0;
+  if (sym) {
+    int x = task;
+    while (x >= tl.nbi - bi) { x -= tl.nbi - bi; ++bi; }
+    bj = bi + x;
+  } else {
+    bi = task / tl.nbj;
+    bj = task % tl.nbj;
+  }
+  const int aw = tl.nbi * 4, bw = tl.nbj * 4;  // staged widths, zero beyond a and b
   int64_t rpc = (op.n + kPch - 1) / kPch;
   rpc = (rpc + kGramRows - 1) / kGramRows * kGramRows;
   const int64_t rb = p * rpc, re = rb + rpc < op.n ? rb + rpc : op.n;
   double acc[4][4] = {};
   for (int64_t r0 = rb; r0 < re; r0 += kGramRows) {
-    for (int e = threadIdx.x; e < kGramRows * kMaxW; e += blockDim.x) {
-      const int rr = e / kMaxW, cc = e % kMaxW;
+    for (int e = threadIdx.x; e < kGramRows * aw; e += blockDim.x) {
+      const int rr = e / aw, cc = e % aw;
       const int64_t r = r0 + rr;
       Xs[rr][cc] = (r < re && cc < op.a) ? op.X[r * op.ldx + cc] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kGramRows * bw; e += blockDim.x) {
+      const int rr = e / bw, cc = e % bw;
+      const int64_t r = r0 + rr;
       Ys[rr][cc] = (r < re && cc < op.b) ? op.Y[r * op.ldy + cc] : 0.0;
     }
     __syncthreads();
-    if (ty * 4 < op.a && tx * 4 < op.b) {
-#pragma unroll 4
-      for (int k = 0; k < kGramRows; ++k) {
+    if (active) {
+      for (int k = rg; k < kGramRows; k += tl.R) {
         double xa[4], yb[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          xa[u] = Xs[k][ty * 4 + u];
-          yb[u] = Ys[k][tx * 4 + u];
+          xa[u] = Xs[k][bi * 4 + u];
+          yb[u] = Ys[k][bj * 4 + u];
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -109,14 +154,26 @@ __global__ void __launch_bounds__(256) k_g_gram(GPools P) {
     }
     __syncthreads();
   }
-  double* part = P.part + ((int64_t)g * kPch + p) * kMaxW * kMaxW;
+  // the row groups' sums, added in group order
+  double* red = stg;  // R * ntask <= 256 tiles of 16 values fit the staging array
+  if (active)
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = ty * 4 + u, j = tx * 4 + v;
-      if (i < op.a && j < op.b) part[i * kMaxW + j] = acc[u][v];
-    }
+      for (int v = 0; v < 4; ++v) red[(rg * tl.ntask + task) * 16 + u * 4 + v] = acc[u][v];
+  __syncthreads();
+  if (t < tl.ntask) {
+    double* part = P.part + ((int64_t)g * kPch + p) * kMaxW * kMaxW;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double sum = 0.0;
+        for (int q = 0; q < tl.R; ++q) sum += red[(q * tl.ntask + t) * 16 + u * 4 + v];
+        const int i = bi * 4 + u, j = bj * 4 + v;
+        if (i < op.a && j < op.b) part[i * kMaxW + j] = sum;
+      }
+  }
 }
 
 template <int SEL>
@@ -124,17 +181,21 @@ __global__ void __launch_bounds__(256) k_g_gram_reduce(GPools P) {
   const int g = blockIdx.x;
   const GramOp op = gram_op(SEL, P, g);
   if (!op.on) return;
+  const bool sym = gram_sym(SEL, op);
   const double* part = P.part + (int64_t)g * kPch * kMaxW * kMaxW;
   for (int e = threadIdx.x; e < op.a * op.b; e += blockDim.x) {
     const int i = e / op.b, j = e % op.b;
+    const int src = (!sym || i / 4 <= j / 4) ? i * kMaxW + j : j * kMaxW + i;  // lower tiles mirrored
     double s = 0.0;
 #pragma unroll
-    for (int p = 0; p < kPch; ++p) s += part[(int64_t)p * kMaxW * kMaxW + i * kMaxW + j];
+    for (int p = 0; p < kPch; ++p) s += part[(int64_t)p * kMaxW * kMaxW + src];
     op.C[i * op.ldc + j] = s;
   }
 }
 
 // ------------------------------------------------------------------ GEMM
+// one output element per thread ((row, column) pairs laid out linearly, so
+// narrow outputs keep every lane busy); B in shared memory
 template <int SEL>
 __global__ void __launch_bounds__(256) k_g_gemm(GPools P) {
   const int g = blockIdx.y;
@@ -143,21 +204,16 @@ __global__ void __launch_bounds__(256) k_g_gemm(GPools P) {
   __shared__ double Bs[kMaxW][kMaxW + 1];
   for (int e = threadIdx.x; e < op.a * op.c; e += blockDim.x) Bs[e / op.c][e % op.c] = op.B[(e / op.c) * op.ldb + e % op.c];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < op.n; r += warps) {
+  const int64_t total = op.n * op.c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / op.c;
+    const int j = (int)(e % op.c);
     const double* x = op.X + r * op.ldx;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = lane + 32 * h;
-      if (j < op.c) {
-        double s = 0.0;
-        for (int k = 0; k < op.a; ++k) s = fma(x[k], Bs[k][j], s);
-        double v = op.alpha * s;
-        if (op.beta != 0.0) v += op.beta * op.Cin[r * op.ldc + j];
-        op.Out[r * op.ldo + j] = v;
-      }
-    }
+    double s = 0.0;
+    for (int k = 0; k < op.a; ++k) s = fma(x[k], Bs[k][j], s);
+    double v = op.alpha * s;
+    if (op.beta != 0.0) v += op.beta * op.Cin[r * op.ldc + j];
+    op.Out[r * op.ldo + j] = v;
   }
 }
 
@@ -478,11 +534,16 @@ int gemm_one(const GPools& P, const LaunchShape& ls, cudaStream_t s) {
 
 template <int SEL>
 int spmm_one(const GPools& P, const LaunchShape& ls, cudaStream_t s) {
-  const int w = SEL == SP_Y1 ? P.K : (SEL == SP_OM ? P.q : P.cmax);
-  if (w <= 32)
-    k_g_spmm<SEL, 1><<<dim3(ls.row_blocks, P.G), 256, 0, s>>>(P);
+  const int w = SEL == SP_Y1 ? P.K : (SEL == SP_OM ? P.q : P.cmax);  // the widest the stage can be
+  const dim3 grid(ls.row_blocks, P.G);
+  if (w <= 8)
+    k_g_spmm<SEL, 1, 8><<<grid, 256, 0, s>>>(P);
+  else if (w <= 16)
+    k_g_spmm<SEL, 1, 16><<<grid, 256, 0, s>>>(P);
+  else if (w <= 32)
+    k_g_spmm<SEL, 1, 32><<<grid, 256, 0, s>>>(P);
   else
-    k_g_spmm<SEL, 2><<<dim3(ls.row_blocks, P.G), 256, 0, s>>>(P);
+    k_g_spmm<SEL, 2, 32><<<grid, 256, 0, s>>>(P);
   return 1;
 }
 
