@@ -98,6 +98,20 @@ struct OpParams {
   const uint8_t* live;
 };
 
+// ------------------------------------------------------------ small problems in one CTA (group_dense.cu)
+// Pivoted Cholesky of G (c x c, upper triangle read, c <= 64) with the drop
+// rule of pchol_inverse (reference |abs_ref_ptr[0]| when given, else
+// abs_ref); T (c x c, ldt) = P R^-1 on the kept pivots, zero elsewhere;
+// info[0..3] = rank, kept_min, dropped_max, 0.  Returns the number of
+// kernels launched, -1 when the size is not taken.
+int pchol_small_f64(const double* G, int ldg, int c, double tol, double abs_ref, const double* abs_ref_ptr, double* T,
+                    int ldt, double* info, cudaStream_t s);
+// Leading k eigenpairs (tracking order of op) of the symmetric m x m A
+// (m <= 64) by cyclic Jacobi: theta (k), F (m x k, ldf), ritz (m, nullable),
+// info[0] = the relative K / K+1 gap (nullable).  Returns launches, or -1.
+int eig_small_f64(const double* A, int lda, int m, int k, int op, double* theta, double* F, int ldf, double* ritz,
+                  double* info, cudaStream_t s);
+
 // ------------------------------------------------------------ checkpoints
 // A checkpoint written by grest_checkpoint, read in place (host pointers into
 // the buffer): the compact CSR, the maintained degrees, the pairs and the

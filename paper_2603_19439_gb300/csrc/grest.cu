@@ -535,7 +535,10 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, 
 void eig(grest_ctx* c, double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf,
          double* ritz, double* info, bool f32) {
   int p = prof_begin(c);
-  c->launches += sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, f32, c->stream);
+  // FP64 problems of at most 64 columns: cyclic Jacobi in one CTA (group_dense.cu)
+  int nl = f32 ? -1 : eig_small_f64(H, (int)ld, m, k, op, theta, F, (int)ldf, ritz, info, c->stream);
+  if (nl < 0) nl = sym_eig_select(H, ld, m, k, op, theta, F, ldf, ritz, info, c->eigwork, f32, c->stream);
+  c->launches += nl;
   prof_end(c, p, 3, 4.0 * m * m * m / 3.0 + 2.0 * m * m * k);
 }
 
@@ -579,8 +582,14 @@ grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n
                          int* rank_out) {
   gram(c, X, ldx, w, X, ldx, w, n, c->G, w, true);
   int p = prof_begin(c);
-  c->launches += pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot,
-                               small_f32<T>(c), c->stream);
+  // FP64 problems of at most 64 columns: one CTA (group_dense.cu); else the cluster kernels
+  int nl = small_f32<T>(c) ? -1
+                           : pchol_small_f64(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->info + info_slot,
+                                             c->stream);
+  if (nl < 0)
+    nl = pchol_inverse(c->G, w, w, tol, abs_ref, abs_ref_ptr, c->T, w, c->piv, c->info + info_slot, small_f32<T>(c),
+                       c->stream);
+  c->launches += nl;
   prof_end(c, p, 3, (double)w * w * w / 3.0 + (double)w * w * w / 3.0);
   int rank = w;
   if (read_rank) {
@@ -732,12 +741,22 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   c->launches += gram_df(c->U32, c->ldu, MUh, MUl, c->ldu, K, N2, c->H, K, c->part, c->part_cap, s);
   prof_end(c, p, 1, 2.0 * N2 * K * K, 12.0 * N2 * K);
   p = prof_begin(c);
-  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
+  {  // the K x K problems of the refinement fit one CTA (K <= 64)
+    int nl = pchol_small_f64(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
+    if (nl < 0) nl = pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
+    c->launches += nl;
+  }
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
   symmetrize(c->Uh, K, K, s);
   c->launches += 2;
   prof_end(c, p, 3, 4.0 * K * K * K);
-  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
+  {
+    p = prof_begin(c);
+    const int ne = eig_small_f64(c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, s);
+    prof_end(c, p, 3, 4.0 * K * K * K);
+    if (ne < 0) eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
+    else c->launches += ne;
+  }
   k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
   c->launches += 1;
   p = prof_begin(c);
@@ -772,12 +791,22 @@ grest_status refine_mixed_f64(grest_ctx* c, int64_t N2) {
   c->launches += nl;
   prof_end(c, p, 1, 2.0 * N2 * K * (K + 1), 16.0 * N2 * K);
   p = prof_begin(c);
-  c->launches += pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
+  {  // the K x K problems of the refinement fit one CTA (K <= 64)
+    int nl = pchol_small_f64(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
+    if (nl < 0) nl = pchol_inverse(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->piv, c->info + 44, false, s);
+    c->launches += nl;
+  }
   k_small_tht<<<1, 256, 0, s>>>(c->T, c->H, K, c->Gs, c->Uh);
   symmetrize(c->Uh, K, K, s);
   c->launches += 2;
   prof_end(c, p, 3, 4.0 * K * K * K);
-  eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
+  {
+    p = prof_begin(c);
+    const int ne = eig_small_f64(c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, s);
+    prof_end(c, p, 3, 4.0 * K * K * K);
+    if (ne < 0) eig(c, c->Uh, K, K, K, c->cfg.op, c->th_new, c->F, K, c->tmpk, c->info + 48, false);
+    else c->launches += ne;
+  }
   k_small_mm<<<1, 256, 0, s>>>(c->T, c->F, K, c->Gs);
   c->launches += 1;
   gemm(c, N2, K, K, 1.0, X64, ldu, c->Gs, K, 0.0, static_cast<const double*>(nullptr), 0, c->U, ldu);

@@ -237,32 +237,31 @@ __device__ inline PcholOp pchol_op(int sel, const GPools& P, int g) {
   return o;
 }
 
-template <int SEL>
-__global__ void __launch_bounds__(256) k_g_pchol(GPools P) {
-  const int g = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  GState& st = P.st[g];
-  const PcholOp op = pchol_op(SEL, P, g);
-  extern __shared__ __align__(16) double pc_sm[];
-  double (*A)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(pc_sm);
-  double (*Rs)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(pc_sm + kMaxW * (kMaxW + 1));  // row k of R, original indices
+// Pivoted Cholesky of G (c x c, upper triangle read) in one CTA, smem =
+// 2 kMaxW (kMaxW + 1) doubles.  Pivot k is the largest remaining diagonal
+// (lowest index on ties); the factorization stops at the first pivot with
+// R_kk^2 <= tol^2 max(R_00^2, abs_ref^2).  T (c x c, ldt) = P R^-1 on the kept
+// pivots, zero elsewhere.  Returns the rank; *ref, *vlast, *vdrop: the
+// reference and the last kept and first dropped squared pivots.
+struct PcholResult {
+  int rank;
+  double ref, vlast, vdrop;
+};
+
+__device__ PcholResult pchol_block(const double* G, int ldg, int c, double tol, double abs_ref, double* T, int ldt,
+                                   double* smem) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  double (*A)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(smem);
+  double (*Rs)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(smem + kMaxW * (kMaxW + 1));  // row k of R, original indices
   __shared__ int done[kMaxW], piv[kMaxW];
   __shared__ double s_ref, s_thr, s_vlast, s_vdrop;
   __shared__ int s_p, s_stop, s_rank;
-  if (!op.on) {
-    // no columns: the widths that follow from an empty basis
-    if (tid == 0 && st.status == 0) {
-      if (SEL == PC_V1) { st.r = 0; st.r2 = 0; st.m = st.Ku; if (st.m < P.K) st.status = GREST_ERR_NUMERIC; }
-      if (SEL == PC_Y2 && st.mode == 4) st.rY2 = 0;
-    }
-    return;
-  }
-  const int c = op.c;
   for (int e = tid; e < c * c; e += nth) {
     const int i = e / c, l = e % c;
-    A[i][l] = i <= l ? op.G[i * op.ldg + l] : op.G[l * op.ldg + i];
+    A[i][l] = i <= l ? G[i * ldg + l] : G[l * ldg + i];
   }
   for (int l = tid; l < c; l += nth) done[l] = 0;
-  if (tid == 0) { s_rank = c; s_vlast = 0.0; s_vdrop = 0.0; }
+  if (tid == 0) { s_rank = c; s_vlast = 0.0; s_vdrop = 0.0; s_ref = 0.0; }
   __syncthreads();
   for (int k = 0; k < c; ++k) {
     if (tid < 32) {
@@ -278,8 +277,8 @@ __global__ void __launch_bounds__(256) k_g_pchol(GPools P) {
       }
       if (tid == 0) {
         if (k == 0) {
-          s_ref = fmax(bv, op.abs_ref * op.abs_ref);
-          s_thr = op.tol * op.tol * s_ref;
+          s_ref = fmax(bv, abs_ref * abs_ref);
+          s_thr = tol * tol * s_ref;
         }
         if (bi >= c || !(bv > 0.0) || !(bv > s_thr) || !isfinite(bv)) {
           s_stop = 1;
@@ -310,30 +309,61 @@ __global__ void __launch_bounds__(256) k_g_pchol(GPools P) {
   // T = P R^-1: column j by back substitution, x_t for t = j .. 0, kept in A[t][j]
   for (int j = tid; j < rk; j += nth) {
     for (int t = j; t >= 0; --t) {
-      double s = t == j ? 1.0 : 0.0;
-      for (int u = t + 1; u <= j; ++u) s = fma(-Rs[t][piv[u]], A[u][j], s);
-      A[t][j] = s / Rs[t][piv[t]];
+      double sum = t == j ? 1.0 : 0.0;
+      for (int u = t + 1; u <= j; ++u) sum = fma(-Rs[t][piv[u]], A[u][j], sum);
+      A[t][j] = sum / Rs[t][piv[t]];
     }
   }
   __syncthreads();
-  for (int e = tid; e < c * rk; e += nth) {
-    const int i = e / rk, j = e % rk;
-    op.T[i * op.ldt + j] = 0.0;
-  }
+  for (int e = tid; e < c * c; e += nth) T[(e / c) * ldt + (e % c)] = 0.0;
   __syncthreads();
   for (int e = tid; e < rk * rk; e += nth) {
     const int t = e / rk, j = e % rk;
-    if (t <= j) op.T[piv[t] * op.ldt + j] = A[t][j];
+    if (t <= j) T[piv[t] * ldt + j] = A[t][j];
   }
+  __syncthreads();
+  return PcholResult{rk, s_ref, s_vlast, s_vdrop};
+}
+
+template <int SEL>
+__global__ void __launch_bounds__(256) k_g_pchol(GPools P) {
+  const int g = blockIdx.x, tid = threadIdx.x;
+  GState& st = P.st[g];
+  const PcholOp op = pchol_op(SEL, P, g);
+  extern __shared__ __align__(16) double pc_sm[];
+  if (!op.on) {
+    // no columns: the widths that follow from an empty basis
+    if (tid == 0 && st.status == 0) {
+      if (SEL == PC_V1) { st.r = 0; st.r2 = 0; st.m = st.Ku; if (st.m < P.K) st.status = GREST_ERR_NUMERIC; }
+      if (SEL == PC_Y2 && st.mode == 4) st.rY2 = 0;
+    }
+    return;
+  }
+  const PcholResult res = pchol_block(op.G, op.ldg, op.c, op.tol, op.abs_ref, op.T, op.ldt, pc_sm);
+  const int rk = res.rank;
   if (tid == 0) {
     *op.rank_out = rk;
     if (op.stats) {
-      st.kept_min = (rk > 0 && s_ref > 0.0) ? sqrt(s_vlast / s_ref) : 0.0;
-      st.dropped_max = (s_ref > 0.0 && s_vdrop > 0.0) ? sqrt(s_vdrop / s_ref) : 0.0;
+      st.kept_min = (rk > 0 && res.ref > 0.0) ? sqrt(res.vlast / res.ref) : 0.0;
+      st.dropped_max = (res.ref > 0.0 && res.vdrop > 0.0) ? sqrt(res.vdrop / res.ref) : 0.0;
     }
     if (SEL == PC_V1 && rk == 0) { st.r2 = 0; st.m = st.Ku; }
     if (SEL == PC_V2) st.m = st.Ku + rk;
     if ((SEL == PC_V1 || SEL == PC_V2) && st.m < P.K && (SEL == PC_V2 || rk == 0)) st.status = GREST_ERR_NUMERIC;
+  }
+}
+
+// one problem: info[0] = rank, info[1] = kept_min, info[2] = dropped_max, info[3] = 0
+__global__ void __launch_bounds__(256) k_pchol_small(const double* G, int ldg, int c, double tol, double abs_ref,
+                                                     const double* abs_ref_ptr, double* T, int ldt, double* info) {
+  extern __shared__ __align__(16) double pc_sm[];
+  const double ref = abs_ref_ptr ? fabs(abs_ref_ptr[0]) : abs_ref;
+  const PcholResult res = pchol_block(G, ldg, c, tol, ref, T, ldt, pc_sm);
+  if (threadIdx.x == 0 && info) {
+    info[0] = res.rank;
+    info[1] = (res.rank > 0 && res.ref > 0.0) ? sqrt(res.vlast / res.ref) : 0.0;
+    info[2] = (res.ref > 0.0 && res.vdrop > 0.0) ? sqrt(res.vdrop / res.ref) : 0.0;
+    info[3] = 0.0;
   }
 }
 
@@ -358,13 +388,12 @@ __device__ inline EigOp eig_op(int sel, const GPools& P, int g) {
 
 constexpr int kJacobiSweeps = 40;
 
-template <int SEL>
-__global__ void __launch_bounds__(256) k_g_eig(GPools P) {
-  const int g = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  GState& st = P.st[g];
-  const EigOp op = eig_op(SEL, P, g);
-  if (!op.on) return;
-  extern __shared__ __align__(16) double eig_sm[];
+// Leading op.k eigenpairs of the symmetric op.m x op.m matrix (symmetrized
+// on load) by cyclic Jacobi in one CTA, smem = 2 kMaxW (kMaxW + 1) doubles:
+// theta (k), F (m x k) and all m values in tracking order (ritz, nullable).
+// Returns the relative gap between tracked values k-1 and k (0 when m <= k).
+__device__ double jacobi_block(const EigOp& op, double* eig_sm) {
+  const int tid = threadIdx.x, nth = blockDim.x;
   double (*A)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(eig_sm);
   double (*V)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(eig_sm + kMaxW * (kMaxW + 1));
   __shared__ double cs[kMaxW / 2], sn[kMaxW / 2];
@@ -495,28 +524,47 @@ __global__ void __launch_bounds__(256) k_g_eig(GPools P) {
     if (t < op.k) op.F[l * op.ldf + t] = V[l][i];
   }
   __syncthreads();
-  if (tid == 0) {
+  double gap = 0.0;
+  if (op.gap && m > op.k) {
+    int ia = 0, ib = 0;
+    for (int i = 0; i < m; ++i) {
+      if (trk[i] == op.k - 1) ia = i;
+      if (trk[i] == op.k) ib = i;
+    }
+    double top = 0.0;
+    for (int i = 0; i < m; ++i)
+      if (trk[i] == 0) top = fabs(d[i]);
+    const double x = op.op == GREST_OP_ADJ ? fabs(d[ia]) : d[ia], y = op.op == GREST_OP_ADJ ? fabs(d[ib]) : d[ib];
+    gap = fabs(x - y) / fmax(top, 1e-300);
+  }
+  __syncthreads();
+  return gap;
+}
+
+template <int SEL>
+__global__ void __launch_bounds__(256) k_g_eig(GPools P) {
+  const int g = blockIdx.x;
+  GState& st = P.st[g];
+  const EigOp op = eig_op(SEL, P, g);
+  if (!op.on) return;
+  extern __shared__ __align__(16) double eig_sm[];
+  const double gap = jacobi_block(op, eig_sm);
+  if (threadIdx.x == 0) {
     if (SEL == EG_GS) {
       st.Lp = op.k;
       st.cb = op.k;
       st.cw = st.Ku + op.k;
-    } else if (op.gap) {
-      double gap = 0.0;
-      if (m > op.k) {
-        int ia = 0, ib = 0;
-        for (int i = 0; i < m; ++i) {
-          if (trk[i] == op.k - 1) ia = i;
-          if (trk[i] == op.k) ib = i;
-        }
-        double top = 0.0;
-        for (int i = 0; i < m; ++i)
-          if (trk[i] == 0) top = fabs(d[i]);
-        const double x = op.op == GREST_OP_ADJ ? fabs(d[ia]) : d[ia], y = op.op == GREST_OP_ADJ ? fabs(d[ib]) : d[ib];
-        gap = fabs(x - y) / fmax(top, 1e-300);
-      }
+    } else {
       st.boundary_gap = gap;
     }
   }
+}
+
+// one problem (plain pointers): info[0] = the gap, when info is given
+__global__ void __launch_bounds__(256) k_eig_small(EigOp op, double* info) {
+  extern __shared__ __align__(16) double eig_sm[];
+  const double gap = jacobi_block(op, eig_sm);
+  if (threadIdx.x == 0 && info) info[0] = gap;
 }
 
 template <int SEL>
@@ -556,6 +604,36 @@ bool prepare_kernels() {
          reserve_dynamic_smem(k_g_pchol<PC_Y1>, kEigSmem) && reserve_dynamic_smem(k_g_pchol<PC_Y2>, kEigSmem) &&
          reserve_dynamic_smem(k_g_pchol<PC_V1>, kEigSmem) && reserve_dynamic_smem(k_g_pchol<PC_V2>, kEigSmem);
 }
+
+}  // namespace grp
+
+int pchol_small_f64(const double* G, int ldg, int c, double tol, double abs_ref, const double* abs_ref_ptr, double* T,
+                    int ldt, double* info, cudaStream_t s) {
+  if (c < 1 || c > grp::kMaxW || !reserve_dynamic_smem(grp::k_pchol_small, grp::kEigSmem)) return -1;
+  grp::k_pchol_small<<<1, 256, grp::kEigSmem, s>>>(G, ldg, c, tol, abs_ref, abs_ref_ptr, T, ldt, info);
+  return 1;
+}
+
+int eig_small_f64(const double* A, int lda, int m, int k, int op, double* theta, double* F, int ldf, double* ritz,
+                  double* info, cudaStream_t s) {
+  if (m < 1 || m > grp::kMaxW || k < 1 || k > m || !reserve_dynamic_smem(grp::k_eig_small, grp::kEigSmem)) return -1;
+  grp::EigOp o{};
+  o.A = A;
+  o.lda = lda;
+  o.m = m;
+  o.k = k;
+  o.op = op;
+  o.F = F;
+  o.ldf = ldf;
+  o.theta = theta;
+  o.ritz = ritz;
+  o.gap = info != nullptr;
+  o.on = true;
+  grp::k_eig_small<<<1, 256, grp::kEigSmem, s>>>(o, info);
+  return 1;
+}
+
+namespace grp {
 
 int launch_spmm(int sel, const GPools& P, const LaunchShape& ls, cudaStream_t s) {
   switch (sel) {
