@@ -414,6 +414,20 @@ grest_status grest_gemm_f32(grest_ctx *ctx, int64_t n, int32_t a, int32_t c, dou
 grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const double *Y, int64_t ldy, int32_t b,
                                 int64_t n, double *C, int64_t ldc, void *cuda_stream);
 
+/*
+ * grest_check_bounded_wait -- a check of the library's failure detection
+ * (the paper has no counterpart).  Every wait of the library's kernels on a
+ * device-side barrier is bounded: after about a second without progress the
+ * kernel records a timeout, waits (bounded) for its own copies, releases its
+ * tensor memory and returns, and the call reports GREST_ERR_TIMEOUT with the
+ * device still usable.  This entry point runs that path on purpose: one
+ * thread waits on a barrier that nothing arrives on.  It returns
+ * GREST_ERR_TIMEOUT (the expected result) after about a second, or
+ * GREST_ERR_OOM / GREST_ERR_CUDA.  Work on cuda_stream (NULL = legacy
+ * default stream); synchronous.
+ */
+grest_status grest_check_bounded_wait(void *cuda_stream);
+
 /* Release every device buffer of the context. NULL is ignored. */
 void grest_destroy(grest_ctx *ctx);
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgrest.so")
-SOURCES = ["scan.cu", "graph.cu", "spmm.cu", "dense.cu", "eig.cu", "rsvd.cu", "grest.cu", "noalloc.cu", "tc_gram.cu", "small.cu", "tc_gemm.cu", "refine.cu", "small32.cu", "central.cu", "serve.cu", "narrow_gram.cu", "group.cu", "group_update.cu", "group_dense.cu"]
+SOURCES = ["scan.cu", "graph.cu", "spmm.cu", "dense.cu", "eig.cu", "rsvd.cu", "grest.cu", "noalloc.cu", "tc_gram.cu", "small.cu", "tc_gemm.cu", "refine.cu", "small32.cu", "central.cu", "serve.cu", "narrow_gram.cu", "group.cu", "group_update.cu", "group_dense.cu", "waitcheck.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE]
 
