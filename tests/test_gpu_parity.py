@@ -259,6 +259,20 @@ def test_gram_f32_tensor_core_entry_point(cuda):
         bound = np.abs(Xh).T @ np.abs(Yh)
         err = np.abs(C.cpu().numpy() - ref)
         assert np.all(err <= 2e-6 * bound + 1e-30), (n, a, b, float((err / np.maximum(bound, 1e-30)).max()))
+    # X = Y (the CholQR Grams): only the upper tiles are computed and mirrored.
+    # The diagonal sums have terms of one sign, so the FP32 accumulation over a
+    # 256-row span reaches its worst-case bound 256 * 2^-24 ~ 1.5e-5 of the sum
+    # of magnitudes (independent random signs above stay within 2e-6)
+    for n, a in ((100_003, 200), (70_001, 100), (4097, 256), (33, 40)):
+        X = torch.tensor(rng.standard_normal((n, a)), dtype=torch.float32, device="cuda")
+        C = torch.empty((a, a), dtype=torch.float64, device="cuda")
+        tr.gram_f32(X, X, C)
+        Xh = X.double().cpu().numpy()
+        err = np.abs(C.cpu().numpy() - Xh.T @ Xh)
+        bound = np.abs(Xh).T @ np.abs(Xh)
+        assert np.all(err <= (256 * 2.0 ** -24 + 2e-7) * bound + 1e-30), (n, a)
+        off = ~np.eye(a, dtype=bool)
+        assert np.all(err[off] <= 2e-6 * bound[off] + 1e-30), (n, a)
     # misaligned base pointer (column offset 1): CUDA-core fallback, same rule
     Z = torch.tensor(rng.standard_normal((5000, 40)), dtype=torch.float32, device="cuda")
     X, Y = Z[:, 1:33], Z[:, 3:40]
