@@ -761,16 +761,19 @@ namespace {
 // whatever its active lanes.
 constexpr int kPairRows = 32;
 
-__global__ void __launch_bounds__(288) k_gram_pair_upper(const double* __restrict__ X, const double* __restrict__ Y,
-                                                         int64_t ld, int k, int64_t n, int64_t rows_per_chunk,
+__global__ void __launch_bounds__(512) k_gram_pair_upper(const double* __restrict__ X, const double* __restrict__ Y,
+                                                         int64_t ld, int k, int64_t n, int64_t rows_per_chunk, int R,
                                                          double* __restrict__ part) {
-  __shared__ double Xs[kPairRows][64 + 1];
-  __shared__ double Ys[kPairRows][64 + 1];
-  const int nb = (k + 3) / 4, npairs = nb * (nb + 1) / 2;
-  const int t = threadIdx.x;
-  const bool active = t < 2 * npairs;
+  __shared__ double XYs[2][kPairRows][64 + 1];
+  double (*Xs)[64 + 1] = XYs[0];
+  double (*Ys)[64 + 1] = XYs[1];
+  const int nb = (k + 3) / 4, npairs = nb * (nb + 1) / 2, ntask = 2 * npairs;
+  // R row groups of ntask threads each (R chosen so that whole warps are
+  // busy); row group g takes the rows g, g + R, ... of every slab
+  const int t = threadIdx.x % ntask, rg = threadIdx.x / ntask;
+  const bool active = rg < R;
   const int which = t < npairs ? 0 : 1;  // 0: X^T X, 1: X^T Y
-  int pi = active ? t - which * npairs : 0, bi = 0;
+  int pi = t - which * npairs, bi = 0;
   while (pi >= nb - bi) { pi -= nb - bi; ++bi; }
   const int bj = bi + pi;
   const int64_t chunk = blockIdx.x;
@@ -778,13 +781,13 @@ __global__ void __launch_bounds__(288) k_gram_pair_upper(const double* __restric
   const int64_t rend = rbeg + rows_per_chunk < n ? rbeg + rows_per_chunk : n;
   double acc[4][4] = {};
   for (int64_t r0 = rbeg; r0 < rend; r0 += kPairRows) {
-    for (int e = t; e < kPairRows * k; e += blockDim.x) {
+    for (int e = threadIdx.x; e < kPairRows * k; e += blockDim.x) {
       const int rr = e / k, cc = e % k;
       const int64_t r = r0 + rr;
       Xs[rr][cc] = r < rend ? X[r * ld + cc] : 0.0;
       Ys[rr][cc] = r < rend ? Y[r * ld + cc] : 0.0;
     }
-    for (int e = t; e < kPairRows * (nb * 4 - k); e += blockDim.x) {  // zero the padding columns
+    for (int e = threadIdx.x; e < kPairRows * (nb * 4 - k); e += blockDim.x) {  // zero the padding columns
       const int rr = e / (nb * 4 - k), cc = k + e % (nb * 4 - k);
       Xs[rr][cc] = 0.0;
       Ys[rr][cc] = 0.0;
@@ -792,8 +795,7 @@ __global__ void __launch_bounds__(288) k_gram_pair_upper(const double* __restric
     __syncthreads();
     if (active) {
       double (*B)[64 + 1] = which ? Ys : Xs;
-#pragma unroll 4
-      for (int kk = 0; kk < kPairRows; ++kk) {
+      for (int kk = rg; kk < kPairRows; kk += R) {
         double xa[4], yb[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -808,7 +810,22 @@ __global__ void __launch_bounds__(288) k_gram_pair_upper(const double* __restric
     }
     __syncthreads();
   }
-  if (!active) return;
+  // groups 1..R-1 stage their sums in the (now free) slab buffer and group 0
+  // adds them in group order, so the result does not depend on timing
+  double* stage = &XYs[0][0][0];
+  if (active && rg > 0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) stage[((rg - 1) * ntask + t) * 16 + u * 4 + v] = acc[u][v];
+  }
+  __syncthreads();
+  if (rg != 0) return;
+  for (int g = 1; g < R; ++g)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += stage[((g - 1) * ntask + t) * 16 + u * 4 + v];
   double* P = part + (chunk * 2 + which) * (int64_t)k * k;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -836,8 +853,17 @@ __global__ void k_gram_pair_reduce(const double* __restrict__ part, int64_t chun
 int gram_pair_sym_f64(const double* X, const double* Y, int64_t ld, int k, int64_t n, double* G, double* H,
                       double* part, int64_t part_cap, cudaStream_t s) {
   if (k < 1 || k > 64 || n < 1) return -1;
-  const int nb = (k + 3) / 4;
-  const int threads = (2 * nb * (nb + 1) / 2 + 31) / 32 * 32;
+  const int nb = (k + 3) / 4, ntask = nb * (nb + 1);
+  // row groups: the R (<= 8, R ntask <= 512, R - 1 staged groups fit in the
+  // slab buffer) that leaves the fewest idle lanes in the last warp
+  int R = 1;
+  double best = 2.0;
+  for (int r = 1; r <= 8 && r * ntask <= 512 && (r - 1) * ntask * 16 <= 2 * kPairRows * 65; ++r) {
+    const int th = (r * ntask + 31) / 32 * 32;
+    const double idle = (double)(th - r * ntask) / th;
+    if (idle < best - 1e-12) { best = idle; R = r; }
+  }
+  const int threads = (R * ntask + 31) / 32 * 32;
   int64_t chunks = 152 * 4;
   const int64_t slabs = cdiv(n, kPairRows);
   if (chunks > slabs) chunks = slabs;
@@ -845,7 +871,7 @@ int gram_pair_sym_f64(const double* X, const double* Y, int64_t ld, int k, int64
   if (chunks < 1) return -1;
   const int64_t rpc = cdiv(cdiv(n, chunks), kPairRows) * kPairRows;
   chunks = cdiv(n, rpc);
-  k_gram_pair_upper<<<(unsigned)chunks, threads, 0, s>>>(X, Y, ld, k, n, rpc, part);
+  k_gram_pair_upper<<<(unsigned)chunks, threads, 0, s>>>(X, Y, ld, k, n, rpc, R, part);
   k_gram_pair_reduce<<<(unsigned)cdiv(2 * (int64_t)k * k, 256), 256, 0, s>>>(part, chunks, k, G, H);
   return 2;
 }
