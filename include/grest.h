@@ -428,6 +428,23 @@ grest_status grest_gram_noalloc(const double *X, int64_t ldx, int32_t a, const d
  */
 grest_status grest_check_bounded_wait(void *cuda_stream);
 
+/*
+ * grest_check_fast_recip -- a check of the FP64 reciprocal that the small
+ * factorizations use in their serial scalar chains (pivots of the pivoted
+ * Cholesky, Householder coefficients, the tridiagonal LU of inverse
+ * iteration, Jacobi rotations; Alg. 1 and the CholQR of Alg. 2): the
+ * hardware's reduced-precision reciprocal refined by two Newton-Raphson
+ * steps, within a few units in the last place of 1 / x for normal x with
+ * normal 1 / x (other inputs take the IEEE division).  The paper has no
+ * counterpart; this is a test hook.
+ * x and out are device arrays of n doubles owned by the caller; out[i] =
+ * that reciprocal of x[i].  Work on cuda_stream (NULL = legacy default
+ * stream); synchronous.  Returns GREST_ERR_INVALID_ARG for n < 0 or a null
+ * array with n > 0, GREST_ERR_CUDA on a CUDA error (including one already
+ * pending on the calling thread).
+ */
+grest_status grest_check_fast_recip(const double *x, int64_t n, double *out, void *cuda_stream);
+
 /* Release every device buffer of the context. NULL is ignored. */
 void grest_destroy(grest_ctx *ctx);
 

@@ -31,6 +31,26 @@ enum DevErr : int32_t {
 
 __device__ __forceinline__ void set_err(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
 
+// 1 / a in FP64 for the serial scalar chains of the small factorizations
+// (pivots, reflector coefficients, tridiagonal LU, Jacobi rotations), where
+// an IEEE division costs several hundred clocks of latency on this part's
+// FP64 pipe: the hardware's reduced-precision reciprocal (rcp.approx.ftz.f64)
+// refined by two Newton-Raphson steps x <- x + x (1 - a x), each of which
+// squares the relative error, so the result is within a couple of units in
+// the last place of 1 / a.  Zero, subnormal, huge (|a| >= 2^1022, whose
+// reciprocal is subnormal), infinite and NaN inputs take the IEEE division
+// instead (an integer test of the exponent field).
+__device__ __forceinline__ double rcp_newton(double a) {
+  const int ex = (__double2hiint(a) >> 20) & 0x7ff;
+  if (ex < 2 || ex > 2044) return 1.0 / a;
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(a));
+  double e = fma(-a, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-a, x, 1.0);
+  return fma(x, e, x);
+}
+
 // Largest dynamic shared memory a launch of `kernel` may request on the
 // current device (opt-in limit minus the kernel's static shared memory), and
 // raise the kernel's limit to `bytes` when that fits.  Returns false (and

@@ -441,17 +441,26 @@ __device__ __forceinline__ double hash_unit(uint32_t a, uint32_t b) {
 
 // --- 4. eigenvectors of T by inverse iteration (tridiagonal LU with partial
 // pivoting, three solves from a fixed pseudo-random start), one thread per
-// selected pair and one warp per block: the chains are serial, so the warps
-// are spread over the SM sub-partitions.  The reciprocal of each U pivot is
+// selected pair and LANES pairs per block: the chains are serial, so the
+// blocks are spread over the SMs (an FP64 warp instruction costs the same
+// for 8 active lanes as for 32, so the FP64 path takes 8 pairs per block and
+// keeps their arrays in shared memory).  The reciprocal of each U pivot is
 // formed once in the LU and reused by the solves.
-template <typename T, bool SMEM>
+template <typename T>
+__device__ __forceinline__ T recip(T a) {
+  if constexpr (sizeof(T) == sizeof(double)) return rcp_newton(a);
+  else return T(1) / a;
+}
+
+template <typename T, bool SMEM, int LANES>
 __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mmax, double* F, int64_t ldf) {
   EigWork L = eig_layout(work, mmax);
   extern __shared__ __align__(16) unsigned char iv_raw[];
-  const int t = blockIdx.x * 32 + threadIdx.x;
-  if (t >= k) return;
+  const int t = blockIdx.x * LANES + threadIdx.x;
+  if (threadIdx.x >= LANES || t >= k) return;
   // per-thread arrays interleaved across threads (coalesced / conflict-free):
-  // element i at [i * stride], in shared memory (stride 32) or global scratch
+  // element i at [i * stride], in shared memory (stride LANES, planes of m)
+  // or global scratch (stride kMaxK, planes of mmax)
   struct Strided {
     T* b;
     int64_t st;
@@ -461,12 +470,12 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
   int64_t st;
   if (SMEM) {
     scr = reinterpret_cast<T*>(iv_raw) + threadIdx.x;
-    st = 32;
+    st = LANES;
   } else {
     scr = reinterpret_cast<T*>(L.scr) + t;
     st = kMaxK;
   }
-  const int64_t pl = (int64_t)mmax * st;
+  const int64_t pl = (int64_t)(SMEM ? m : mmax) * st;
   const Strided ur{scr, st}, c{scr + pl, st}, c2{scr + 2 * pl, st}, l{scr + 3 * pl, st}, y{scr + 4 * pl, st},
       flags{scr + 5 * pl, st};
   constexpr bool F32 = sizeof(T) == 4;
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
     const T cn = i + 2 < m ? ee(i + 1) : T(0);
     if (fabs(ai) >= fabs(b)) {
       if (ai == T(0)) ai = eps;
-      const T r = T(1) / ai;
+      const T r = recip(ai);
       ur[i] = r;
       const T f = b * r;
       l[i] = f;
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
       ai = an - f * ci;
       ci = cn;
     } else {
-      const T r = T(1) / b;
+      const T r = recip(b);
       ur[i] = r;
       const T f = ai * r;
       l[i] = f;
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
     }
   }
   if (ai == T(0)) ai = eps;
-  ur[m - 1] = T(1) / ai;
+  ur[m - 1] = recip(ai);
   c[m - 1] = 0;
   c2[m - 1] = 0;
   for (int i = 0; i < m; ++i) y[i] = (T)(hash_unit((uint32_t)i, (uint32_t)(t * 7919 + 13)) + 0.5 / (1 + i % 7));
@@ -531,7 +540,8 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
     }
     T nr = 0;
     for (int i = 0; i < m; ++i) nr = fma(y[i], y[i], nr);
-    nr = T(1) / sqrt(nr);
+    if constexpr (sizeof(T) == sizeof(double)) nr = rsqrt(nr);
+    else nr = T(1) / sqrt(nr);
     for (int i = 0; i < m; ++i) y[i] *= nr;
   }
   for (int i = 0; i < m; ++i) F[(int64_t)i * ldf + t] = (double)y[i];
@@ -663,17 +673,21 @@ int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, d
   if (f32) {
     k_multisect<float><<<m, 32, 0, s>>>(m, work, mmax);
     k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, (double)FLT_EPSILON);
-    const size_t ism = sizeof(float) * 6 * 32 * (size_t)mmax;
-    if (reserve_dynamic_smem(k_invit<float, true>, ism))
-      k_invit<float, true><<<niv, 32, ism, s>>>(m, k, work, mmax, F, ldf);
+    const size_t ism = sizeof(float) * 6 * 32 * (size_t)m;
+    if (reserve_dynamic_smem(k_invit<float, true, 32>, ism))
+      k_invit<float, true, 32><<<niv, 32, ism, s>>>(m, k, work, mmax, F, ldf);
     else
-      k_invit<float, false><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+      k_invit<float, false, 32><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
     k_cluster_orth<float><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
     k_backtransform<float><<<nbt, kBtWarps * 32, sizeof(float) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F, ldf);
   } else {
     k_multisect<double><<<m, 32, 0, s>>>(m, work, mmax);
     k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, DBL_EPSILON);
-    k_invit<double, false><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
+    const size_t dsm = sizeof(double) * 6 * 8 * (size_t)m;
+    if (reserve_dynamic_smem(k_invit<double, true, 8>, dsm))
+      k_invit<double, true, 8><<<(unsigned)((k + 7) / 8), 8, dsm, s>>>(m, k, work, mmax, F, ldf);
+    else
+      k_invit<double, false, 32><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
     k_cluster_orth<double><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
     k_backtransform<double><<<nbt, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F,
                                                                                        ldf);

@@ -254,7 +254,8 @@ __device__ PcholResult pchol_block(const double* G, int ldg, int c, double tol, 
   double (*A)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(smem);
   double (*Rs)[kMaxW + 1] = reinterpret_cast<double (*)[kMaxW + 1]>(smem + kMaxW * (kMaxW + 1));  // row k of R, original indices
   __shared__ int done[kMaxW], piv[kMaxW];
-  __shared__ double s_ref, s_thr, s_vlast, s_vdrop;
+  __shared__ double rinv[kMaxW];  // 1 / R_kk
+  __shared__ double s_ref, s_thr, s_vlast, s_vdrop, s_rkk;
   __shared__ int s_p, s_stop, s_rank;
   for (int e = tid; e < c * c; e += nth) {
     const int i = e / c, l = e % c;
@@ -290,14 +291,18 @@ __device__ PcholResult pchol_block(const double* G, int ldg, int c, double tol, 
           s_vlast = bv;
           piv[k] = bi;
           done[bi] = 1;
+          // once per pivot (a short FP64 chain): 1 / R_kk and R_kk = v / sqrt(v)
+          const double ri = rsqrt(bv);
+          rinv[k] = ri;
+          s_rkk = bv * ri;
         }
       }
     }
     __syncthreads();
     if (s_stop) break;
     const int p = s_p;
-    const double ri = 1.0 / sqrt(s_vlast);
-    for (int l = tid; l < c; l += nth) Rs[k][l] = (l == p) ? sqrt(s_vlast) : (done[l] ? 0.0 : A[p][l] * ri);
+    const double ri = rinv[k], rkk = s_rkk;
+    for (int l = tid; l < c; l += nth) Rs[k][l] = (l == p) ? rkk : (done[l] ? 0.0 : A[p][l] * ri);
     __syncthreads();
     for (int e = tid; e < c * c; e += nth) {
       const int i = e / c, l = e % c;
@@ -311,7 +316,7 @@ __device__ PcholResult pchol_block(const double* G, int ldg, int c, double tol, 
     for (int t = j; t >= 0; --t) {
       double sum = t == j ? 1.0 : 0.0;
       for (int u = t + 1; u <= j; ++u) sum = fma(-Rs[t][piv[u]], A[u][j], sum);
-      A[t][j] = sum / Rs[t][piv[t]];
+      A[t][j] = sum * rinv[t];
     }
   }
   __syncthreads();
@@ -447,12 +452,26 @@ __device__ double jacobi_block(const EigOp& op, double* eig_sm) {
         double c = 1.0, s = 0.0;
         if (q < m) {
           const double apq = A[p][q];
-          // threshold Jacobi: entries below the rounding level of their diagonal are left alone
-          if (fabs(apq) > 1e-18 * sqrt(fabs(A[p][p] * A[q][q])) && apq != 0.0) {
+          // threshold Jacobi: entries below the rounding level of their
+          // diagonal are left alone (|apq| > 1e-18 sqrt|a_pp a_qq|, squared)
+          if (apq * apq > 1e-36 * fabs(A[p][p] * A[q][q]) && apq != 0.0) {
             s_rot = 1;
-            const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            // the rotation's scalars with reciprocal square roots and Newton
+            // reciprocals, whose serial chain is several times shorter than
+            // IEEE square roots and divisions on the FP64 pipe
+            const double tau = (A[q][q] - A[p][p]) * rcp_newton(2.0 * apq);
+            const double at = fabs(tau);
+            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)); for |tau| >= 2^500,
+            // 1 / (2 |tau|) (tau^2 would overflow; the relative error is below 2^-1000)
+            double t;
+            if (at < 0x1p500) {
+              const double u = fma(tau, tau, 1.0);
+              t = rcp_newton(fma(u, rsqrt(u), at));
+            } else {
+              t = rcp_newton(2.0 * at);
+            }
+            t = tau >= 0.0 ? t : -t;
+            c = rsqrt(fma(t, t, 1.0));
             s = t * c;
           }
         }

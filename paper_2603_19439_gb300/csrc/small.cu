@@ -100,8 +100,18 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cl(double* H, int64_t ld
     const T nrm2 = cl_block_sum(s, red, bc);
     if (tid == 0) {
       const T x0 = v[j + 1];
-      const T alpha = nrm2 > T(0) ? -copysign(sqrt(nrm2), x0) : T(0);
-      const T beta = nrm2 > T(0) ? T(1) / (nrm2 - alpha * x0) : T(0);
+      T alpha = 0, beta = 0;
+      if (nrm2 > T(0)) {
+        if constexpr (sizeof(T) == sizeof(double)) {
+          // FP64: reciprocal square root and Newton reciprocal (short latency
+          // chains); nrm2 - alpha x0 = nrm2 + |x0| sqrt(nrm2) > 0
+          alpha = -copysign(nrm2 * rsqrt(nrm2), x0);
+          beta = rcp_newton(nrm2 - alpha * x0);
+        } else {
+          alpha = -copysign(sqrt(nrm2), x0);
+          beta = T(1) / (nrm2 - alpha * x0);
+        }
+      }
       v[j + 1] = x0 - alpha;
       bc[1] = alpha;
       bc[2] = beta;
@@ -258,7 +268,9 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
           s_vdrop = v > 0.0 ? v : 0.0;
         } else {
           s_stop = 0;
-          const T ri = T(1) / sqrt((T)v);
+          T ri;
+          if constexpr (sizeof(T) == sizeof(double)) ri = rsqrt(v);  // one short FP64 chain
+          else ri = T(1) / sqrt((T)v);
           s_rinv = ri;
           s_vlast = v;
           s_p = bi;

@@ -6,6 +6,10 @@
 // memory and no copies in flight.  The host reads the word, so a caller (or
 // a test) can see that an expired wait turns into GREST_ERR_TIMEOUT and that
 // the device stays usable afterwards.
+//
+// grest_check_fast_recip: evaluates the Newton reciprocal of the small
+// factorizations (common.cuh, rcp_newton) on caller-given inputs, so that a
+// test can hold it to its error bound against correctly rounded 1 / x.
 #include "tc_util.cuh"
 
 namespace grest {
@@ -22,8 +26,26 @@ __global__ void k_wait_never_arrives(int32_t* err) {
   if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0)) atomicCAS(err, 0, DERR_TIMEOUT);
 }
 
+__global__ void k_fast_recip(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = rcp_newton(x[i]);
+}
+
 }  // namespace
 }  // namespace grest
+
+extern "C" grest_status grest_check_fast_recip(const double* x, int64_t n, double* out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return GREST_ERR_INVALID_ARG;
+  if (n == 0) return GREST_OK;
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return GREST_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t blocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+  grest::k_fast_recip<<<(unsigned)blocks, 256, 0, s>>>(x, n, out);
+  e = cudaPeekAtLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? GREST_OK : GREST_ERR_CUDA;
+}
 
 extern "C" grest_status grest_check_bounded_wait(void* cuda_stream) {
   int32_t* err = nullptr;

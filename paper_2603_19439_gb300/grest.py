@@ -76,7 +76,8 @@ EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sy
            "grest_server_get_embedding", "grest_server_resident", "grest_server_destroy", "grest_checkpoint",
            "grest_restore", "grest_checkpoint_embedding", "grest_server_set_eviction", "grest_server_counters",
            "grest_group_create", "grest_group_apply_updates", "grest_group_get_embedding", "grest_group_get_ritz_values",
-           "grest_group_info", "grest_group_destroy", "grest_check_bounded_wait", "grest_destroy", "grest_status_str"]
+           "grest_group_info", "grest_group_destroy", "grest_check_bounded_wait", "grest_check_fast_recip",
+           "grest_destroy", "grest_status_str"]
 
 _lib = None
 
@@ -132,6 +133,7 @@ def load_library(path=None):
     lib.grest_group_get_ritz_values.argtypes = [vp, i32, vp, C.POINTER(i32)]
     lib.grest_group_info.argtypes = [vp] + [C.POINTER(i32)] * 6
     lib.grest_check_bounded_wait.argtypes = [vp]
+    lib.grest_check_fast_recip.argtypes = [vp, i64, vp, vp]
     lib.grest_group_destroy.argtypes = [vp]
     lib.grest_group_destroy.restype = None
     lib.grest_destroy.argtypes = [vp]
