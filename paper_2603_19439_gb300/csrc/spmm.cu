@@ -12,11 +12,6 @@
 // graphs) go to a second kernel where a block of 8 warps splits the
 // neighbour list and reduces in shared memory in a fixed order, so results
 // are deterministic.
-//
-// Cache use: X is larger than L2 at the benchmark sizes, and the hubs' rows
-// are gathered far more often than the rest; the column indices, weights and
-// the rows of Y pass through once, so they are loaded and stored with the
-// streaming (evict-first) hint and leave L2 to the rows of X.
 #include "common.cuh"
 
 namespace grest {
@@ -39,7 +34,7 @@ __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, co
     // slot each when T is double
     for (int64_t j0 = beg; j0 < end; j0 += 32) {
       const int64_t j = j0 + lane;
-      const int32_t mc = j < end ? __ldcs(col + j) : 0;  // streamed once: evict first
+      const int32_t mc = j < end ? col[j] : 0;
       const int cnt = (int)((end - j0) < 32 ? (end - j0) : 32);
       int k = 0;
       for (; NCH <= 2 && k + 8 <= cnt; k += 8) {
@@ -87,8 +82,8 @@ __device__ __forceinline__ void gather_range(const int32_t* __restrict__ col, co
     int32_t mc = 0;
     T ma = 0;
     if (j < end) {
-      mc = __ldcs(col + j);
-      double a = HASVAL ? __ldcs(val + j) : 1.0;
+      mc = col[j];
+      double a = HASVAL ? val[j] : 1.0;
       if (nl) a *= op.dis[mc];
       ma = (T)a;
     }
@@ -201,7 +196,7 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ r
       if (c < w) {
         T y = (T)scale * acc.v[ch];
         if (has_diag) y += (T)dcoef * (T)xr[c];
-        __stcs(yr + c, y);  // written once here: keep L2 for the gathered rows of X
+        yr[c] = y;
       }
     }
   }
