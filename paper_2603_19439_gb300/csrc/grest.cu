@@ -100,6 +100,14 @@ struct grest_ctx {
   double* XZ = nullptr;         // X_bar^T Z (LOWRANK mode), 64 x mmax
   uint8_t* gemm_img = nullptr;  // tensor-core GEMM: B^T operand images
   size_t gemm_img_cap = 0;
+  // second lane of the step (large graphs with an RSVD new-node block): a
+  // high-priority stream and its own Gram / GEMM scratch, so that the RSVD
+  // sketch (A5, S.1) runs beside A3 and A4 (see step_t)
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double* part2 = nullptr;
+  uint8_t* gemm_img2 = nullptr;
+  double* Cv2 = nullptr;
   double* eigwork = nullptr;
   int32_t* err = nullptr;
   // grest_centrality scratch (allocated on first use)
@@ -191,7 +199,7 @@ void free_ctx(grest_ctx* c) {
                   c->U, c->Un, c->theta, c->Zv, c->MZv, c->V2v, c->Yrv, c->Yr2v, c->Omv, c->EtMv, c->Idv, c->U32,
                   c->Rres, c->Cm, c->Cv,
                   c->G, c->T, c->H, c->F, c->XtM, c->Gs, c->Uh, c->ritz, c->th_new, c->tmpk, c->info, c->part,
-                  c->ipart, c->piv, c->gemm_img, c->dmax_old, c->XZ, c->gw.edel, c->eigwork, c->err, c->resn, c->cent_work, c->cent_buf, c->top_id_buf, c->top_val_buf, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
+                  c->ipart, c->piv, c->gemm_img, c->part2, c->gemm_img2, c->Cv2, c->dmax_old, c->XZ, c->gw.edel, c->eigwork, c->err, c->resn, c->cent_work, c->cent_buf, c->top_id_buf, c->top_val_buf, c->b_iu, c->b_iv, c->b_du, c->b_dv, c->b_dn, c->b_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_info) cudaFreeHost(c->h_info);
@@ -201,6 +209,9 @@ void free_ctx(grest_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->pev)
     if (e) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->s2) cudaStreamDestroy(c->s2);
   delete c;
 }
 
@@ -575,6 +586,24 @@ void project_out(grest_ctx* c, T* X, int64_t ldx, int w, int64_t n) {
   gemm(c, n, c->Ku, w, -1.0, Zp<T>(c), c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx);
 }
 
+// Graphs of at least this many nodes at grest_init get the step's second lane.
+constexpr int64_t kOverlapRows = 1 << 17;
+
+// While alive, the step's launch wrappers enqueue on the second lane: its
+// stream and its own Gram partials, GEMM operand images and projection
+// coefficients (the wrappers read these from the context).
+struct Lane2 {
+  grest_ctx* c;
+  explicit Lane2(grest_ctx* ctx) : c(ctx) { flip(); }
+  ~Lane2() { flip(); }
+  void flip() {
+    std::swap(c->stream, c->s2);
+    std::swap(c->part, c->part2);
+    std::swap(c->gemm_img, c->gemm_img2);
+    std::swap(c->Cv, c->Cv2);
+  }
+};
+
 // CholQR with pivoting: Out (n x rank) = X (n x w) T; returns rank via info slot
 template <typename T>
 grest_status cholqr_pass(grest_ctx* c, const T* X, int64_t ldx, int w, int64_t n, double tol, double abs_ref,
@@ -817,6 +846,42 @@ grest_status refine_mixed_f64(grest_ctx* c, int64_t N2) {
   return GREST_OK;
 }
 
+// A5 with an RSVD block (Sec. 3.5), the part that needs X_bar but not
+// M X_bar: S.1 Y = P_perp Delta_2 Omega and its CholQR2 with pivoting (basis
+// in Yr, rank rY), then Delta_2^T Yr (rows N.. of M Yr into EtM) and
+// X_bar^T Yr for S.2.
+template <typename T>
+grest_status rsvd_sketch(grest_ctx* c, int64_t N, int64_t N2, int64_t S, int* rY_out) {
+  const int q = c->q, Ku = c->Ku;
+  const int64_t ldq = c->ldq, ldz = c->ldz;
+  T* Z = Zp<T>(c);
+  T* Yr = Yrp<T>(c);
+  T* Yr2 = Yr2p<T>(c);
+  T* Om = Omp<T>(c);
+  T* EtM = EtMp<T>(c);
+  // S.1: Y = P_perp Delta_2 Omega
+  gaussian_omega(Om, ldq, S, q, c->cfg.seed, (uint64_t)c->step, c->stream);
+  c->launches += 1;
+  spmm(c, Om, ldq, Yr, ldq, q, 0, N2, N, c->batch_new_edges + S, S);
+  project_out(c, Yr, ldq, q, N2);
+  project_out(c, Yr, ldq, q, N2);
+  // M = orth(Y): CholQR2 with pivoting
+  int rY = 0;
+  grest_status st = cholqr_pass(c, Yr, ldq, q, N2, c->cfg.drop_tol, 0.0, c->theta, Yr2, ldq, 8, true, &rY);
+  if (st != GREST_OK) return st;
+  int rY2 = 0;
+  st = cholqr_pass(c, Yr2, ldq, rY, N2, 1e-14, 0.0, nullptr, Yr, ldq, 12, false, &rY2);
+  if (st != GREST_OK) return st;
+  c->stats.rank_y = rY;
+  if (rY > 0) {
+    // S.2, first products: Delta_2^T M (rows N.. of M Yr) and X_bar^T M
+    spmm(c, Yr, ldq, EtM, ldq, rY, N, N2, 0, c->batch_new_edges + S, N2);
+    gram(c, Z, ldz, Ku, Yr, ldq, rY, N2, c->XtM, rY, false);
+  }
+  *rY_out = rY;
+  return GREST_OK;
+}
+
 template <typename T>
 grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   const int64_t N2 = N + S;
@@ -843,6 +908,19 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
     c->Ku = r1;
   }
   const int Ku = c->Ku;
+  // A5 with an RSVD block: its sketch (S.1 and the products of S.2 that need
+  // X_bar only) is independent of A3 and A4; with a second lane it runs there,
+  // beside them (its pivoted Cholesky and eigen kernels hold few SMs, and
+  // A3 / A4 fill the rest), joined before S.2's use of M X_bar.  The same
+  // kernels see the same inputs either way, so the results do not change.
+  const bool rsvd_block = S > 0 && c->cfg.subspace != GREST_SUB_GREST2 &&
+                          (c->cfg.subspace == GREST_SUB_RSVD || (c->cfg.subspace == GREST_SUB_AUTO && S > c->q));
+  const bool overlap = rsvd_block && c->s2 != nullptr;
+  if (rsvd_block) {
+    grest_status st = ensure_S(c, S);
+    if (st != GREST_OK) return st;
+  }
+  if (overlap) CK(cudaEventRecord(c->ev_fork, s));
   const bool lowrank = c->cfg.projection == GREST_PROJ_LOWRANK;
   const bool delta_w = c->cfg.w_block == GREST_WB_DELTA;
   // A3: MZ[:, 0:Ku] = M X_bar (EXACT projection) or Delta X_bar (LOWRANK,
@@ -871,6 +949,18 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   gram(c, Z, ldz, Ku, src, lds, Ku, N2, c->Cm, Ku, false);
   gemm(c, N2, Ku, Ku, -1.0, Z, ldz, c->Cm, Ku, 1.0, src, lds, W, ldz);
   project_out(c, W, ldz, Ku, N2);
+  int rY = 0;
+  if (overlap) {
+    grest_status st2;
+    {
+      Lane2 lane(c);
+      CK(cudaStreamWaitEvent(c->stream, c->ev_fork, 0));
+      st2 = rsvd_sketch<T>(c, N, N2, S, &rY);
+      CK(cudaEventRecord(c->ev_join, c->stream));
+    }
+    CK(cudaStreamWaitEvent(s, c->ev_join, 0));
+    if (st2 != GREST_OK) return st2;
+  }
   // A5: new-node block
   int cb = 0;
   int mode = 2;
@@ -887,30 +977,14 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
       cb = (int)S;
     } else {
       mode = 4;
-      grest_status st = ensure_S(c, S);
-      if (st != GREST_OK) return st;
+      if (!overlap) {
+        grest_status st = rsvd_sketch<T>(c, N, N2, S, &rY);
+        if (st != GREST_OK) return st;
+      }
       T* Yr = Yrp<T>(c);
-      T* Yr2 = Yr2p<T>(c);
-      T* Om = Omp<T>(c);
       T* EtM = EtMp<T>(c);
-      // S.1: Y = P_perp Delta_2 Omega
-      gaussian_omega(Om, ldq, S, q, c->cfg.seed, (uint64_t)c->step, s);
-      c->launches += 1;
-      spmm(c, Om, ldq, Yr, ldq, q, 0, N2, N, c->batch_new_edges + S, S);
-      project_out(c, Yr, ldq, q, N2);
-      project_out(c, Yr, ldq, q, N2);
-      // M = orth(Y): CholQR2 with pivoting
-      int rY = 0;
-      st = cholqr_pass(c, Yr, ldq, q, N2, c->cfg.drop_tol, 0.0, c->theta, Yr2, ldq, 8, true, &rY);
-      if (st != GREST_OK) return st;
-      int rY2 = 0;
-      st = cholqr_pass(c, Yr2, ldq, rY, N2, 1e-14, 0.0, nullptr, Yr, ldq, 12, false, &rY2);
-      if (st != GREST_OK) return st;
-      c->stats.rank_y = rY;
       if (rY > 0) {
-        // S.2: B_s^T = Delta_2^T M - (Delta_2^T X_bar)(X_bar^T M), Delta_2^T X_bar = Y1[N:N2]
-        spmm(c, Yr, ldq, EtM, ldq, rY, N, N2, 0, c->batch_new_edges + S, N2);
-        gram(c, Z, ldz, Ku, Yr, ldq, rY, N2, c->XtM, rY, false);
+        // S.2 (cont.): B_s^T = Delta_2^T M - (Delta_2^T X_bar)(X_bar^T M), Delta_2^T X_bar = Y1[N:N2]
         gemm(c, S, Ku, rY, -1.0, MZ + N * ldz, ldz, c->XtM, rY, 1.0, EtM, ldq, EtM, ldq);
         // left singular vectors of B_s via eig(B_s B_s^T), L leading
         gram(c, EtM, ldq, rY, EtM, ldq, rY, S, c->Gs, rY, true);
@@ -1459,6 +1533,17 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&c->XZ, (int64_t)64 * mm));
   c->gemm_img_cap = gemm_tc_img_bytes(512, 256);
   IK(dalloc(&c->gemm_img, c->gemm_img_cap));
+  if (n >= kOverlapRows && !(cfg->flags & GREST_FLAG_ONE_STREAM) &&
+      (cfg->subspace == GREST_SUB_AUTO || cfg->subspace == GREST_SUB_RSVD)) {
+    int lo = 0, hi = 0;
+    IK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    IK(cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi));
+    IK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    IK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    IK(dalloc(&c->part2, c->part_cap));
+    IK(dmalloc((void**)&c->gemm_img2, c->gemm_img_cap));
+    IK(dalloc(&c->Cv2, (int64_t)64 * (cm + 64)));
+  }
   IK(dalloc(&c->err, 1));
   IK(cudaMallocHost((void**)&c->h_info, sizeof(double) * 64));
   IK(cudaMallocHost((void**)&c->h_err, sizeof(int32_t)));

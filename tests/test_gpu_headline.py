@@ -14,7 +14,10 @@ compared:
   * GREST_MIXED and GREST_MIXED_FAST: tracked values within 1e-6 |theta_1|,
     per-pair residuals within 1e-6 |theta_1| of the oracle's, the Galerkin
     residual U^T (M U - U Theta) and the orthonormality at FP64 level, and
-    the same basis dimension m as the oracle."""
+    the same basis dimension m as the oracle;
+  * the second stream of a large context (the RSVD sketch beside the
+    projection of the previous pairs) changes no bit of the result: a
+    GREST_MIXED tracker with GREST_FLAG_ONE_STREAM gives identical pairs."""
 import numpy as np
 import pytest
 
@@ -82,3 +85,19 @@ def test_mixed_paths_match_oracle_at_1m(stream, prec):
         assert d["galerkin"] < 1e-12 and d["orth_err"] < 1e-12, f"step {t}"
         assert abs(d["max_residual"] - rg.max() / abs(thg[0])) <= 1e-9
     tr.close()
+
+
+def test_second_stream_changes_nothing_at_1m(stream):
+    s = stream
+    out = []
+    for flags in (0, G.FLAG_ONE_STREAM):
+        tr = G.Tracker(s["g"].n, s["rp"], s["col"], None, s["X0"], s["th0"], K, L=100, P=100, seed=SEED,
+                       precision=G.MIXED, drop_tol=1e-3, flags=flags, node_capacity=s["g"].n + 20_000)
+        for b in s["batches"]:
+            d = tr.update(b)
+            assert d["mode"] == 4
+        Ug, thg, _ = tr.embedding()
+        out.append((Ug, thg, tr.ritz_values()))
+        tr.close()
+    (U1, t1, r1), (U2, t2, r2) = out
+    assert np.array_equal(U1, U2) and np.array_equal(t1, t2) and np.array_equal(r1, r2)
