@@ -94,18 +94,19 @@ enum { GREST_WB_RESID = 0, GREST_WB_DELTA = 1 };
 /* grest_config.flags */
 #define GREST_FLAG_CHECK 1u   /* after each step compute residual diagnostics into grest_stats */
 #define GREST_FLAG_PROFILE 2u /* time every kernel class with CUDA events (grest_stats.prof_*) */
-/* Streams.  A context whose graph has at least 131,072 nodes at grest_init
- * (and whose subspace setting allows the RSVD new-node block) also creates a
- * second, high-priority CUDA stream of its own, with its own Gram and GEMM
- * scratch (about 70 MB): in a step with an RSVD block, the sketch of Sec. 3.5
- * (S.1, its CholQR2 and the first products of S.2) runs there beside the
- * projection of the previous pairs (Alg. 2, Y1 = M X_bar and W), and the
- * caller's stream waits for it before S.2 continues, so the step's work is
- * still complete when the caller's stream is.  The results are the same
- * bits either way.  With GREST_PROFILE the per-class times of the two
- * streams overlap and can add up to more than the step.
- * GREST_FLAG_ONE_STREAM keeps the whole step on the caller's stream. */
-#define GREST_FLAG_ONE_STREAM 4u
+/* GREST_FLAG_TWO_STREAMS: a context whose graph has at least 131,072 nodes
+ * at grest_init (and whose subspace setting allows the RSVD new-node block)
+ * also creates a second, high-priority CUDA stream of its own, with its own
+ * Gram and GEMM scratch (about 70 MB).  In a step with an RSVD block, the
+ * sketch of Sec. 3.5 (S.1, its CholQR2 and the first products of S.2) then
+ * runs there beside the projection of the previous pairs (Alg. 2,
+ * Y1 = M X_bar and W), and the caller's stream waits for it before S.2
+ * continues, so the step's work is still complete when the caller's stream
+ * is.  The results are the same bits either way.  Off by default: the gain
+ * is about 2% of a step at n = 1M, and the kernels of the two streams slow
+ * each other, so GREST_FLAG_PROFILE's per-class times no longer describe
+ * the kernels alone. */
+#define GREST_FLAG_TWO_STREAMS 4u
 
 typedef struct {
   int32_t op;          /* GREST_OP_*                                                   */

@@ -586,7 +586,8 @@ void project_out(grest_ctx* c, T* X, int64_t ldx, int w, int64_t n) {
   gemm(c, n, c->Ku, w, -1.0, Zp<T>(c), c->ldz, c->Cv, w, 1.0, X, ldx, X, ldx);
 }
 
-// Graphs of at least this many nodes at grest_init get the step's second lane.
+// With GREST_FLAG_TWO_STREAMS, graphs of at least this many nodes at
+// grest_init get the step's second lane.
 constexpr int64_t kOverlapRows = 1 << 17;
 
 // While alive, the step's launch wrappers enqueue on the second lane: its
@@ -909,10 +910,11 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   }
   const int Ku = c->Ku;
   // A5 with an RSVD block: its sketch (S.1 and the products of S.2 that need
-  // X_bar only) is independent of A3 and A4; with a second lane it runs there,
-  // beside them (its pivoted Cholesky and eigen kernels hold few SMs, and
-  // A3 / A4 fill the rest), joined before S.2's use of M X_bar.  The same
-  // kernels see the same inputs either way, so the results do not change.
+  // X_bar only) is independent of A3 and A4; with a second lane
+  // (GREST_FLAG_TWO_STREAMS) it runs there, beside them (its pivoted
+  // Cholesky and eigen kernels hold few SMs, and A3 / A4 fill the rest),
+  // joined before S.2's use of M X_bar.  The same kernels see the same
+  // inputs either way, so the results do not change.
   const bool rsvd_block = S > 0 && c->cfg.subspace != GREST_SUB_GREST2 &&
                           (c->cfg.subspace == GREST_SUB_RSVD || (c->cfg.subspace == GREST_SUB_AUTO && S > c->q));
   const bool overlap = rsvd_block && c->s2 != nullptr;
@@ -1533,7 +1535,7 @@ grest_status grest_init(const grest_config* cfg, int64_t n, const int64_t* rowpt
   IK(dalloc(&c->XZ, (int64_t)64 * mm));
   c->gemm_img_cap = gemm_tc_img_bytes(512, 256);
   IK(dalloc(&c->gemm_img, c->gemm_img_cap));
-  if (n >= kOverlapRows && !(cfg->flags & GREST_FLAG_ONE_STREAM) &&
+  if (n >= kOverlapRows && (cfg->flags & GREST_FLAG_TWO_STREAMS) &&
       (cfg->subspace == GREST_SUB_AUTO || cfg->subspace == GREST_SUB_RSVD)) {
     int lo = 0, hi = 0;
     IK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -1762,7 +1764,10 @@ grest_status grest_get_embedding(grest_ctx* c, double* U, double* theta, uint8_t
   *n_out = n;
   cudaStream_t s = c->stream;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K, n, kind, s));
+  // rows of U are contiguous when ldu = K: one linear copy (a pitched copy
+  // of n rows of 8 K bytes runs far below the host link's bandwidth)
+  if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, kind, s));
+  else if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K, n, kind, s));
   if (theta) CK(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->K, kind, s));
   if (live) CK(cudaMemcpyAsync(live, c->g.live, n, kind, s));
   return from_cuda(cudaStreamSynchronize(s));

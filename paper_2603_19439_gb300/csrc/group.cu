@@ -550,7 +550,9 @@ grest_status grest_group_get_embedding(grest_group* G, int32_t i, double* U, dou
   *n_out = st.N;
   const int K = G->P.K;
   const GMeta& m = G->meta[i];
-  if (U)
+  if (U && G->P.ldu == K)  // contiguous rows: one linear copy
+    GK(cudaMemcpy(U, G->P.U + m.node_off * G->P.ldu, sizeof(double) * K * st.N, cudaMemcpyDeviceToHost));
+  else if (U)
     GK(cudaMemcpy2D(U, sizeof(double) * K, G->P.U + m.node_off * G->P.ldu, sizeof(double) * G->P.ldu,
                     sizeof(double) * K, st.N, cudaMemcpyDeviceToHost));
   if (theta) {

@@ -22,7 +22,7 @@ PROJ_EXACT, PROJ_LOWRANK = 0, 1
 WB_RESID, WB_DELTA = 0, 1
 FLAG_CHECK = 1
 FLAG_PROFILE = 2
-FLAG_ONE_STREAM = 4
+FLAG_TWO_STREAMS = 4
 PROF_CLASSES = ("spmm", "gram", "gemm", "small", "graph")
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid update batch", 3: "device out of memory",

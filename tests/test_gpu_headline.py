@@ -15,9 +15,9 @@ compared:
     per-pair residuals within 1e-6 |theta_1| of the oracle's, the Galerkin
     residual U^T (M U - U Theta) and the orthonormality at FP64 level, and
     the same basis dimension m as the oracle;
-  * the second stream of a large context (the RSVD sketch beside the
+  * the second stream of GREST_FLAG_TWO_STREAMS (the RSVD sketch beside the
     projection of the previous pairs) changes no bit of the result: a
-    GREST_MIXED tracker with GREST_FLAG_ONE_STREAM gives identical pairs."""
+    GREST_MIXED tracker with and without it gives identical pairs."""
 import numpy as np
 import pytest
 
@@ -90,7 +90,7 @@ def test_mixed_paths_match_oracle_at_1m(stream, prec):
 def test_second_stream_changes_nothing_at_1m(stream):
     s = stream
     out = []
-    for flags in (0, G.FLAG_ONE_STREAM):
+    for flags in (G.FLAG_TWO_STREAMS, 0):
         tr = G.Tracker(s["g"].n, s["rp"], s["col"], None, s["X0"], s["th0"], K, L=100, P=100, seed=SEED,
                        precision=G.MIXED, drop_tol=1e-3, flags=flags, node_capacity=s["g"].n + 20_000)
         for b in s["batches"]:
