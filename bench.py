@@ -21,7 +21,8 @@ FP64 arm is part of the line.
 memory; `e2e` times K further steps through the same public call with the
 batches in pinned host memory (host->device copies inside the timed region)
 and a device->host read of the updated embedding (U and theta) after every
-step.  Under torchrun every rank runs an independent replica (the update
+step, started without waiting (grest_get_embedding_async) so that it
+overlaps the next update; every read completes inside the timed region.  Under torchrun every rank runs an independent replica (the update
 does not shard; there is no collective on the data path) and rank 0 prints
 the line.  --workload cl200k / sbm2k run the other two single-graph
 workloads (FP64, with the oracle timed beside them).
@@ -507,20 +508,24 @@ def run_grest(args):
     if tr_head is not tr64:
         tr64.close()
     # ---- end to end through the public call from pinned host memory (headline arm)
+    # every step's pairs are read into pinned host memory with
+    # grest_get_embedding_async, so the copy of step t overlaps update t + 1
+    # (two host buffers, used in turn; all reads complete inside the region)
     cap = stream_node_capacity(g.n, batches)
-    U_h = torch.empty((cap, K), dtype=torch.float64).pin_memory().numpy()
-    theta_h = torch.empty(K, dtype=torch.float64).pin_memory().numpy()
+    U_h = [torch.empty((cap, K), dtype=torch.float64).pin_memory() for _ in range(2)]
+    theta_h = [torch.empty(K, dtype=torch.float64).pin_memory() for _ in range(2)]
     h2d = d2h = 0
     barrier()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     e2.record(stream)
-    nn = G.C.c_int64()
-    for b in host:
+    for i, b in enumerate(host):
         tr_head.update(b, on_device=False)
-        tr_head.lib.grest_get_embedding(tr_head.h, U_h.ctypes.data, theta_h.ctypes.data, None, G.C.byref(nn), 0)
+        tr_head.wait_embedding()  # the read of step i - 2 (done by now) frees its buffer
+        rows = tr_head.embedding_async(U_h[i % 2], theta_h[i % 2])
         h2d += 4 * (2 * b.n_ins + 2 * b.n_del + b.del_nodes.size)
-        d2h += 8 * (nn.value * K + K)
+        d2h += 8 * (rows * K + K)
+    tr_head.wait_embedding()
     e3.record(stream)
     barrier()
     t_e2e = max_over_ranks(e2.elapsed_time(e3) * 1e-3, world)
@@ -576,7 +581,8 @@ def run_grest(args):
         "arms": arms,
         "e2e": {"value": world * steps / t_e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // steps,
                 "d2h_bytes_per_step": d2h // steps, "precision": headline,
-                "returns": "U (N' x K FP64) and theta after every step"},
+                "returns": "U (N' x K FP64) and theta after every step, read with grest_get_embedding_async into "
+                           "pinned host memory (overlapping the next update); all reads complete inside the region"},
         "gpu_launches": int(main["prof"]["launches"]),
         "roofline": arms[headline]["roofline"],
         "clocks": main["clk"],

@@ -266,6 +266,27 @@ grest_status grest_get_embedding(grest_ctx *ctx, double *U, double *theta, uint8
                                  int64_t *n_out, int32_t on_device);
 
 /*
+ * The same read of (X_K, Lambda_K) as grest_get_embedding (U and theta; no
+ * live mask), started without waiting, so that the copy to the host overlaps
+ * the next grest_apply_update (the pairs are the step's result, Alg. 2; the
+ * paper has no counterpart for the transfer).  The copies run on a copy
+ * stream of the context after the work enqueued so far on its stream; U
+ * (n_out x k, row-major) and theta (k) are caller-owned host or device
+ * memory, and for the copy to overlap anything host memory must be pinned
+ * (cudaHostAlloc / cudaHostRegister).  n_out (required) receives the number
+ * of node ids now.  The outputs are complete after grest_wait_embedding (or
+ * grest_destroy); until then the caller must not read or reuse them.  The
+ * next update keeps the pairs being copied until the copy is done: its lift
+ * (the first write to them) waits for the copy on the device, and a
+ * capacity growth or grest_set_embedding waits on the host.  Several reads
+ * may be outstanding; they complete in order.
+ */
+grest_status grest_get_embedding_async(grest_ctx *ctx, double *U, double *theta, int64_t *n_out);
+
+/* Wait (host) until every read started by grest_get_embedding_async is complete. */
+grest_status grest_wait_embedding(grest_ctx *ctx);
+
+/*
  * Replace (X_K, Lambda_K) for the current graph, e.g. to resume from a saved
  * embedding or to start from pairs computed after grest_init.  U: n x k
  * row-major with orthonormal columns (rows of tombstoned ids are ignored and

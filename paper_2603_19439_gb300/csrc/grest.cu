@@ -108,6 +108,11 @@ struct grest_ctx {
   double* part2 = nullptr;
   uint8_t* gemm_img2 = nullptr;
   double* Cv2 = nullptr;
+  // grest_get_embedding_async: copy stream, its events, and whether a copy
+  // of U may still be reading the pairs
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_copied = nullptr;
+  bool copy_pending = false;
   double* eigwork = nullptr;
   int32_t* err = nullptr;
   // grest_centrality scratch (allocated on first use)
@@ -179,6 +184,15 @@ void dfree(void* p, size_t bytes) {
   t_dev_bytes -= bytes;
 }
 
+// wait (host) until an embedding copy started by grest_get_embedding_async
+// has finished reading the device pairs
+grest_status settle_copy(grest_ctx* c) {
+  if (!c->copy_pending) return GREST_OK;
+  const cudaError_t e = cudaEventSynchronize(c->ev_copied);
+  c->copy_pending = false;
+  return e == cudaSuccess ? GREST_OK : GREST_ERR_CUDA;
+}
+
 grest_status map_dev_err(int32_t e) {
   switch (e) {
     case DERR_NONE: return GREST_OK;
@@ -212,6 +226,9 @@ void free_ctx(grest_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->s2) cudaStreamDestroy(c->s2);
+  if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
   delete c;
 }
 
@@ -302,6 +319,10 @@ std::vector<NodeArray> node_arrays(grest_ctx* c) {
 // buffer is allocated before an old one is released, so a failed
 // allocation returns GREST_ERR_OOM with the context unchanged.
 grest_status grow_nodes(grest_ctx* c, int64_t need) {
+  {
+    const grest_status st = settle_copy(c);  // U moves to a new buffer
+    if (st != GREST_OK) return st;
+  }
   const int64_t old_cap = c->g.n_cap, n = c->g.n;
   int64_t cap = std::max<int64_t>(need, old_cap + old_cap / 2);
   cap = std::min<int64_t>(round_up(cap, 1024), (int64_t)INT32_MAX);
@@ -1038,6 +1059,9 @@ grest_status step_t(grest_ctx* c, int64_t N, int64_t S, bool removed) {
   // A9: leading K eigenpairs of H (Alg. 1)
   eig(c, c->H, m, m, K, c->cfg.op, c->th_new, c->F, K, c->ritz, c->info + 28, small_f32<T>(c));
   CK(cudaEventRecord(c->ev[6], s));
+  // the lift is the step's first write to the buffers of the previous pairs:
+  // a copy of them started by grest_get_embedding_async finishes first
+  if (c->copy_pending) CK(cudaStreamWaitEvent(s, c->ev_copied, 0));
   // A10: X = Z F_K, sign normalization
   if constexpr (sizeof(T) == sizeof(double)) {
     gemm(c, N2, m, K, 1.0, Z, ldz, c->F, K, 0.0, static_cast<const T*>(nullptr), 0, c->Un, c->ldu);
@@ -1773,9 +1797,41 @@ grest_status grest_get_embedding(grest_ctx* c, double* U, double* theta, uint8_t
   return from_cuda(cudaStreamSynchronize(s));
 }
 
+grest_status grest_get_embedding_async(grest_ctx* c, double* U, double* theta, int64_t* n_out) {
+  if (!c || !n_out) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  if (!c->cstream) {
+    CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+  }
+  const int64_t n = c->g.n;
+  *n_out = n;
+  cudaStream_t cs = c->cstream;
+  CK(cudaEventRecord(c->ev_ready, c->stream));
+  CK(cudaStreamWaitEvent(cs, c->ev_ready, 0));
+  if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, cudaMemcpyDefault, cs));
+  else if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K, n,
+                                   cudaMemcpyDefault, cs));
+  if (theta) CK(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->K, cudaMemcpyDefault, cs));
+  CK(cudaEventRecord(c->ev_copied, cs));
+  c->copy_pending = true;
+  return GREST_OK;
+}
+
+grest_status grest_wait_embedding(grest_ctx* c) {
+  if (!c) return GREST_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  return settle_copy(c);
+}
+
 grest_status grest_set_embedding(grest_ctx* c, const double* U, const double* theta, int32_t on_device) {
   if (!c || !U || !theta) return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
+  {
+    const grest_status st = settle_copy(c);
+    if (st != GREST_OK) return st;
+  }
   cudaStream_t s = c->stream;
   const int64_t n = c->g.n;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -2110,6 +2166,7 @@ void grest_destroy(grest_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   cudaStreamSynchronize(c->stream);
+  if (c->cstream) cudaStreamSynchronize(c->cstream);
   free_ctx(c);
 }
 

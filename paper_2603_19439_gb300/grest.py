@@ -70,7 +70,7 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["grest_config_default", "grest_init", "grest_apply_update", "grest_sync", "grest_get_embedding",
-           "grest_set_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
+           "grest_set_embedding", "grest_get_embedding_async", "grest_wait_embedding", "grest_get_ritz_values", "grest_get_stats", "grest_apply_operator", "grest_gram",
            "grest_gram_f32", "grest_gemm_f32", "grest_gram_noalloc", "grest_centrality", "grest_batch_create",
            "grest_batch_apply_updates", "grest_batch_destroy", "grest_get_device_bytes", "grest_server_create",
            "grest_server_add_graph", "grest_server_submit", "grest_server_wait", "grest_server_poll", "grest_server_remove_graph",
@@ -99,6 +99,8 @@ def load_library(path=None):
     lib.grest_sync.argtypes = [vp]
     lib.grest_get_embedding.argtypes = [vp, vp, vp, vp, C.POINTER(i64), i32]
     lib.grest_set_embedding.argtypes = [vp, vp, vp, i32]
+    lib.grest_get_embedding_async.argtypes = [vp, vp, vp, C.POINTER(i64)]
+    lib.grest_wait_embedding.argtypes = [vp]
     lib.grest_get_ritz_values.argtypes = [vp, vp, C.POINTER(i32)]
     lib.grest_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.grest_apply_operator.argtypes = [vp, vp, i64, vp, i64, i32]
@@ -471,6 +473,7 @@ class Tracker:
             raise GrestError(st, "grest_init")
         self.h = h
         self._keep = None
+        self.n = int(n)  # node ids after the last update
 
     def update(self, batch, on_device=False):
         """Apply one batch (workloads.Batch with host arrays, or torch CUDA tensors
@@ -485,6 +488,7 @@ class Tracker:
         st = self.lib.grest_apply_update(self.h, C.byref(u), C.byref(s))
         if st != 0:
             raise GrestError(st, "grest_apply_update")
+        self.n = int(s.n_nodes)
         return s.as_dict()
 
     def embedding(self):
@@ -499,6 +503,26 @@ class Tracker:
         if st != 0:
             raise GrestError(st, "grest_get_embedding")
         return U, th, live.astype(bool)
+
+    def embedding_async(self, U_buf, theta_buf):
+        """Start copying (X_K, Lambda_K) into caller buffers (numpy arrays or
+        tensors: U_buf rows >= n, k columns, contiguous float64; pinned host
+        memory for the copy to overlap the next update).  Returns n; the
+        buffers are complete after wait_embedding()."""
+        if U_buf is not None and (U_buf.shape[0] < self.n or U_buf.shape[1] != self.k):
+            raise ValueError("U_buf needs at least %d rows and %d columns" % (self.n, self.k))
+        if theta_buf is not None and theta_buf.shape[0] < self.k:
+            raise ValueError("theta_buf needs %d values" % self.k)
+        n = C.c_int64()
+        st = self.lib.grest_get_embedding_async(self.h, _ptr(U_buf), _ptr(theta_buf), C.byref(n))
+        if st != 0:
+            raise GrestError(st, "grest_get_embedding_async")
+        return n.value
+
+    def wait_embedding(self):
+        st = self.lib.grest_wait_embedding(self.h)
+        if st != 0:
+            raise GrestError(st, "grest_wait_embedding")
 
     def embedding_device(self, U_dev, theta_dev):
         """Copy (X_K, Lambda_K) into device tensors (n x k and k, float64)."""
@@ -610,6 +634,7 @@ class Tracker:
             raise GrestError(st, "grest_restore")
         self = cls.__new__(cls)
         self.lib, self.k, self.cfg, self.h, self._keep = lib, k.value, None, h, None
+        self.n = n.value
         return self
 
     def device_bytes(self):
