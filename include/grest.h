@@ -272,8 +272,11 @@ grest_status grest_get_embedding(grest_ctx *ctx, double *U, double *theta, uint8
  * paper has no counterpart for the transfer).  The copies run on a copy
  * stream of the context after the work enqueued so far on its stream; U
  * (n_out x k, row-major) and theta (k) are caller-owned host or device
- * memory, and for the copy to overlap anything host memory must be pinned
- * (cudaHostAlloc / cudaHostRegister).  n_out (required) receives the number
+ * memory.  Pinned host memory mapped into the device's address space
+ * (cudaHostAlloc, or cudaHostRegister with cudaHostRegisterMapped) is
+ * written by a kernel over the host link, leaving the copy engines to the
+ * next update's own small reads; other memory is copied with
+ * cudaMemcpyAsync (pageable host memory makes that copy wait on the host).  n_out (required) receives the number
  * of node ids now.  The outputs are complete after grest_wait_embedding (or
  * grest_destroy); until then the caller must not read or reuse them.  The
  * next update keeps the pairs being copied until the copy is done: its lift

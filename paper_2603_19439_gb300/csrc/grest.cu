@@ -1797,6 +1797,34 @@ grest_status grest_get_embedding(grest_ctx* c, double* U, double* theta, uint8_t
   return from_cuda(cudaStreamSynchronize(s));
 }
 
+}  // extern "C"
+
+namespace grest {
+// (X_K, Lambda_K) -> host memory mapped into the device's address space,
+// written by the SMs over the host link: the GPU's copy engines stay free for
+// the small reads the next update makes (a copy-engine transfer of U would
+// hold them, and each such read would wait behind it).  16-byte stores when
+// both sides allow them.
+__global__ void k_pairs_to_host(const double* __restrict__ U, int64_t ldu, int K, int64_t n,
+                                const double* __restrict__ theta, double* __restrict__ outU,
+                                double* __restrict__ outT) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  if (outT && tid < K) outT[tid] = theta[tid];
+  if (!outU) return;
+  const int64_t total = n * K;
+  if (ldu == K && ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(outU)) & 15) == 0) {
+    const double2* src = reinterpret_cast<const double2*>(U);
+    double2* dst = reinterpret_cast<double2*>(outU);
+    for (int64_t e = tid; e < total / 2; e += nth) dst[e] = src[e];
+    if ((total & 1) && tid == 0) outU[total - 1] = U[total - 1];
+  } else {
+    for (int64_t e = tid; e < total; e += nth) outU[e] = U[(e / K) * ldu + (e % K)];
+  }
+}
+}  // namespace grest
+
+extern "C" {
+
 grest_status grest_get_embedding_async(grest_ctx* c, double* U, double* theta, int64_t* n_out) {
   if (!c || !n_out) return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
@@ -1810,10 +1838,21 @@ grest_status grest_get_embedding_async(grest_ctx* c, double* U, double* theta, i
   cudaStream_t cs = c->cstream;
   CK(cudaEventRecord(c->ev_ready, c->stream));
   CK(cudaStreamWaitEvent(cs, c->ev_ready, 0));
-  if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, cudaMemcpyDefault, cs));
-  else if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K, n,
-                                   cudaMemcpyDefault, cs));
-  if (theta) CK(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->K, cudaMemcpyDefault, cs));
+  // pinned (mapped) host outputs: written by a kernel; anything else (device
+  // memory, pageable host memory): cudaMemcpyAsync on the copy stream
+  double *dU = nullptr, *dT = nullptr;
+  const bool mapped = (!U || cudaHostGetDevicePointer((void**)&dU, U, 0) == cudaSuccess) &&
+                      (!theta || cudaHostGetDevicePointer((void**)&dT, theta, 0) == cudaSuccess);
+  cudaGetLastError();  // a failed lookup only selects the copy path
+  if (mapped) {
+    grest::k_pairs_to_host<<<64, 256, 0, cs>>>(c->U, c->ldu, c->K, n, c->theta, dU, dT);
+    CK(cudaGetLastError());
+  } else {
+    if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, cudaMemcpyDefault, cs));
+    else if (U) CK(cudaMemcpy2DAsync(U, sizeof(double) * c->K, c->U, sizeof(double) * c->ldu, sizeof(double) * c->K,
+                                     n, cudaMemcpyDefault, cs));
+    if (theta) CK(cudaMemcpyAsync(theta, c->theta, sizeof(double) * c->K, cudaMemcpyDefault, cs));
+  }
   CK(cudaEventRecord(c->ev_copied, cs));
   c->copy_pending = true;
   return GREST_OK;

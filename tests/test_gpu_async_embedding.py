@@ -2,7 +2,8 @@
 pinned host memory while the next update runs gives, bit for bit, what the
 synchronous grest_get_embedding gives after that step, in the FP64 and the
 mixed path, including a step that grows the node capacity while a copy is
-still outstanding (the growth moves U, so it must wait for the copy)."""
+still outstanding (the growth moves U, so it must wait for the copy); pinned
+buffers take the kernel path, pageable ones the cudaMemcpyAsync path."""
 import numpy as np
 import pytest
 
@@ -23,8 +24,9 @@ def cuda():
     return torch
 
 
-@pytest.mark.parametrize("prec", [G.FP64, G.MIXED], ids=["fp64", "mixed"])
-def test_async_reads_equal_sync_reads(cuda, prec):
+@pytest.mark.parametrize("prec,pinned", [(G.FP64, True), (G.MIXED, True), (G.MIXED, False)],
+                         ids=["fp64-pinned", "mixed-pinned", "mixed-pageable"])
+def test_async_reads_equal_sync_reads(cuda, prec, pinned):
     torch = cuda
     K, steps = 6, 4
     g0, batches = wl.sbm_stream(n0=3000, steps=steps, n_new=150, n_rand=200)
@@ -41,8 +43,10 @@ def test_async_reads_equal_sync_reads(cuda, prec):
         U, th, _ = sync_tr.embedding()
         want.append((U, th))
     n_max = g0.n + sum(b.n_new for b in batches)
-    bufs = [(torch.empty((n_max, K), dtype=torch.float64).pin_memory(),
-             torch.empty(K, dtype=torch.float64).pin_memory()) for _ in batches]
+    def host(*shape):
+        t = torch.empty(shape, dtype=torch.float64)
+        return t.pin_memory() if pinned else t  # pinned: written by a kernel; pageable: cudaMemcpyAsync
+    bufs = [(host(n_max, K), host(K)) for _ in batches]
     rows = []
     for b, (Ub, tb) in zip(batches, bufs):
         async_tr.update(b)  # the previous read may still be in flight
