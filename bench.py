@@ -30,6 +30,7 @@ workloads (FP64, with the oracle timed beside them).
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -259,15 +260,52 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
-def roofline(prof_ms, prof_work, prof_bytes, prof_launch, traffic_file, precision="fp64"):
-    """Roofline of the dominant kernel class of the step (by device time).
+# Sources of each kernel kind (GREST_KIND_*): a traffic figure taken with ncu
+# counts only while these files are unchanged.
+KIND_SOURCES = {
+    "spmm_f32": ["paper_2603_19439_gb300/csrc/spmm.cu"],
+    "spmm_f64": ["paper_2603_19439_gb300/csrc/spmm.cu"],
+    "gram_tc": ["paper_2603_19439_gb300/csrc/tc_gram.cu", "paper_2603_19439_gb300/csrc/tc_util.cuh"],
+    "gram_narrow": ["paper_2603_19439_gb300/csrc/narrow_gram.cu"],
+    "gram_cuda": ["paper_2603_19439_gb300/csrc/dense.cu"],
+    "gemm_tc": ["paper_2603_19439_gb300/csrc/tc_gemm.cu", "paper_2603_19439_gb300/csrc/tc_util.cuh"],
+    "gemm_cuda": ["paper_2603_19439_gb300/csrc/dense.cu"],
+}
+KIND_CLASS = {"spmm_f32": 0, "spmm_f64": 0, "gram_tc": 1, "gram_narrow": 1, "gram_cuda": 1, "gemm_tc": 2,
+              "gemm_cuda": 2, "small": 3, "graph": 4}
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "traffic_grest_step_mixed_chung_lu_1M.md")
+
+
+def read_traffic(path, n_mean):
+    """DRAM bytes per launch per kernel kind from an ncu capture summary (its
+    table rows: | kind | launches per step | DRAM bytes per launch | mean node
+    ids | sources hash |), scaled from the captured steps' mean node count to
+    n_mean; a kind whose sources changed since the capture gets none."""
+    out = {}
+    try:
+        text = open(path).read()
+    except OSError:
+        return out
+    for m in re.finditer(r"^\| `?([a-z_0-9]+)`? \| ([0-9.]+) \| ([0-9.]+) \| ([0-9.]+) \| `?([0-9a-f]{16})`? \|$",
+                         text, re.M):
+        kind, _, per_launch, n_cap, h = m.groups()
+        if kind in KIND_SOURCES and source_hash(KIND_SOURCES[kind]) == h and n_mean:
+            out[kind] = float(per_launch) * n_mean / float(n_cap)
+    return out
+
+
+def roofline(prof_ms, prof_work, prof_bytes, prof_launch, kinds, n_mean, precision="fp64"):
+    """Roofline of the dominant kernel class of the step (by device time),
+    with every class and every kernel kind (GREST_KIND_*) listed beside it.
 
     SpMM, Gram and GEMM are HBM-bound in the mixed path (tensor cores keep the
     products at or below the ridge): achieved = compulsory bytes / time
-    against the measured copy bandwidth.  In the FP64 path the Gram and GEMM
-    are FP64-pipe bound (flops against the derived FP64 peak); the small dense
-    class is latency / ALU bound.  Every class is also listed under
-    "classes" with its own figure."""
+    against the measured copy bandwidth.  FP64 work (the FP64 path, and in the
+    mixed path the refinement's FP64 SpMM, Gram and lift) is FP64-pipe bound:
+    flops against the derived FP64 peak; the small dense class is latency /
+    ALU bound.  `traffic` (DRAM bytes per launch) comes from the ncu capture
+    summary in profiles/ for the kinds whose sources are unchanged; a class
+    gets it when every launch of the class is of such a kind."""
     from paper_2603_19439_gb300 import grest as G
     peaks = {}
     try:
@@ -276,43 +314,57 @@ def roofline(prof_ms, prof_work, prof_bytes, prof_launch, traffic_file, precisio
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s (of fallback)"
+    fp64 = (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)")
+    fp32 = (FP32_PEAK_TFLOPS, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (derived)")
 
-    def one(cls):
-        name = G.PROF_CLASSES[cls]
-        ms = float(prof_ms[cls])
+    def fig(bound, ms, work, byts, launches, alu=fp64):
         if ms <= 0:
             return None
-        if name in ("spmm", "graph") or (precision != "fp64" and name in ("gram", "gemm")):
-            return {"bound": "hbm", "unit": "GB/s", "achieved": prof_bytes[cls] / (ms * 1e-3) / 1e9, "peak": hbm,
-                    "peak_source": hbm_src}
-        if precision == "fp64" or name == "small":
-            peak, src = FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"
-            if precision == "mixed_fast":  # its projected problems run in FP32 arithmetic
-                peak, src = FP32_PEAK_TFLOPS, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz (derived)"
-            return {"bound": "alu", "unit": "TFLOP/s", "achieved": prof_work[cls] / (ms * 1e-3) / 1e12, "peak": peak,
-                    "peak_source": src}
-        return None
+        if bound == "hbm":
+            r = {"bound": "hbm", "unit": "GB/s", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm, "peak_source": hbm_src}
+        else:
+            r = {"bound": "alu", "unit": "TFLOP/s", "achieved": work / (ms * 1e-3) / 1e12, "peak": alu[0],
+                 "peak_source": alu[1]}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["ms_per_step"] = float(ms)
+        r["launches_per_step"] = float(launches)
+        return r
 
     classes = {}
     for c in range(5):
-        r = one(c)
+        name = G.PROF_CLASSES[c]
+        hbm_bound = name in ("spmm", "graph") or (precision != "fp64" and name in ("gram", "gemm"))
+        alu = fp32 if (precision == "mixed_fast" and name == "small") else fp64
+        r = fig("hbm" if hbm_bound else "alu", prof_ms[c], prof_work[c], prof_bytes[c], prof_launch[c], alu)
         if r:
-            r["frac"] = r["achieved"] / r["peak"]
-            r["ms_per_step"] = float(prof_ms[c])
-            r["launches_per_step"] = float(prof_launch[c])
-            classes[G.PROF_CLASSES[c]] = r
+            classes[name] = r
+    kms, kwork, kbytes, kn = kinds
+    fp64_kinds = {"spmm_f64", "gram_cuda", "gemm_cuda"}
+    kernels = {}
+    for i, name in enumerate(G.PROF_KINDS):
+        if name in ("small", "graph", "double_float"):
+            continue
+        r = fig("alu" if name in fp64_kinds else "hbm", kms[i], kwork[i], kbytes[i], kn[i])
+        if r:
+            r["kernels"] = G.PROF_KIND_KERNELS[i]
+            kernels[name] = r
+    traffic = read_traffic(TRAFFIC_PROFILE, n_mean)
+    for name, r in kernels.items():
+        r["traffic"] = traffic.get(name)
+    for cname, r in classes.items():
+        c = G.PROF_CLASSES.index(cname)
+        ks = [k for k, cc in KIND_CLASS.items() if cc == c and k in kernels]
+        covered = sum(kernels[k]["launches_per_step"] for k in ks)
+        r["traffic"] = None
+        if ks and abs(covered - r["launches_per_step"]) < 0.5 and all(kernels[k]["traffic"] is not None for k in ks):
+            r["traffic"] = sum(kernels[k]["traffic"] * kernels[k]["launches_per_step"] for k in ks) / covered
     cls = int(np.argmax(prof_ms))
     name = G.PROF_CLASSES[cls]
     out = dict(classes.get(name, {}))
-    traffic = None
-    try:
-        t = json.load(open(traffic_file))
-        entry = t.get(name)
-        if entry and entry.get("source_hash") == source_hash(entry.get("sources", [])):
-            traffic = entry["bytes_per_launch"]
-    except (OSError, ValueError):
-        pass
-    out.update({"kernel_class": name, "traffic": traffic, "classes": classes})
+    out.update({"kernel_class": name, "traffic": classes.get(name, {}).get("traffic"), "classes": classes,
+                "kernels": kernels,
+                "traffic_source": "profiles/traffic_grest_step_mixed_chung_lu_1M.md (ncu DRAM bytes per launch, "
+                                  "scaled to this run's mean node count; null where the kernel changed since)"})
     return out
 
 
@@ -466,7 +518,8 @@ def run_grest(args):
         for b in dev[:W]:
             tr.update(b, on_device=True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        prof = {"ms": np.zeros(5), "work": np.zeros(5), "bytes": np.zeros(5), "n": np.zeros(5), "launches": 0}
+        prof = {"ms": np.zeros(5), "work": np.zeros(5), "bytes": np.zeros(5), "n": np.zeros(5), "launches": 0,
+                "kms": np.zeros(10), "kwork": np.zeros(10), "kbytes": np.zeros(10), "kn": np.zeros(10), "nodes": 0.0}
         clocks = ClockSampler(bus)
         clocks.start()
         barrier()
@@ -483,6 +536,11 @@ def run_grest(args):
             prof["bytes"] += s["prof_bytes"]
             prof["n"] += s["prof_launches"]
             prof["launches"] += s["kernel_launches"]
+            prof["kms"] += s["prof_kind_ms"]
+            prof["kwork"] += s["prof_kind_work"]
+            prof["kbytes"] += s["prof_kind_bytes"]
+            prof["kn"] += s["prof_kind_launches"]
+            prof["nodes"] += s["n_nodes"]
             last = s
         e1.record(stream)
         barrier()
@@ -564,7 +622,9 @@ def run_grest(args):
                                                         "pivot_kept_min", "boundary_gap", "ms_refine")},
                 "accuracy": accuracy(r),
                 "roofline": roofline(r["prof"]["ms"] / steps, r["prof"]["work"] / steps, r["prof"]["bytes"] / steps,
-                                     r["prof"]["n"] / steps, os.path.join(ROOT, "profiles", "traffic.json"), p),
+                                     r["prof"]["n"] / steps,
+                                     tuple(r["prof"][k] / steps for k in ("kms", "kwork", "kbytes", "kn")),
+                                     r["prof"]["nodes"] / steps, p),
                 "clocks": r["clk"]}
 
     main = results[headline]

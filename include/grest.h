@@ -158,6 +158,22 @@ typedef struct {
   int32_t on_device;
 } grest_update;
 
+/* Kernel kinds of GREST_FLAG_PROFILE (grest_stats.prof_kind_*): each timed
+ * launch group of a step is one of these. */
+enum {
+  GREST_KIND_SPMM_F32 = 0,     /* k_spmm_rows / k_spmm_long on FP32 blocks (mixed path)        */
+  GREST_KIND_SPMM_F64 = 1,     /* the same on FP64 blocks (FP64 path, mixed refinement)         */
+  GREST_KIND_GRAM_TC = 2,      /* k_gram_tc (+ its reduce): tcgen05 3xTF32 Gram                  */
+  GREST_KIND_GRAM_NARROW = 3,  /* k_gram_narrow (+ reduce): FP32 Gram with a side <= 32         */
+  GREST_KIND_GRAM_CUDA = 4,    /* CUDA-core Grams: FP64 split-K, the refinement's pair Gram   */
+  GREST_KIND_GEMM_TC = 5,      /* k_gemm_tc (+ k_gemm_prep): tcgen05 3xTF32 block update        */
+  GREST_KIND_GEMM_CUDA = 6,    /* CUDA-core block updates (FP64, FP32 fallback)                 */
+  GREST_KIND_DOUBLE_FLOAT = 7, /* GREST_MIXED_FAST refinement kernels (double-float)           */
+  GREST_KIND_SMALL = 8,        /* small dense: pivoted Cholesky, eigensolver (several kernels) */
+  GREST_KIND_GRAPH = 9,        /* graph update (several kernels)                              */
+  GREST_KIND_COUNT = 10
+};
+
 /* Per-step diagnostics (filled by grest_apply_update / grest_get_stats). */
 typedef struct {
   int64_t step;            /* updates applied so far                                   */
@@ -187,6 +203,13 @@ typedef struct {
   /* GREST_FLAG_PROFILE: compulsory HBM bytes per class (each operand block read
    * once, each output written once; SpMM as in prof_work). */
   double prof_bytes[5];
+  /* GREST_FLAG_PROFILE: the same figures per kernel kind (GREST_KIND_*), so
+   * that the classes that mix kernels (the Gram class holds the tensor-core,
+   * the narrow and the CUDA-core Grams) can be told apart. */
+  double prof_kind_ms[GREST_KIND_COUNT];
+  double prof_kind_work[GREST_KIND_COUNT];
+  double prof_kind_bytes[GREST_KIND_COUNT];
+  int64_t prof_kind_launches[GREST_KIND_COUNT];
 } grest_stats;
 
 /* Fill *cfg with defaults for k tracked pairs: ADJ, AUTO, L = P = 100

@@ -142,6 +142,7 @@ struct grest_ctx {
   cudaEvent_t pev[kProfEvents];
   int prof_n = 0;
   int prof_cls[kProfEvents / 2];
+  int prof_kind[kProfEvents / 2];  // GREST_KIND_*, or -1
   double prof_work[kProfEvents / 2];
   double prof_bytes[kProfEvents / 2];
   bool profiling() const { return (cfg.flags & GREST_FLAG_PROFILE) != 0; }
@@ -434,10 +435,11 @@ int prof_begin(grest_ctx* c) {
   return i;
 }
 
-void prof_end(grest_ctx* c, int i, int cls, double work, double bytes = 0.0) {
+void prof_end(grest_ctx* c, int i, int cls, double work, double bytes = 0.0, int kind = -1) {
   if (i < 0) return;
   cudaEventRecord(c->pev[i + 1], c->stream);
   c->prof_cls[i / 2] = cls;
+  c->prof_kind[i / 2] = kind >= 0 ? kind : (cls == 3 ? GREST_KIND_SMALL : cls == 4 ? GREST_KIND_GRAPH : -1);
   c->prof_work[i / 2] = work;
   c->prof_bytes[i / 2] = bytes;
 }
@@ -449,6 +451,12 @@ void prof_collect(grest_ctx* c, grest_stats& st) {
     st.prof_bytes[k] = 0.0;
     st.prof_launches[k] = 0;
   }
+  for (int k = 0; k < GREST_KIND_COUNT; ++k) {
+    st.prof_kind_ms[k] = 0.0;
+    st.prof_kind_work[k] = 0.0;
+    st.prof_kind_bytes[k] = 0.0;
+    st.prof_kind_launches[k] = 0;
+  }
   for (int i = 0; i + 1 < c->prof_n; i += 2) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->pev[i], c->pev[i + 1]);
@@ -457,6 +465,13 @@ void prof_collect(grest_ctx* c, grest_stats& st) {
     st.prof_work[k] += c->prof_work[i / 2];
     st.prof_bytes[k] += c->prof_bytes[i / 2];
     st.prof_launches[k] += 1;
+    const int kd = c->prof_kind[i / 2];
+    if (kd >= 0 && kd < GREST_KIND_COUNT) {
+      st.prof_kind_ms[kd] += ms;
+      st.prof_kind_work[kd] += c->prof_work[i / 2];
+      st.prof_kind_bytes[kd] += c->prof_bytes[i / 2];
+      st.prof_kind_launches[kd] += 1;
+    }
   }
   c->prof_n = 0;
 }
@@ -475,34 +490,34 @@ OpParams op_params(const grest_ctx* c) {
 // nnz_proc: entries of the processed rows that take part (all of them, or the
 // new-node block); x_rows: rows of X read at least once
 void prof_spmm(grest_ctx* c, int p, int w, int64_t r0, int64_t r1, int64_t col_lo, int64_t nnz_proc, int64_t x_rows,
-               double xbytes, double ybytes) {
+               double xbytes, double ybytes, int kind) {
   if (r1 > r0 && w > 0) c->launches += col_lo == 0 ? 2 : 1;
   if (nnz_proc < 0) nnz_proc = c->nnz;
   if (x_rows < 0) x_rows = r1 - r0;
   const double eb = c->g.val ? 12.0 : 4.0;
   const double by = 12.0 * (r1 - r0) + eb * nnz_proc + w * (ybytes * (r1 - r0) + xbytes * x_rows);
-  prof_end(c, p, 0, by, by);
+  prof_end(c, p, 0, by, by, kind);
 }
 
 void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
           int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
   int p = prof_begin(c);
   spmm_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
-  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 8.0, 8.0);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 8.0, 8.0, GREST_KIND_SPMM_F64);
 }
 
 void spmm(grest_ctx* c, const float* X, int64_t ldx, float* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
           int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
   int p = prof_begin(c);
   spmm_f32(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
-  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 4.0);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 4.0, GREST_KIND_SPMM_F32);
 }
 
 void spmm(grest_ctx* c, const float* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
           int64_t col_lo, int64_t nnz_proc = -1, int64_t x_rows = -1) {
   int p = prof_begin(c);
   spmm_f32_f64(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, X, ldx, Y, ldy, w, r0, r1, col_lo, c->stream);
-  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 8.0);
+  prof_spmm(c, p, w, r0, r1, col_lo, nnz_proc, x_rows, 4.0, 8.0, GREST_KIND_SPMM_F32);
 }
 
 // Y = Delta X (Sec. 3.3 block, Eq. main3) for the batch just applied
@@ -519,26 +534,32 @@ void gram(grest_ctx* c, const double* X, int64_t ldx, int a, const double* Y, in
   int p = prof_begin(c);
   gram_f64(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
-  prof_end(c, p, 1, 2.0 * n * a * b, 8.0 * n * (X == Y && a == b ? a : a + b));
+  prof_end(c, p, 1, 2.0 * n * a * b, 8.0 * n * (X == Y && a == b ? a : a + b), GREST_KIND_GRAM_CUDA);
 }
 
 // FP32 Gram of the mixed path: a narrow side (the projections X_bar^T Y, K
 // columns) on the CUDA cores, wider products on the tensor cores; false when
 // neither kernel takes the shape or alignment
-bool gram_f32_fast(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
-                   int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s) {
-  if (n <= 0) return false;
-  if (std::min(a, b) <= 32 && gram_f32_narrow(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0) return true;
-  return gram_tc_supported(X, ldx, a, Y, ldy, b) && gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0;
+int gram_f32_fast(const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
+                  int64_t ldc, double* part, int64_t part_cap, int32_t* err, cudaStream_t s) {
+  if (n <= 0) return -1;
+  if (std::min(a, b) <= 32 && gram_f32_narrow(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0)
+    return GREST_KIND_GRAM_NARROW;
+  if (gram_tc_supported(X, ldx, a, Y, ldy, b) && gram_f32_tc(X, ldx, a, Y, ldy, b, n, C, ldc, part, part_cap, err, s) == 0)
+    return GREST_KIND_GRAM_TC;
+  return -1;
 }
 
 void gram(grest_ctx* c, const float* X, int64_t ldx, int a, const float* Y, int64_t ldy, int b, int64_t n, double* C,
           int64_t ldc, bool sym) {
   int p = prof_begin(c);
-  const bool done = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream);
-  if (!done) gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+  int kind = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream);
+  if (kind < 0) {
+    gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, sym, c->stream);
+    kind = GREST_KIND_GRAM_CUDA;
+  }
   if (a > 0 && b > 0 && n > 0) c->launches += 2;
-  prof_end(c, p, 1, 2.0 * n * a * b, 4.0 * n * (X == Y && a == b ? a : a + b));
+  prof_end(c, p, 1, 2.0 * n * a * b, 4.0 * n * (X == Y && a == b ? a : a + b), kind);
 }
 
 void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X, int64_t ldx, const double* B,
@@ -546,20 +567,22 @@ void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const double* X,
   int p = prof_begin(c);
   gemm_nn_f64(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
   if (n > 0 && cc > 0) c->launches += 1;
-  prof_end(c, p, 2, 2.0 * n * a * cc, 8.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)));
+  prof_end(c, p, 2, 2.0 * n * a * cc, 8.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)), GREST_KIND_GEMM_CUDA);
 }
 
 void gemm(grest_ctx* c, int64_t n, int a, int cc, double alpha, const float* X, int64_t ldx, const double* B,
           int64_t ldb, double beta, const float* Cin, int64_t ldc, float* Out, int64_t ldo) {
   int p = prof_begin(c);
+  int kind = GREST_KIND_GEMM_CUDA;
   if (n > 0 && cc > 0 && gemm_f32_tc(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->gemm_img,
                                      c->gemm_img_cap, c->err, c->stream) == 0) {
     c->launches += 2;
+    kind = GREST_KIND_GEMM_TC;
   } else {
     gemm_nn_f32(n, a, cc, alpha, X, ldx, B, ldb, beta, Cin, ldc, Out, ldo, c->stream);
     if (n > 0 && cc > 0) c->launches += 1;
   }
-  prof_end(c, p, 2, 2.0 * n * a * cc, 4.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)));
+  prof_end(c, p, 2, 2.0 * n * a * cc, 4.0 * n * (a + cc * (beta != 0.0 ? 2 : 1)), kind);
 }
 
 // f32: the projected problem's entries come from FP32 blocks (mixed path), so
@@ -780,17 +803,17 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   float* MUl = MUh + (size_t)c->g.n_cap * c->ldu;
   int p = prof_begin(c);
   c->launches += gram_df(c->U32, c->ldu, c->U32, nullptr, c->ldu, K, N2, c->G, K, c->part, c->part_cap, s);
-  prof_end(c, p, 1, 2.0 * N2 * K * K, 4.0 * N2 * K);
+  prof_end(c, p, 1, 2.0 * N2 * K * K, 4.0 * N2 * K, GREST_KIND_DOUBLE_FLOAT);
   p = prof_begin(c);
   c->launches += spmm_df(c->g, op_params(c), c->gw.long_rows, c->gw.scalars + 1, c->U32, c->ldu, MUh, MUl, c->ldu,
                          K, N2, s);
   {
     const double by = 12.0 * N2 + (c->g.val ? 12.0 : 4.0) * c->nnz + K * (8.0 * N2 + 4.0 * N2);
-    prof_end(c, p, 0, by, by);
+    prof_end(c, p, 0, by, by, GREST_KIND_DOUBLE_FLOAT);
   }
   p = prof_begin(c);
   c->launches += gram_df(c->U32, c->ldu, MUh, MUl, c->ldu, K, N2, c->H, K, c->part, c->part_cap, s);
-  prof_end(c, p, 1, 2.0 * N2 * K * K, 12.0 * N2 * K);
+  prof_end(c, p, 1, 2.0 * N2 * K * K, 12.0 * N2 * K, GREST_KIND_DOUBLE_FLOAT);
   p = prof_begin(c);
   {  // the K x K problems of the refinement fit one CTA (K <= 64)
     int nl = pchol_small_f64(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
@@ -813,7 +836,7 @@ grest_status refine_mixed(grest_ctx* c, int64_t N2) {
   p = prof_begin(c);
   c->launches += lift_df(c->U32, c->ldu, c->Gs, K, N2, c->U, c->ldu, s);
   c->launches += sign_normalize_fast(c->U, c->ldu, K, N2, c->part, c->ipart, s);
-  prof_end(c, p, 2, 2.0 * N2 * K * K, 4.0 * N2 * K + 8.0 * N2 * K * 3);
+  prof_end(c, p, 2, 2.0 * N2 * K * K, 4.0 * N2 * K + 8.0 * N2 * K * 3, GREST_KIND_DOUBLE_FLOAT);
   CK(cudaMemcpyAsync(c->theta, c->th_new, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
   return GREST_OK;
 }
@@ -840,7 +863,7 @@ grest_status refine_mixed_f64(grest_ctx* c, int64_t N2) {
   const int nl = gram_pair_sym_f64(X64, MU, ldu, K, N2, c->G, c->H, c->part, c->part_cap, s);
   if (nl < 0) return GREST_ERR_CAPACITY;
   c->launches += nl;
-  prof_end(c, p, 1, 2.0 * N2 * K * (K + 1), 16.0 * N2 * K);
+  prof_end(c, p, 1, 2.0 * N2 * K * (K + 1), 16.0 * N2 * K, GREST_KIND_GRAM_CUDA);
   p = prof_begin(c);
   {  // the K x K problems of the refinement fit one CTA (K <= 64)
     int nl = pchol_small_f64(c->G, K, K, 1e-14, 0.0, nullptr, c->T, K, c->info + 44, s);
@@ -2172,7 +2195,7 @@ grest_status grest_gram_f32(grest_ctx* c, const float* X, int64_t ldx, int32_t a
     return GREST_ERR_INVALID_ARG;
   if (cudaSetDevice(c->dev) != cudaSuccess) return GREST_ERR_CUDA;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int32_t), c->stream));
-  const bool done = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream);
+  const bool done = gram_f32_fast(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, c->part_cap, c->err, c->stream) >= 0;
   if (!done) {
     if (gram_parts(n, a, b) * (int64_t)a * b > c->part_cap) return GREST_ERR_CAPACITY;
     gram_f32(X, ldx, a, Y, ldy, b, n, C, ldc, c->part, false, c->stream);

@@ -24,6 +24,11 @@ FLAG_CHECK = 1
 FLAG_PROFILE = 2
 FLAG_TWO_STREAMS = 4
 PROF_CLASSES = ("spmm", "gram", "gemm", "small", "graph")
+PROF_KINDS = ("spmm_f32", "spmm_f64", "gram_tc", "gram_narrow", "gram_cuda", "gemm_tc", "gemm_cuda", "double_float",
+              "small", "graph")
+PROF_KIND_KERNELS = ("k_spmm_rows<float> + k_spmm_long<float>", "k_spmm_rows<double> + k_spmm_long<double>",
+                     "k_gram_tc", "k_gram_narrow", "k_gram_part / k_gram_pair_upper", "k_gemm_tc", "k_gemm_nn",
+                     "k_spmm_df / k_gram_df / k_lift_df", "small dense group", "graph update group")
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid update batch", 3: "device out of memory",
           4: "capacity exceeded", 5: "numerical breakdown", 6: "CUDA error", 7: "device wait timed out",
@@ -57,7 +62,9 @@ class Stats(C.Structure):
                 ("ms_total", C.c_float), ("ms_graph", C.c_float), ("ms_spmm", C.c_float), ("ms_basis", C.c_float),
                 ("ms_project", C.c_float), ("ms_eig", C.c_float), ("ms_lift", C.c_float), ("ms_refine", C.c_float),
                 ("prof_ms", C.c_double * 5), ("prof_work", C.c_double * 5), ("prof_launches", C.c_int64 * 5),
-                ("kernel_launches", C.c_int64), ("prof_bytes", C.c_double * 5)]
+                ("kernel_launches", C.c_int64), ("prof_bytes", C.c_double * 5),
+                ("prof_kind_ms", C.c_double * 10), ("prof_kind_work", C.c_double * 10),
+                ("prof_kind_bytes", C.c_double * 10), ("prof_kind_launches", C.c_int64 * 10)]
 
     def as_dict(self):
         out = {}

@@ -102,3 +102,38 @@ def test_reference_arm_other_ranks_exit_quietly():
                        env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+
+
+def test_roofline_traffic_per_kind_and_class(tmp_path, monkeypatch):
+    """Traffic from an ncu summary: scaled by the node count, dropped for a
+    kind whose sources changed since the capture, and combined into a class
+    figure only when every launch of the class is of a kind with a figure."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    h = {k: bench.source_hash(v) for k, v in bench.KIND_SOURCES.items()}
+    prof = tmp_path / "traffic.md"
+    prof.write_text("\n".join([
+        "| kind | launches per step | DRAM bytes per launch | mean node ids | sources hash |",
+        "|---|---|---|---|---|",
+        f"| `gram_tc` | 6 | 1000000 | 500000 | `{h['gram_tc']}` |",
+        f"| `gram_narrow` | 7 | 200000 | 500000 | `{h['gram_narrow']}` |",
+        f"| `gram_cuda` | 1 | 300000 | 500000 | `{h['gram_cuda']}` |",
+        "| `gemm_tc` | 13 | 900000 | 500000 | `0123456789abcdef` |",  # stale: sources changed
+    ]) + "\n")
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(prof))
+    ms = np.array([7.0, 9.0, 7.0, 7.5, 1.0])
+    work = np.full(5, 1e9)
+    byts = np.full(5, 5e9)
+    launches = np.array([5.0, 14.0, 16.0, 8.0, 1.0])
+    kms = np.array([5.0, 2.0, 4.6, 1.9, 2.5, 4.5, 1.8, 0.0, 7.5, 1.0])
+    kn = np.array([4.0, 1.0, 6.0, 7.0, 1.0, 13.0, 1.0, 0.0, 8.0, 1.0])
+    r = bench.roofline(ms, work, byts, launches, (kms, np.full(10, 1e9), np.full(10, 1e9), kn), 1_000_000, "mixed")
+    assert r["kernel_class"] == "gram"
+    k = r["kernels"]
+    assert k["gram_tc"]["traffic"] == 2_000_000 and k["gram_narrow"]["traffic"] == 400_000
+    assert k["gemm_tc"]["traffic"] is None and k["spmm_f32"]["traffic"] is None
+    assert k["gram_cuda"]["bound"] == "alu" and k["gram_tc"]["bound"] == "hbm"
+    # the Gram class: 6 + 7 + 1 = 14 launches, all with a figure
+    assert r["traffic"] == (6 * 2_000_000 + 7 * 400_000 + 1 * 600_000) / 14
+    assert r["classes"]["gemm"]["traffic"] is None  # gemm_tc's figure is stale

@@ -51,7 +51,27 @@ def test_struct_sizes_match_header():
     # int32 x 9, pad, uint64, double, int64 x 3
     assert ctypes.sizeof(grest.Config) == 40 + 8 + 8 + 24
     assert ctypes.sizeof(grest.Update) == 8 * 10 + 8
-    assert ctypes.sizeof(grest.Stats) == 24 + 24 + 48 + 32 + 3 * 40 + 8 + 40
+    # ..., prof_* per class (5), kernel_launches, prof_bytes, prof_kind_* (10 kinds x 4)
+    assert ctypes.sizeof(grest.Stats) == 24 + 24 + 48 + 32 + 3 * 40 + 8 + 40 + 4 * 80
+
+
+def test_struct_sizes_match_a_c_compiler(tmp_path):
+    """The ctypes layouts against sizeof() from a C compiler reading the header."""
+    import shutil
+    import subprocess
+    from paper_2603_19439_gb300 import grest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "grest.h"\n'
+                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(grest_config), sizeof(grest_update), '
+                   'sizeof(grest_stats)); return 0; }\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert [int(x) for x in out] == [ctypes.sizeof(grest.Config), ctypes.sizeof(grest.Update),
+                                     ctypes.sizeof(grest.Stats)]
 
 
 def test_init_rejects_bad_arguments_without_gpu(lib):
