@@ -194,14 +194,15 @@ typedef struct {
   float ms_total, ms_graph, ms_spmm, ms_basis, ms_project, ms_eig, ms_lift, ms_refine;
   /* GREST_FLAG_PROFILE: summed device time and algorithmic work per kernel class
    * (index 0 SpMM, 1 Gram X^T Y, 2 tall-skinny GEMM X B, 3 small dense: Cholesky,
-   * eigensolver; 4 graph update).  Work is bytes for SpMM (row pointers, column
-   * indices, one read of X and one write of Y) and flops for the dense classes. */
+   * eigensolver; 4 graph update).  Work is flops: 2 per nonzero and column
+   * for SpMM, the products' flops for the dense classes. */
   double prof_ms[5];
   double prof_work[5];
   int64_t prof_launches[5];
   int64_t kernel_launches; /* kernels this library enqueued during the step       */
   /* GREST_FLAG_PROFILE: compulsory HBM bytes per class (each operand block read
-   * once, each output written once; SpMM as in prof_work). */
+   * once, each output written once; SpMM: row pointers, column indices,
+   * one read of X and one write of Y). */
   double prof_bytes[5];
   /* GREST_FLAG_PROFILE: the same figures per kernel kind (GREST_KIND_*), so
    * that the classes that mix kernels (the Gram class holds the tensor-core,

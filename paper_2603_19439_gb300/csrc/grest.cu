@@ -496,7 +496,7 @@ void prof_spmm(grest_ctx* c, int p, int w, int64_t r0, int64_t r1, int64_t col_l
   if (x_rows < 0) x_rows = r1 - r0;
   const double eb = c->g.val ? 12.0 : 4.0;
   const double by = 12.0 * (r1 - r0) + eb * nnz_proc + w * (ybytes * (r1 - r0) + xbytes * x_rows);
-  prof_end(c, p, 0, by, by, kind);
+  prof_end(c, p, 0, 2.0 * nnz_proc * w, by, kind);  // work: a multiply-add per nonzero and column
 }
 
 void spmm(grest_ctx* c, const double* X, int64_t ldx, double* Y, int64_t ldy, int w, int64_t r0, int64_t r1,
