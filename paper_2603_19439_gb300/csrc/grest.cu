@@ -904,11 +904,13 @@ grest_status rsvd_sketch(grest_ctx* c, int64_t N, int64_t N2, int64_t S, int* rY
   T* Yr2 = Yr2p<T>(c);
   T* Om = Omp<T>(c);
   T* EtM = EtMp<T>(c);
-  // S.1: Y = P_perp Delta_2 Omega
+  // S.1: Y = P_perp Delta_2 Omega, one projection as in S.1: the basis only
+  // enters S.2 through Delta_2^T P_perp M (the formula below applies P_perp
+  // itself) and A6 projects the block R = M U_hat again, so rounding left
+  // along X_bar here does not reach the result
   gaussian_omega(Om, ldq, S, q, c->cfg.seed, (uint64_t)c->step, c->stream);
   c->launches += 1;
   spmm(c, Om, ldq, Yr, ldq, q, 0, N2, N, c->batch_new_edges + S, S);
-  project_out(c, Yr, ldq, q, N2);
   project_out(c, Yr, ldq, q, N2);
   // M = orth(Y): CholQR2 with pivoting
   int rY = 0;

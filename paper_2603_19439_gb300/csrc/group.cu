@@ -305,10 +305,8 @@ int enqueue_step(grest_group* G, cudaStream_t s) {
   // RSVD new-node block (graphs in mode 4)
   n += launch_omega(P, ls, s);
   n += launch_spmm(SP_OM, P, ls, s);
-  for (int t = 0; t < 2; ++t) {
-    n += launch_gram(GR_PY, P, s);
-    n += launch_gemm(GM_PY, P, ls, s);
-  }
+  n += launch_gram(GR_PY, P, s);  // one projection, as in the single-graph update
+  n += launch_gemm(GM_PY, P, ls, s);
   n += launch_gram(GR_GY, P, s);
   n += launch_pchol(PC_Y1, P, s);
   n += launch_gemm(GM_QY, P, ls, s);
