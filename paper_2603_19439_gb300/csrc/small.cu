@@ -177,6 +177,20 @@ __global__ void __launch_bounds__(kClThreads) k_tridiag_cl(double* H, int64_t ld
 // which cannot win a pivot search, map to -1).
 __device__ __forceinline__ long long pivot_key(double x) { return x >= 0.0 ? __double_as_longlong(x) : -1ll; }
 
+// Warp-wide (key, index) argmax, largest key and the lowest index among the
+// lanes that hold it, in every lane: three redux.sync steps on the key's two
+// halves and the index (exact, the same result as a shuffle tree).  Keys are
+// >= -2 (no candidate: -2).
+__device__ __forceinline__ void warp_argmax_key(long long& bk, int& bi) {
+  const unsigned long long u = (unsigned long long)(bk + 2);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const unsigned midx = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? (unsigned)bi : 0xffffffffu);
+  bk = (long long)(((unsigned long long)mhi << 32) | mlo) - 2;
+  bi = (int)midx;
+}
+
 // --- Cholesky with diagonal pivoting of the Gram matrix G (c x c, upper
 // triangle read), rows cyclic over the cluster.  Pivot k is the largest
 // remaining Schur-complement diagonal (lowest index on ties); factorization
@@ -230,12 +244,7 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
           if (key > bk || (key == bk && i < bi)) { bk = key; bi = i; }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
-      }
+      warp_argmax_key(bk, bi);
       if (lane == 0) {
         slot_key[k & 1] = bk;
         slot_idx[k & 1] = bi;
@@ -249,12 +258,7 @@ __global__ void __launch_bounds__(kClThreads) k_pchol_cl(double* G, int64_t ld, 
         bk = cl.map_shared_rank(slot_key, lane)[k & 1];
         bi = cl.map_shared_rank(slot_idx, lane)[k & 1];
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ok > bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
-      }
+      warp_argmax_key(bk, bi);
       if (lane == 0) {
         const double v = bk >= 0 ? __longlong_as_double(bk) : -1.0;  // exact value of the pivot
         if (k == 0) {
