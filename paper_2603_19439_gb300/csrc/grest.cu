@@ -1840,7 +1840,17 @@ __global__ void k_pairs_to_host(const double* __restrict__ U, int64_t ldu, int K
   if (ldu == K && ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(outU)) & 15) == 0) {
     const double2* src = reinterpret_cast<const double2*>(U);
     double2* dst = reinterpret_cast<double2*>(outU);
-    for (int64_t e = tid; e < total / 2; e += nth) dst[e] = src[e];
+    const int64_t m = total / 2;
+    int64_t e = tid;
+    // four 16-byte loads in flight per thread before their stores
+    for (; e + 3 * nth < m; e += 4 * nth) {
+      const double2 a = src[e], b = src[e + nth], c = src[e + 2 * nth], d = src[e + 3 * nth];
+      dst[e] = a;
+      dst[e + nth] = b;
+      dst[e + 2 * nth] = c;
+      dst[e + 3 * nth] = d;
+    }
+    for (; e < m; e += nth) dst[e] = src[e];
     if ((total & 1) && tid == 0) outU[total - 1] = U[total - 1];
   } else {
     for (int64_t e = tid; e < total; e += nth) outU[e] = U[(e / K) * ldu + (e % K)];
@@ -1870,7 +1880,7 @@ grest_status grest_get_embedding_async(grest_ctx* c, double* U, double* theta, i
                       (!theta || cudaHostGetDevicePointer((void**)&dT, theta, 0) == cudaSuccess);
   cudaGetLastError();  // a failed lookup only selects the copy path
   if (mapped) {
-    grest::k_pairs_to_host<<<64, 256, 0, cs>>>(c->U, c->ldu, c->K, n, c->theta, dU, dT);
+    grest::k_pairs_to_host<<<304, 256, 0, cs>>>(c->U, c->ldu, c->K, n, c->theta, dU, dT);
     CK(cudaGetLastError());
   } else {
     if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, cudaMemcpyDefault, cs));
