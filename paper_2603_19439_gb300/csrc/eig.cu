@@ -551,13 +551,22 @@ __global__ void __launch_bounds__(32) k_invit(int m, int k, double* work, int mm
 // twice, in ascending order; all projections of one vector run in parallel
 // (one warp per earlier cluster member), so a cluster of c vectors costs
 // O(c) block synchronizations instead of O(c^2).
-template <typename T>
-__global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work, int mmax, double* F,
-                                                      int64_t ldf) {
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work, int mmax, double* Fg,
+                                                      int64_t ldg) {
   __shared__ T dots[kMaxK];
   __shared__ T red[32];
+  extern __shared__ __align__(16) double co_sm[];
   EigWork L = eig_layout(work, mmax);
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  // the k vectors (m x k) in shared memory when they fit: every dot product
+  // and update below then runs on shared memory instead of global loads
+  double* F = SMEM ? co_sm : Fg;
+  const int64_t ldf = SMEM ? k : ldg;
+  if (SMEM) {
+    for (int e = tid; e < m * k; e += nth) co_sm[e] = Fg[(int64_t)(e / k) * ldg + (e % k)];
+    __syncthreads();
+  }
   for (int a = 1; a < k; ++a) {
     const int ta = L.sel[a];
     const int b0 = L.cl0[a];
@@ -582,40 +591,69 @@ __global__ void __launch_bounds__(256) k_cluster_orth(int m, int k, double* work
     T s2 = 0;
     for (int i = tid; i < m; i += nth) s2 = fma((T)F[(int64_t)i * ldf + ta], (T)F[(int64_t)i * ldf + ta], s2);
     s2 = block_sum(s2, red);
-    const T inv = s2 > T(0) ? T(1) / sqrt(s2) : T(0);
+    T inv = 0;
+    if (s2 > T(0)) {
+      if constexpr (sizeof(T) == sizeof(double)) inv = rsqrt(s2);
+      else inv = T(1) / sqrt(s2);
+    }
     for (int i = tid; i < m; i += nth) F[(int64_t)i * ldf + ta] = (double)((T)F[(int64_t)i * ldf + ta] * inv);
     __syncthreads();
   }
+  if (SMEM)
+    for (int e = tid; e < m * k; e += nth) Fg[(int64_t)(e / k) * ldg + (e % k)] = co_sm[e];
 }
 
 // --- 5. F = Q Y, Q = P_0 P_1 ... P_{m-3}; one warp per selected vector, four
 // warps per block (one per SM sub-partition).
 constexpr int kBtWarps = 4;
 
-template <typename T>
+// Row j of the packed reflector block starts at off(j) = j (2m - j - 1) / 2
+// (row r holds the m - r - 1 entries right of the diagonal).
+__device__ __forceinline__ int64_t refl_off(int m, int j) { return (int64_t)j * (2 * m - j - 1) / 2; }
+inline int64_t refl_off_host(int m, int j) { return (int64_t)j * (2 * m - j - 1) / 2; }
+
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(kBtWarps * 32) k_backtransform(const double* H, int64_t ld, int m, int k,
                                                                 double* work, int mmax, double* F, int64_t ldf) {
-  extern __shared__ __align__(16) unsigned char bt_raw[];  // kBtWarps x m
+  extern __shared__ __align__(16) unsigned char bt_raw[];  // kBtWarps x m, then (SMEM) the packed reflectors
   EigWork L = eig_layout(work, mmax);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int t = blockIdx.x * kBtWarps + wid;
+  constexpr bool F32 = sizeof(T) == 4;
+  T* vs = reinterpret_cast<T*>(bt_raw) + kBtWarps * m;
+  if (SMEM) {
+    // every reflector once into shared memory (independent loads, all in
+    // flight together), so the serial chain below waits on no global load
+    const int64_t total = refl_off(m, m - 1);
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+      const float q = (float)(2 * m - 1);
+      int j = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)e, 0.f))) * 0.5f);
+      j = j < 0 ? 0 : (j > m - 2 ? m - 2 : j);
+      while (j > 0 && refl_off(m, j) > e) --j;
+      while (j < m - 2 && refl_off(m, j + 1) <= e) ++j;
+      const int i = (int)(e - refl_off(m, j));
+      vs[e] = F32 ? (T)L.vf[(size_t)j * m + j + 1 + i] : (T)H[(int64_t)j * ld + j + 1 + i];
+    }
+    __syncthreads();
+  }
   if (t >= k) return;
   T* x = reinterpret_cast<T*>(bt_raw) + wid * m;
   for (int i = lane; i < m; i += 32) x[i] = (T)F[(int64_t)i * ldf + t];
   __syncwarp();
-  constexpr bool F32 = sizeof(T) == 4;
   for (int j = m - 3; j >= 0; --j) {
     const T b = F32 ? (T)L.betaf[j] : (T)L.beta[j];
     if (b == T(0)) continue;
     const double* v = H + (int64_t)j * ld + j + 1;
     const float* vfj = L.vf + (size_t)j * m + j + 1;
+    const T* vj = vs + refl_off(m, j);
     const int n = m - j - 1;
+    auto vat = [&](int i) -> T { return SMEM ? vj[i] : (F32 ? (T)vfj[i] : (T)v[i]); };
     T s = 0;
-    for (int i = lane; i < n; i += 32) s = fma(F32 ? (T)vfj[i] : (T)v[i], x[j + 1 + i], s);
+    for (int i = lane; i < n; i += 32) s = fma(vat(i), x[j + 1 + i], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     s *= b;
-    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * (F32 ? (T)vfj[i] : (T)v[i]);
+    for (int i = lane; i < n; i += 32) x[j + 1 + i] -= s * vat(i);
     __syncwarp();
   }
   for (int i = lane; i < m; i += 32) F[(int64_t)i * ldf + t] = (double)x[i];
@@ -639,6 +677,27 @@ size_t eig_work_doubles(int mmax) {
 bool tridiag_cluster(double* H, int64_t ld, int m, double* d, double* e, double* beta, bool f32, cudaStream_t s);
 bool tridiag_f32_1cta(const double* H, int64_t ld, int m, double* d, double* e, double* beta, float* df, float* ef,
                       float* betaf, float* vf, cudaStream_t s);
+
+template <typename T>
+void backtransform(const double* H, int64_t ld, int m, int k, double* work, int mmax, double* F, int64_t ldf,
+                   cudaStream_t s) {
+  const unsigned nbt = (unsigned)((k + kBtWarps - 1) / kBtWarps);
+  const size_t vec = sizeof(T) * kBtWarps * (size_t)m;
+  const size_t refl = m >= 2 ? sizeof(T) * (size_t)refl_off_host(m, m - 1) : 0;
+  if (m >= 3 && reserve_dynamic_smem(k_backtransform<T, true>, vec + refl))
+    k_backtransform<T, true><<<nbt, kBtWarps * 32, vec + refl, s>>>(H, ld, m, k, work, mmax, F, ldf);
+  else
+    k_backtransform<T, false><<<nbt, kBtWarps * 32, vec, s>>>(H, ld, m, k, work, mmax, F, ldf);
+}
+
+template <typename T>
+void cluster_orth(int m, int k, double* work, int mmax, double* F, int64_t ldf, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)m * k;
+  if (reserve_dynamic_smem(k_cluster_orth<T, true>, smem))
+    k_cluster_orth<T, true><<<1, 256, smem, s>>>(m, k, work, mmax, F, ldf);
+  else
+    k_cluster_orth<T, false><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
+}
 
 int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, double* F, int64_t ldf, double* ritz,
                    double* info, double* work, bool f32, cudaStream_t s) {
@@ -668,7 +727,6 @@ int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, d
     }
   }
   k_sturm_prep<<<1, 256, 0, s>>>(m, work, mmax);
-  const unsigned nbt = (unsigned)((k + kBtWarps - 1) / kBtWarps);
   const unsigned niv = (unsigned)((k + 31) / 32);
   if (f32) {
     k_multisect<float><<<m, 32, 0, s>>>(m, work, mmax);
@@ -678,8 +736,8 @@ int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, d
       k_invit<float, true, 32><<<niv, 32, ism, s>>>(m, k, work, mmax, F, ldf);
     else
       k_invit<float, false, 32><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
-    k_cluster_orth<float><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
-    k_backtransform<float><<<nbt, kBtWarps * 32, sizeof(float) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F, ldf);
+    cluster_orth<float>(m, k, work, mmax, F, ldf, s);
+    backtransform<float>(H, ld, m, k, work, mmax, F, ldf, s);
   } else {
     k_multisect<double><<<m, 32, 0, s>>>(m, work, mmax);
     k_select<<<1, 256, 0, s>>>(m, k, op, work, mmax, theta, ritz, info, DBL_EPSILON);
@@ -688,9 +746,8 @@ int sym_eig_select(double* H, int64_t ld, int m, int k, int op, double* theta, d
       k_invit<double, true, 8><<<(unsigned)((k + 7) / 8), 8, dsm, s>>>(m, k, work, mmax, F, ldf);
     else
       k_invit<double, false, 32><<<niv, 32, 0, s>>>(m, k, work, mmax, F, ldf);
-    k_cluster_orth<double><<<1, 256, 0, s>>>(m, k, work, mmax, F, ldf);
-    k_backtransform<double><<<nbt, kBtWarps * 32, sizeof(double) * kBtWarps * m, s>>>(H, ld, m, k, work, mmax, F,
-                                                                                       ldf);
+    cluster_orth<double>(m, k, work, mmax, F, ldf, s);
+    backtransform<double>(H, ld, m, k, work, mmax, F, ldf, s);
   }
   return launches;
 }
