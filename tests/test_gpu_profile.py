@@ -3,9 +3,9 @@ counted under one kind (grest_stats.prof_kind_*) and one class (prof_*), so
 the kinds of each class add up to the class, and each path uses the kinds
 it should: the mixed path's tensor-core and narrow Grams and tensor-core
 GEMMs with its FP64 refinement (CUDA-core Gram and GEMM, FP64 SpMM); the
-FP64 path only CUDA-core kinds.  The GEMM class also times the elementwise
-passes around the lift (the sign normalization; in the mixed path also the
-widening of U to FP64), which have no kind."""
+FP64 path only CUDA-core kinds.  The mixed path's GEMM class also times
+two elementwise passes of the refinement (the widening of U to FP64 and the
+sign normalization), which have no kind."""
 import numpy as np
 import pytest
 
@@ -51,7 +51,7 @@ def test_kinds_add_up_to_classes(prec):
         cl = np.array(d["prof_launches"])
         kms = np.array(d["prof_kind_ms"])
         cms = np.array(d["prof_ms"])
-        elementwise = {G.FP64: 1, G.MIXED: 2}[prec]
+        elementwise = {G.FP64: 0, G.MIXED: 2}[prec]
         for c in range(5):
             ks = [KIND[k] for k, cc in CLASS_OF.items() if cc == c]
             assert kl[ks].sum() == cl[c] - (elementwise if c == 2 else 0), (c, kl, cl)
