@@ -9,7 +9,7 @@
 // (coalesced) and broadcasts them by shuffle, then every lane gathers its
 // columns of the neighbour's row (a whole row of X is one contiguous run, so
 // a gather is fully coalesced).  Rows longer than kLongRow (hubs of power-law
-// graphs) go to a second kernel where a block of 8 warps splits the
+// graphs) go to a second kernel where a block of 16 warps splits the
 // neighbour list and reduces in shared memory in a fixed order, so results
 // are deterministic.
 #include "common.cuh"
@@ -202,15 +202,17 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ r
   }
 }
 
-// one block (8 warps) per long row; fixed-order reduction in shared memory
+// one block (kLongWarps warps) per long row; fixed-order reduction in shared memory
+constexpr int kLongWarps = 16;
+
 template <typename Tx, typename T, int NCH, bool HASVAL>
-__global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
+__global__ void __launch_bounds__(kLongWarps * 32) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                                    OpParams op, const int32_t* __restrict__ rows,
                                                    const int64_t* __restrict__ n_rows, const Tx* __restrict__ X,
                                                    int64_t ldx, T* __restrict__ Y, int64_t ldy, int w, int64_t r0,
                                                    int64_t r1) {
-  __shared__ T part[8][NCH * 32];
+  __shared__ T part[kLongWarps][NCH * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nr = *n_rows;
   for (int64_t t = blockIdx.x; t < nr; t += gridDim.x) {
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ r
       continue;
     }
     const int64_t beg = row_off[r], len = row_len[r];
-    const int64_t per = ((len + 7) / 8 + 31) & ~(int64_t)31;
+    const int64_t per = ((len + kLongWarps - 1) / kLongWarps + 31) & ~(int64_t)31;
     int64_t s = beg + wid * per, e = s + per;
     if (e > beg + len) e = beg + len;
     Acc<T, NCH> acc;
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(256) k_spmm_long(const int64_t* __restrict__ r
     for (int c = threadIdx.x; c < w; c += blockDim.x) {
       T sum = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) sum += part[q][c];
+      for (int q = 0; q < kLongWarps; ++q) sum += part[q][c];
       T y = (T)scale * sum;
       if (dcoef != 0.0) y += (T)dcoef * (T)xr[c];
       yr[c] = y;
@@ -259,13 +261,13 @@ void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, cons
     k_spmm_rows<Tx, T, NCH, true><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, X, ldx, Y,
                                                                    ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<Tx, T, NCH, true><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows,
+      k_spmm_long<Tx, T, NCH, true><<<152 * 2, kLongWarps * 32, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows,
                                                              n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   } else {
     k_spmm_rows<Tx, T, NCH, false><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, X, ldx,
                                                                     Y, ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<Tx, T, NCH, false><<<152 * 4, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
+      k_spmm_long<Tx, T, NCH, false><<<152 * 2, kLongWarps * 32, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
                                                               n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   }
 }
