@@ -9,7 +9,7 @@
 // (coalesced) and broadcasts them by shuffle, then every lane gathers its
 // columns of the neighbour's row (a whole row of X is one contiguous run, so
 // a gather is fully coalesced).  Rows longer than kLongRow (hubs of power-law
-// graphs) go to a second kernel where a block of 16 or 32 warps splits the
+// graphs) go to a second kernel where a block of 16 warps splits the
 // neighbour list and reduces in shared memory in a fixed order, so results
 // are deterministic.
 #include "common.cuh"
@@ -202,20 +202,16 @@ __global__ void __launch_bounds__(256) k_spmm_rows(const int64_t* __restrict__ r
   }
 }
 
-// one block of long_warps<T>() warps per long row (the warps split its
-// neighbour list, so the serial chain of gathers per warp is short);
-// fixed-order reduction in shared memory
-template <typename T>
-constexpr int long_warps() { return sizeof(T) == 4 ? 32 : 16; }
+// one block (kLongWarps warps) per long row; fixed-order reduction in shared memory
+constexpr int kLongWarps = 16;
 
 template <typename Tx, typename T, int NCH, bool HASVAL>
-__global__ void __launch_bounds__(long_warps<T>() * 32) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
+__global__ void __launch_bounds__(kLongWarps * 32) k_spmm_long(const int64_t* __restrict__ row_off, const int32_t* __restrict__ row_len,
                                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                                    OpParams op, const int32_t* __restrict__ rows,
                                                    const int64_t* __restrict__ n_rows, const Tx* __restrict__ X,
                                                    int64_t ldx, T* __restrict__ Y, int64_t ldy, int w, int64_t r0,
                                                    int64_t r1) {
-  constexpr int kLongWarps = long_warps<T>();
   __shared__ T part[kLongWarps][NCH * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nr = *n_rows;
@@ -265,13 +261,13 @@ void launch_nch(const Csr& g, const OpParams& op, const int32_t* long_rows, cons
     k_spmm_rows<Tx, T, NCH, true><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, X, ldx, Y,
                                                                    ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<Tx, T, NCH, true><<<152 * 32 / long_warps<T>(), long_warps<T>() * 32, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows,
+      k_spmm_long<Tx, T, NCH, true><<<152 * 2, kLongWarps * 32, 0, s>>>(g.row_off, g.row_len, g.col, g.val, op, long_rows,
                                                              n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   } else {
     k_spmm_rows<Tx, T, NCH, false><<<(unsigned)blocks, 256, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, X, ldx,
                                                                     Y, ldy, w, r0, r1, col_lo);
     if (col_lo == 0)
-      k_spmm_long<Tx, T, NCH, false><<<152 * 32 / long_warps<T>(), long_warps<T>() * 32, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
+      k_spmm_long<Tx, T, NCH, false><<<152 * 2, kLongWarps * 32, 0, s>>>(g.row_off, g.row_len, g.col, nullptr, op, long_rows,
                                                               n_long_dev, X, ldx, Y, ldy, w, r0, r1);
   }
 }
