@@ -1880,7 +1880,8 @@ grest_status grest_get_embedding_async(grest_ctx* c, double* U, double* theta, i
                       (!theta || cudaHostGetDevicePointer((void**)&dT, theta, 0) == cudaSuccess);
   cudaGetLastError();  // a failed lookup only selects the copy path
   if (mapped) {
-    grest::k_pairs_to_host<<<304, 256, 0, cs>>>(c->U, c->ldu, c->K, n, c->theta, dU, dT);
+    // few blocks: the copy overlaps the next update and should take little of it
+    grest::k_pairs_to_host<<<64, 256, 0, cs>>>(c->U, c->ldu, c->K, n, c->theta, dU, dT);
     CK(cudaGetLastError());
   } else {
     if (U && c->ldu == c->K) CK(cudaMemcpyAsync(U, c->U, sizeof(double) * c->K * n, cudaMemcpyDefault, cs));
