@@ -48,7 +48,7 @@ typedef enum {
   GREST_ERR_NUMERIC = 5,         /* fewer than K Ritz pairs, or a Cholesky broke down */
   GREST_ERR_CUDA = 6,            /* CUDA runtime error (no device, launch failure) */
   GREST_ERR_TIMEOUT = 7,         /* a bounded device-side wait expired */
-  GREST_ERR_UNSUPPORTED = 8      /* option not implemented in this build */
+  GREST_ERR_UNSUPPORTED = 8      /* option or combination not implemented   */
 } grest_status;
 
 /* Operator whose leading eigenpairs are tracked (Sec. 2 and Sec. 4.2). */
