@@ -273,3 +273,24 @@ def test_group_create_rejects_bad_arguments_without_gpu(lib):
     assert L.grest_group_apply_updates(None, None, None, None) == 1
     assert L.grest_group_info(None, None, None, None, None, None, None) == 1
     L.grest_group_destroy(None)
+
+
+def test_embedding_async_checks_buffers_before_any_device_call():
+    """Tracker.embedding_async rejects a U buffer with too few rows or the
+    wrong width, and a short theta buffer, on the host, before the library
+    is called (a short buffer would be written past its end by the device)."""
+    import numpy as np
+    from paper_2603_19439_gb300 import grest
+
+    class NoLib:
+        def __getattr__(self, name):
+            raise AssertionError("the library must not be called")
+
+    tr = grest.Tracker.__new__(grest.Tracker)
+    tr.lib, tr.h, tr.k, tr.n = NoLib(), None, 4, 100
+    with pytest.raises(ValueError):
+        tr.embedding_async(np.zeros((99, 4)), np.zeros(4))
+    with pytest.raises(ValueError):
+        tr.embedding_async(np.zeros((100, 3)), np.zeros(4))
+    with pytest.raises(ValueError):
+        tr.embedding_async(np.zeros((100, 4)), np.zeros(3))
