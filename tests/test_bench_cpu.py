@@ -137,3 +137,19 @@ def test_roofline_traffic_per_kind_and_class(tmp_path, monkeypatch):
     # the Gram class: 6 + 7 + 1 = 14 launches, all with a figure
     assert r["traffic"] == (6 * 2_000_000 + 7 * 400_000 + 1 * 600_000) / 14
     assert r["classes"]["gemm"]["traffic"] is None  # gemm_tc's figure is stale
+
+
+def test_kind_sources_exist_and_profile_parses():
+    """Every source file a traffic figure is tied to exists (a renamed file
+    would silently drop the figure), and the committed ncu summary parses
+    into one positive figure per kernel kind it lists."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kind, files in bench.KIND_SOURCES.items():
+        assert bench.source_hash(files) is not None, kind
+    text = open(bench.TRAFFIC_PROFILE).read()
+    rows = [l for l in text.splitlines() if l.startswith("| `") and l.count("|") == 6]
+    assert {r.split("`")[1] for r in rows} == set(bench.KIND_SOURCES)
+    for r in rows:
+        cells = [c.strip() for c in r.strip("|").split("|")]
+        assert float(cells[1]) > 0 and float(cells[2]) > 0 and float(cells[3]) > 0
